@@ -1,0 +1,219 @@
+"""FP64 CPU oracle of TPC sector track finding -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the CPU-baseline leg of the benchmark
+load this package.  It wraps ``tpct_oracle.c`` (plain single-threaded C,
+double precision, compiled with FMA contraction off) through ctypes and
+shares no code with the CUDA library.
+
+Parity status of each oracle function (what pins it, in tests/test_oracle_*):
+  propagation       closed form: exact circle geometry (analytic helix), straight
+                    lines, round trip, mirror symmetry
+  Jacobian          central finite differences
+  Kalman update     batch least squares on linear problems; noiseless helices
+  neighbour finder  brute-force all-pairs search on small events; hand-built fixture
+  clean/start/select brute-force set definitions on small events
+  whole tracker     generator truth (efficiency, fake rate, chi2/ndf, pulls);
+                    the absolute efficiency level is parity unpinned (the paper
+                    prints no tracking-efficiency number)
+"""
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, asdict
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tpct_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libtpct_oracle.so")
+_lib = None
+
+(ORC_UP, ORC_DOWN, ORC_UPC, ORC_DOWNC, ORC_NF_MARGIN, ORC_WEIGHT, ORC_TL_INST, ORC_TL_START,
+ ORC_TL_NHITS, ORC_TL_STOP_UP, ORC_TL_STOP_DOWN, ORC_TL_ROWREF, ORC_TL_XREF, ORC_TL_MARGIN,
+ ORC_TL_PARAM, ORC_TL_HITS, ORC_TR_INST, ORC_TR_TRACKLET, ORC_TR_NCL, ORC_TR_OFFSET, ORC_TR_NDF,
+ ORC_TR_STATUS, ORC_TR_XREF, ORC_TR_CHI2, ORC_TR_MARGIN, ORC_TR_PARAM, ORC_TR_COV,
+ ORC_TR_IDS) = range(28)
+
+_DTYPES = {ORC_NF_MARGIN: np.float64, ORC_WEIGHT: np.uint32, ORC_TL_XREF: np.float64,
+           ORC_TL_MARGIN: np.float64, ORC_TL_PARAM: np.float64, ORC_TR_XREF: np.float64,
+           ORC_TR_CHI2: np.float64, ORC_TR_MARGIN: np.float64, ORC_TR_PARAM: np.float64,
+           ORC_TR_COV: np.float64}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "tpct_oracle.h"))):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int), ("row_x", ctypes.POINTER(ctypes.c_double)),
+                ("tan_half_sector", ctypes.c_double), ("z_max", ctypes.c_double)]
+
+
+class _Cuts(ctypes.Structure):
+    _fields_ = [("bz", ctypes.c_double), ("nf_wy", ctypes.c_double), ("nf_wz", ctypes.c_double),
+                ("nf_dmax", ctypes.c_double), ("s_max", ctypes.c_double),
+                ("edge_margin", ctypes.c_double),
+                ("search_k", ctypes.c_double), ("chi2_max", ctypes.c_double),
+                ("max_miss", ctypes.c_int), ("n_min", ctypes.c_int), ("f_shared", ctypes.c_double),
+                ("n_refit", ctypes.c_int), ("sig_readout", ctypes.c_double),
+                ("sig_cathode", ctypes.c_double), ("c_s", ctypes.c_double), ("c_t", ctypes.c_double),
+                ("c_qpt", ctypes.c_double), ("c_yz_refit", ctypes.c_double),
+                ("c_qpt_refit", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.orc_track.restype = ctypes.c_void_p
+        L.orc_track.argtypes = [ctypes.POINTER(_Geom), ctypes.POINTER(_Cuts), ctypes.c_int64,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_int]
+        L.orc_free.argtypes = [ctypes.c_void_p]
+        L.orc_count.restype = ctypes.c_int64
+        L.orc_count.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_array.restype = ctypes.c_void_p
+        L.orc_array.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_propagate.restype = ctypes.c_int
+        L.orc_propagate.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_kf_update.restype = ctypes.c_double
+        L.orc_kf_update.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double]
+        _lib = L
+    return _lib
+
+
+@dataclass
+class Cuts:
+    """Tracking constants (the stated readings; the paper gives none)."""
+    bz: float = 0.5
+    nf_wy: float = 2.0
+    nf_wz: float = 2.0
+    nf_dmax: float = 0.25
+    s_max: float = 0.999
+    edge_margin: float = 1.0
+    search_k: float = 5.0
+    chi2_max: float = 25.0
+    max_miss: int = 8
+    n_min: int = 20
+    f_shared: float = 0.1
+    n_refit: int = 3
+    sig_readout: float = 0.1
+    sig_cathode: float = 0.1
+    c_s: float = 1.0
+    c_t: float = 1.0
+    c_qpt: float = 100.0
+    c_yz_refit: float = 100.0
+    c_qpt_refit: float = 1.0e4
+
+    @classmethod
+    def for_event(cls, ev, **over):
+        c = cls(bz=ev.bz, sig_readout=ev.sigma.at_readout, sig_cathode=ev.sigma.at_cathode)
+        for k, v in over.items():
+            setattr(c, k, v)
+        return c
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+class Result:
+    """Oracle output as numpy arrays (copied out of the C result)."""
+
+    def __init__(self, handle, n_rows):
+        L = lib()
+        self.n_rows = n_rows
+        names = {
+            ORC_UP: "up", ORC_DOWN: "down", ORC_UPC: "upc", ORC_DOWNC: "downc",
+            ORC_NF_MARGIN: "nf_margin", ORC_WEIGHT: "weight", ORC_TL_INST: "tl_inst",
+            ORC_TL_START: "tl_start", ORC_TL_NHITS: "tl_nhits", ORC_TL_STOP_UP: "tl_stop_up",
+            ORC_TL_STOP_DOWN: "tl_stop_down", ORC_TL_ROWREF: "tl_row_ref", ORC_TL_XREF: "tl_x_ref",
+            ORC_TL_MARGIN: "tl_margin", ORC_TL_PARAM: "tl_param", ORC_TL_HITS: "tl_hits",
+            ORC_TR_INST: "tr_inst", ORC_TR_TRACKLET: "tr_tracklet", ORC_TR_NCL: "tr_ncl",
+            ORC_TR_OFFSET: "tr_offset", ORC_TR_NDF: "tr_ndf", ORC_TR_STATUS: "tr_status",
+            ORC_TR_XREF: "tr_x_ref", ORC_TR_CHI2: "tr_chi2", ORC_TR_MARGIN: "tr_margin",
+            ORC_TR_PARAM: "tr_param", ORC_TR_COV: "tr_cov", ORC_TR_IDS: "tr_ids"}
+        for w, name in names.items():
+            n = L.orc_count(handle, w)
+            dt = _DTYPES.get(w, np.int32)
+            p = L.orc_array(handle, w)
+            if n <= 0 or not p:
+                arr = np.zeros(0, dt)
+            else:
+                buf = (ctypes.c_char * (n * np.dtype(dt).itemsize)).from_address(p)
+                arr = np.frombuffer(buf, dtype=dt).copy()
+            setattr(self, name, arr)
+        self.tl_param = self.tl_param.reshape(-1, 5)
+        self.tl_hits = self.tl_hits.reshape(-1, n_rows)
+        self.tr_param = self.tr_param.reshape(-1, 5)
+        self.tr_cov = self.tr_cov.reshape(-1, 15)
+
+    @property
+    def n_tracks(self):
+        return int(self.tr_inst.shape[0])
+
+    @property
+    def n_tracklets(self):
+        return int(self.tl_inst.shape[0])
+
+    def track_ids(self, k):
+        o = int(self.tr_offset[k])
+        return self.tr_ids[o:o + int(self.tr_ncl[k])]
+
+
+def track(geometry, cuts, sector_offsets, y, z, row=None, x=None, brute_force_nf=False) -> Result:
+    """Run the oracle on all sector instances.  y, z are converted to float64."""
+    L = lib()
+    rx = np.ascontiguousarray(geometry.row_x, dtype=np.float64)
+    g = _Geom(int(rx.shape[0]), rx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+              float(geometry.tan_half_sector), float(geometry.z_max))
+    c = _Cuts(**asdict(cuts))
+    offs = np.ascontiguousarray(sector_offsets, dtype=np.int64)
+    y64 = np.ascontiguousarray(y, dtype=np.float64)
+    z64 = np.ascontiguousarray(z, dtype=np.float64)
+    r32 = None if row is None else np.ascontiguousarray(row, dtype=np.int32)
+    x64 = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+    h = L.orc_track(ctypes.byref(g), ctypes.byref(c), offs.shape[0] - 1, _ptr(offs), _ptr(x64),
+                    _ptr(y64), _ptr(z64), _ptr(r32), int(bool(brute_force_nf)))
+    if not h:
+        raise RuntimeError("oracle failed (invalid arguments or out of memory)")
+    try:
+        return Result(h, int(rx.shape[0]))
+    finally:
+        L.orc_free(h)
+
+
+def track_event(ev, cuts=None, geometry=None, exact=False, **kw) -> Result:
+    """Oracle on a synthetic Event (FP32 positions widened to FP64, or the
+    exact FP64 positions if ``exact``)."""
+    from synth import default_geometry
+    geometry = geometry or default_geometry()
+    cuts = cuts or Cuts.for_event(ev)
+    y = ev.y64 if exact else ev.y
+    z = ev.z64 if exact else ev.z
+    return track(geometry, cuts, ev.sector_offsets, y, z, row=ev.row, **kw)
+
+
+def propagate(bz, s_max, x0, x1, p, want_jacobian=True):
+    L = lib()
+    p = np.ascontiguousarray(p, dtype=np.float64).copy()
+    F = np.zeros(25) if want_jacobian else None
+    rc = L.orc_propagate(bz, s_max, x0, x1, _ptr(p), _ptr(F))
+    return rc, p, (F.reshape(5, 5) if F is not None else None)
+
+
+def kf_update(p, C, my, mz, vy, vz):
+    L = lib()
+    p = np.ascontiguousarray(p, dtype=np.float64).copy()
+    C = np.ascontiguousarray(C, dtype=np.float64).copy()
+    chi2 = L.orc_kf_update(_ptr(p), _ptr(C), my, mz, vy, vz)
+    return chi2, p, C
