@@ -1,0 +1,197 @@
+/*
+ * tpct.h -- C ABI of the GB300 TPC sector track finder.
+ *
+ * The library implements the sector track-finding part of "TPC Processing
+ * (Tracking)", the step that dominates the reconstruction time tables of the
+ * paper (Table 1: 99.37 % of synchronous reconstruction together with
+ * clustering and compression; Tables 2 and 3: 61.41 % and 52.39 % of
+ * asynchronous reconstruction).  The paper names the step but prints no
+ * algorithm; the steps and constants are the stated reading (tpct_cuts):
+ *   1. per sector instance and pad row, bin the clusters in a y/z grid;
+ *   2. link every cluster to the best pair of clusters in the rows above and
+ *      below by a straight-line criterion;
+ *   3. keep reciprocal links only;
+ *   4. start hits: bottoms of linked chains of at least three clusters;
+ *   5. grow a tracklet from every start hit with a Kalman filter on
+ *      (y, z, sin phi, tan lambda, q/pT) with a 5x5 covariance, first upward
+ *      (following links, else searching the grid), then downward;
+ *   6. select tracklets by owned-cluster count and shared fraction;
+ *   7. refit the selected tracks (iterated, FP64 in the default precision).
+ *
+ * Conventions
+ *   - Every pointer inside tpct_clusters, tpct_tracks_out, tpct_debug_out and
+ *     every workspace pointer is DEVICE memory owned by the caller; the
+ *     library never allocates or frees device memory.  Host pointers are
+ *     marked "host".
+ *   - A "sector instance" is one sector of one collision; a batch holds many.
+ *     Clusters are grouped by instance: instance i owns cluster ids
+ *     [sector_offsets[i], sector_offsets[i+1]).  A cluster id is the position
+ *     in the caller's arrays.
+ *   - Calls that take a stream only enqueue work and return; results are
+ *     ready when the stream reaches them.  Errors the host can see are
+ *     returned at once; errors found on the device (output overflow, a
+ *     tracklet count beyond the workspace plan) set a sticky device status
+ *     word read by tpct_last_device_status().
+ *   - A context is not thread-safe; use one context per stream.
+ */
+#ifndef TPCT_H
+#define TPCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tpct_ctx tpct_ctx;
+typedef struct CUstream_st* tpct_stream;   /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  TPCT_OK = 0,
+  TPCT_E_INVALID = 1,    /* bad argument (NULL pointer, negative size, bad geometry) */
+  TPCT_E_NOMEM = 2,      /* host allocation failed, or the workspace is too small */
+  TPCT_E_CAPACITY = 3,   /* device: an output buffer was too small (needed sizes written) */
+  TPCT_E_CUDA = 4,       /* a CUDA runtime call failed */
+  TPCT_E_TIMEOUT = 5,    /* device: a bounded wait gave up */
+  TPCT_E_BUDGET = 6,     /* serving: request larger than the memory budget */
+  TPCT_E_STATE = 7       /* call not valid in the current state (e.g. no workspace) */
+} tpct_status;
+
+/* Readout geometry (host, copied by tpct_create). */
+typedef struct {
+  int n_rows;                 /* pad rows, 3..256 (152 for the TPC) */
+  const double* row_x;        /* host [n_rows]: local x of each row [cm], strictly ascending */
+  double tan_half_sector;     /* acceptance |y| <= x * tan_half_sector (tan 10 deg) */
+  double z_max;               /* drift length [cm] (250) */
+} tpct_geometry;
+
+/* Tracking constants.  tpct_default_cuts() fills the stated readings. */
+typedef struct {
+  double nf_wy, nf_wz;        /* neighbour window |dy|,|dz| <= w * dx            (2, 2) */
+  double nf_dmax;             /* accept best pair iff D <= nf_dmax [cm^2]        (0.25) */
+  double s_max;               /* |sin phi| limit                                  (0.999) */
+  double edge_margin;         /* stop when |y| > x tan + edge_margin [cm]         (1) */
+  double search_k;            /* grid search window in sigmas                    (5) */
+  double chi2_max;            /* per-cluster chi2 cut                            (25) */
+  int max_miss;               /* stop after more consecutive missed rows         (8) */
+  int n_min;                  /* minimum owned clusters per track                (20) */
+  double f_shared;            /* maximum shared fraction                         (0.1) */
+  int n_refit;                /* refit passes                                    (3) */
+  double sig_readout;         /* cluster sigma at drift length 0 [cm]            (0.1) */
+  double sig_cathode;         /* cluster sigma at drift length z_max [cm]        (0.1) */
+  double c_s, c_t, c_qpt;     /* initial variances of sin phi, tan l, q/pT      (1, 1, 100) */
+  double c_yz_refit;          /* refit prior variance of y, z [cm^2]            (100) */
+  double c_qpt_refit;         /* refit prior variance of q/pT                    (1e4) */
+} tpct_cuts;
+
+/* Arithmetic of steps 2-7.  FP32: everything in float.  MIXED (default):
+ * neighbour tests, grid search and helix-transport arithmetic in float; track
+ * state, covariance, Kalman update and refit in double.  FP64: all double. */
+typedef enum { TPCT_PREC_FP32 = 0, TPCT_PREC_MIXED = 1, TPCT_PREC_FP64 = 2 } tpct_precision;
+
+/* Input clusters (device, caller-owned, read-only). */
+typedef struct {
+  const float* x;                 /* [n] local x; used only when row == NULL (nearest row) */
+  const float* y;                 /* [n] local y [cm] */
+  const float* z;                 /* [n] z [cm] */
+  const uint16_t* charge;         /* [n] may be NULL (carried, not used by tracking) */
+  const uint8_t* row;             /* [n] pad row, or NULL */
+  const int64_t* sector_offsets;  /* [n_instances+1], non-decreasing, [0] = 0, [n_instances] = n */
+  int32_t n_instances;
+} tpct_clusters;
+
+/* Output tracks (device, caller-owned).  Tracks are ordered by (instance,
+ * rank of the start hit); each holds its owned clusters, row-ascending. */
+typedef struct {
+  int32_t capacity_tracks;        /* rows of the per-track arrays */
+  int32_t capacity_ids;           /* length of cluster_ids */
+  int32_t* n_tracks;              /* [1] number of tracks (also written on overflow) */
+  int32_t* n_ids;                 /* [1] total cluster ids (also written on overflow) */
+  int32_t* instance;              /* [K] sector instance */
+  int32_t* n_cl;                  /* [K] owned clusters */
+  int32_t* offset;                /* [K] first entry in cluster_ids */
+  int32_t* ndf;                   /* [K] 2 n_cl - 5 */
+  int32_t* status;                /* [K] 0 = refit converged, 1 = transport failed */
+  double* x_ref;                  /* [K] x of the innermost cluster */
+  double* param;                  /* [K*5] y, z, sin phi, tan lambda, q/pT at x_ref */
+  double* cov;                    /* [K*15] covariance, lower triangle row-major */
+  double* chi2;                   /* [K] */
+  int32_t* cluster_ids;           /* [capacity_ids] */
+} tpct_tracks_out;
+
+/* Intermediate results for parity checks (device, caller-owned; any pointer
+ * may be NULL to skip it).  Ids are input cluster ids. */
+typedef struct {
+  int32_t* up;                    /* [n] best neighbour in row r+1 or -1 */
+  int32_t* down;                  /* [n] best neighbour in row r-1 or -1 */
+  int32_t* upc;                   /* [n] reciprocal up link or -1 */
+  int32_t* downc;                 /* [n] reciprocal down link or -1 */
+  uint32_t* weight;               /* [n] selection weight W */
+  int32_t capacity_tracklets;
+  int32_t* n_tracklets;           /* [1] */
+  int32_t* tl_start;              /* [T] start hit id, in (instance, row, id) order */
+  int32_t* tl_nhits;              /* [T] */
+  int32_t* tl_hits;               /* [T*n_rows] row-indexed cluster ids, -1 = none */
+  double* tl_param;               /* [T*5] state at the innermost hit */
+  int32_t* tl_row_ref;            /* [T] row of the innermost hit */
+  int32_t* tr_tracklet;           /* [K] tracklet of each output track (K <= capacity_tracklets) */
+} tpct_debug_out;
+
+/* ---------------------------------------------------------------- context */
+void tpct_default_cuts(tpct_cuts* cuts);
+
+/* Create a context for one geometry, field and cut set.  bz_tesla: field
+ * along +z.  Returns TPCT_E_INVALID for a bad geometry or cut set. */
+tpct_status tpct_create(const tpct_geometry* geometry, double bz_tesla, const tpct_cuts* cuts,
+                        tpct_precision precision, tpct_ctx** out);
+void tpct_destroy(tpct_ctx* ctx);
+
+/* Tuning knobs that never change results (only speed): clusters per grid
+ * bin, threads per block of the tracklet and refit kernels.  0 = default. */
+tpct_status tpct_set_tuning(tpct_ctx* ctx, int clusters_per_bin, int tracklet_block, int refit_block);
+
+/* ---------------------------------------------------------------- workspace */
+/* Device bytes needed to track up to max_clusters clusters in up to
+ * max_instances sector instances in one call. */
+size_t tpct_workspace_bytes(const tpct_ctx* ctx, int64_t max_clusters, int32_t max_instances);
+/* Attach caller-owned device memory (256-byte aligned, >= the size above). */
+tpct_status tpct_set_workspace(tpct_ctx* ctx, void* device_ptr, size_t bytes,
+                               int64_t max_clusters, int32_t max_instances);
+
+/* ---------------------------------------------------------------- tracking */
+/* Track n clusters (all instances of `clusters`) on `stream`: the plain
+ * form, one launch per step. */
+tpct_status tpct_track(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n,
+                       tpct_tracks_out* out, tpct_stream stream);
+
+/* Batched form: the same result as tpct_track on the same batch, run by
+ * persistent kernels that pull work items from device queues, captured once
+ * into a CUDA graph per (n, n_instances) and replayed. */
+tpct_status tpct_track_batch(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n,
+                             tpct_tracks_out* out, tpct_stream stream);
+
+/* Copy intermediate arrays of the last tpct_track / tpct_track_batch call on
+ * this context (enqueued on `stream`). */
+tpct_status tpct_debug_export(tpct_ctx* ctx, tpct_debug_out* dbg, tpct_stream stream);
+
+/* Sticky device status of this context (synchronises the context's last
+ * stream); TPCT_OK, TPCT_E_CAPACITY or TPCT_E_TIMEOUT.  Reading it clears it. */
+tpct_status tpct_last_device_status(tpct_ctx* ctx);
+
+const char* tpct_status_str(tpct_status s);
+
+/* ---------------------------------------------------------------- diagnostics */
+/* Launch count of this context's kernels so far (each kernel launch and each
+ * graph kernel node replay counts one). */
+int64_t tpct_kernel_launches(const tpct_ctx* ctx);
+
+/* Throughput probe of the FP64 and FP32 FMA pipes: runs `blocks` x 256
+ * threads of `iters` independent FMA chains on `stream`, writes nothing to
+ * the caller; returns elapsed milliseconds via *ms (synchronises). */
+tpct_status tpct_probe_fma(int use_fp64, int blocks, int iters, tpct_stream stream, float* ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

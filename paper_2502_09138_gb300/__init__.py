@@ -1,0 +1,232 @@
+"""GB300 TPC sector track finding (arxiv 2502.09138, the "TPC Processing
+(Tracking)" step of its Tables 1-3): Python front end of libtpct.so.
+
+    trk = Tracker(precision="mixed")
+    trk.reserve(max_clusters, max_instances)
+    res = trk.track(DeviceClusters.from_event(ev))      # plain form
+    res = trk.track(..., batched=True)                  # graph-captured form
+
+Device buffers are torch tensors; every step runs in the library's kernels.
+"""
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+N_ROWS_TPC = 152
+
+
+def default_cuts(**over) -> B.Cuts:
+    c = B.Cuts()
+    B.load().tpct_default_cuts(ctypes.byref(c))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+@dataclass
+class DeviceClusters:
+    """Clusters resident on the device (SoA)."""
+    x: torch.Tensor
+    y: torch.Tensor
+    z: torch.Tensor
+    charge: torch.Tensor
+    row: torch.Tensor            # uint8, or None (row from x)
+    sector_offsets: torch.Tensor  # int64 [n_instances + 1]
+
+    @property
+    def n(self):
+        return int(self.y.shape[0])
+
+    @property
+    def n_instances(self):
+        return int(self.sector_offsets.shape[0] - 1)
+
+    @classmethod
+    def from_event(cls, ev, device="cuda", with_row=True, non_blocking=False):
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device, non_blocking=non_blocking)
+        return cls(t(ev.x), t(ev.y), t(ev.z), t(ev.charge), t(ev.row) if with_row else None,
+                   t(ev.sector_offsets.astype(np.int64)))
+
+    def as_struct(self) -> B.Clusters:
+        return B.Clusters(_ptr(self.x), _ptr(self.y), _ptr(self.z), _ptr(self.charge), _ptr(self.row),
+                          _ptr(self.sector_offsets), self.n_instances)
+
+
+class Tracks:
+    """Output buffers of one tracking call (device tensors)."""
+
+    def __init__(self, cap_tracks, cap_ids, device):
+        kw = dict(device=device)
+        self.capacity_tracks, self.capacity_ids = int(cap_tracks), int(cap_ids)
+        self.counts = torch.zeros(2, dtype=torch.int32, **kw)
+        self.instance = torch.empty(cap_tracks, dtype=torch.int32, **kw)
+        self.n_cl = torch.empty(cap_tracks, dtype=torch.int32, **kw)
+        self.offset = torch.empty(cap_tracks, dtype=torch.int32, **kw)
+        self.ndf = torch.empty(cap_tracks, dtype=torch.int32, **kw)
+        self.status = torch.empty(cap_tracks, dtype=torch.int32, **kw)
+        self.x_ref = torch.empty(cap_tracks, dtype=torch.float64, **kw)
+        self.param = torch.empty(cap_tracks, 5, dtype=torch.float64, **kw)
+        self.cov = torch.empty(cap_tracks, 15, dtype=torch.float64, **kw)
+        self.chi2 = torch.empty(cap_tracks, dtype=torch.float64, **kw)
+        self.cluster_ids = torch.empty(max(1, cap_ids), dtype=torch.int32, **kw)
+
+    def as_struct(self) -> B.TracksOut:
+        c = self.counts
+        return B.TracksOut(self.capacity_tracks, self.capacity_ids, ctypes.c_void_p(c.data_ptr()),
+                           ctypes.c_void_p(c.data_ptr() + 4), _ptr(self.instance), _ptr(self.n_cl),
+                           _ptr(self.offset), _ptr(self.ndf), _ptr(self.status), _ptr(self.x_ref),
+                           _ptr(self.param), _ptr(self.cov), _ptr(self.chi2), _ptr(self.cluster_ids))
+
+    def to_host(self):
+        """Copy the filled part to numpy (synchronises)."""
+        nt, ni = (int(v) for v in self.counts.cpu())
+        nt_, ni_ = min(nt, self.capacity_tracks), min(ni, self.capacity_ids)
+        g = lambda t, k: t[:k].cpu().numpy()
+        return dict(n_tracks=nt, n_ids=ni, instance=g(self.instance, nt_), n_cl=g(self.n_cl, nt_),
+                    offset=g(self.offset, nt_), ndf=g(self.ndf, nt_), status=g(self.status, nt_),
+                    x_ref=g(self.x_ref, nt_), param=g(self.param, nt_), cov=g(self.cov, nt_),
+                    chi2=g(self.chi2, nt_), cluster_ids=g(self.cluster_ids, ni_))
+
+
+class Debug:
+    """Intermediate arrays for parity checks (device tensors)."""
+
+    def __init__(self, n, cap_tracklets, n_rows, device):
+        i32 = dict(dtype=torch.int32, device=device)
+        self.n_rows = n_rows
+        self.up = torch.empty(max(1, n), **i32)
+        self.down = torch.empty(max(1, n), **i32)
+        self.upc = torch.empty(max(1, n), **i32)
+        self.downc = torch.empty(max(1, n), **i32)
+        self.weight = torch.empty(max(1, n), dtype=torch.int32, device=device)
+        self.cap = int(cap_tracklets)
+        self.n_tracklets = torch.zeros(1, **i32)
+        self.tl_start = torch.empty(max(1, cap_tracklets), **i32)
+        self.tl_nhits = torch.empty(max(1, cap_tracklets), **i32)
+        self.tl_hits = torch.empty(max(1, cap_tracklets) * n_rows, **i32)
+        self.tl_param = torch.empty(max(1, cap_tracklets) * 5, dtype=torch.float64, device=device)
+        self.tl_row_ref = torch.empty(max(1, cap_tracklets), **i32)
+        self.tr_tracklet = torch.full((max(1, cap_tracklets),), -1, **i32)
+        self._n = n
+
+    def as_struct(self) -> B.DebugOut:
+        return B.DebugOut(_ptr(self.up), _ptr(self.down), _ptr(self.upc), _ptr(self.downc),
+                          _ptr(self.weight), self.cap, _ptr(self.n_tracklets), _ptr(self.tl_start),
+                          _ptr(self.tl_nhits), _ptr(self.tl_hits), _ptr(self.tl_param), _ptr(self.tl_row_ref),
+                          _ptr(self.tr_tracklet))
+
+    def to_host(self):
+        n = self._n
+        T = int(self.n_tracklets.cpu()[0])
+        Tc = min(T, self.cap)
+        g = lambda t, k: t[:k].cpu().numpy()
+        return dict(up=g(self.up, n), down=g(self.down, n), upc=g(self.upc, n), downc=g(self.downc, n),
+                    weight=g(self.weight, n).view(np.uint32), n_tracklets=T, tl_start=g(self.tl_start, Tc),
+                    tl_nhits=g(self.tl_nhits, Tc), tl_hits=g(self.tl_hits, Tc * self.n_rows).reshape(Tc, self.n_rows),
+                    tl_param=g(self.tl_param, Tc * 5).reshape(Tc, 5), tl_row_ref=g(self.tl_row_ref, Tc),
+                    tr_tracklet=self.tr_tracklet.cpu().numpy())
+
+
+class Tracker:
+    """One context of the CUDA library (one geometry, field, cut set, precision)."""
+
+    def __init__(self, row_x=None, tan_half_sector=None, z_max=250.0, bz=0.5, cuts=None,
+                 precision="mixed", device="cuda"):
+        import math
+        L = B.load()
+        if row_x is None:
+            from synth.geometry import row_radii   # the TPC's 152 rows
+            row_x = row_radii()
+        self.row_x = np.ascontiguousarray(row_x, dtype=np.float64)
+        self.n_rows = int(self.row_x.shape[0])
+        tan_half_sector = math.tan(math.radians(10.0)) if tan_half_sector is None else tan_half_sector
+        g = B.Geometry(self.n_rows, self.row_x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       float(tan_half_sector), float(z_max))
+        self.cuts = cuts if cuts is not None else default_cuts()
+        self.precision = precision
+        h = ctypes.c_void_p()
+        B.check(L.tpct_create(ctypes.byref(g), float(bz), ctypes.byref(self.cuts), B.PRECISION[precision],
+                              ctypes.byref(h)), "tpct_create")
+        self._h = h
+        self.device = torch.device(device)
+        self._ws = None
+        self._plan = (0, 0)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.load().tpct_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, clusters_per_bin=0, tracklet_block=0, refit_block=0):
+        B.check(B.load().tpct_set_tuning(self._h, clusters_per_bin, tracklet_block, refit_block),
+                "tpct_set_tuning")
+
+    def workspace_bytes(self, max_clusters, max_instances):
+        return int(B.load().tpct_workspace_bytes(self._h, int(max_clusters), int(max_instances)))
+
+    def reserve(self, max_clusters, max_instances):
+        nb = self.workspace_bytes(max_clusters, max_instances)
+        if nb == 0:
+            raise ValueError("invalid workspace plan")
+        self._ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        B.check(B.load().tpct_set_workspace(self._h, ctypes.c_void_p(aligned), nb, int(max_clusters),
+                                            int(max_instances)), "tpct_set_workspace")
+        self._plan = (int(max_clusters), int(max_instances))
+
+    def make_output(self, n, cap_tracks=None, cap_ids=None):
+        cap_tracks = n // 3 + 1 if cap_tracks is None else cap_tracks
+        cap_ids = n if cap_ids is None else cap_ids
+        return Tracks(cap_tracks, cap_ids, self.device)
+
+    def track(self, clusters: DeviceClusters, out: Tracks = None, batched=False, stream=None):
+        n, ni = clusters.n, clusters.n_instances
+        if self._ws is None or n > self._plan[0] or ni > self._plan[1]:
+            self.reserve(max(n, self._plan[0]), max(ni, self._plan[1]))
+        if out is None:
+            out = self.make_output(n)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._keep = (clusters, out)
+        cs, os_ = clusters.as_struct(), out.as_struct()
+        fn = B.load().tpct_track_batch if batched else B.load().tpct_track
+        B.check(fn(self._h, ctypes.byref(cs), n, ctypes.byref(os_), ctypes.c_void_p(s.cuda_stream)),
+                "tpct_track_batch" if batched else "tpct_track")
+        return out
+
+    def debug(self, n, cap_tracklets=None, stream=None):
+        cap_tracklets = n // 3 + 1 if cap_tracklets is None else cap_tracklets
+        d = Debug(n, cap_tracklets, self.n_rows, self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ds = d.as_struct()
+        B.check(B.load().tpct_debug_export(self._h, ctypes.byref(ds), ctypes.c_void_p(s.cuda_stream)),
+                "tpct_debug_export")
+        return d
+
+    def device_status(self):
+        return int(B.load().tpct_last_device_status(self._h))
+
+    def kernel_launches(self):
+        return int(B.load().tpct_kernel_launches(self._h))
+
+
+def probe_fma(use_fp64, blocks, iters, stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    ms = ctypes.c_float()
+    B.check(B.load().tpct_probe_fma(int(use_fp64), int(blocks), int(iters), ctypes.c_void_p(s.cuda_stream),
+                                    ctypes.byref(ms)), "tpct_probe_fma")
+    return float(ms.value)

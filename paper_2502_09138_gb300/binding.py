@@ -1,0 +1,97 @@
+"""ctypes binding of libtpct.so (include/tpct.h).  Argument marshalling only:
+every step of track finding runs in the library's CUDA kernels.  PyTorch
+provides device memory and streams."""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtpct.so")
+
+c_int, c_int32, c_int64, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
+                                                        ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t)
+
+TPCT_OK, TPCT_E_INVALID, TPCT_E_NOMEM, TPCT_E_CAPACITY, TPCT_E_CUDA, TPCT_E_TIMEOUT, TPCT_E_BUDGET, \
+    TPCT_E_STATE = range(8)
+PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_rows", c_int), ("row_x", ctypes.POINTER(c_double)),
+                ("tan_half_sector", c_double), ("z_max", c_double)]
+
+
+class Cuts(ctypes.Structure):
+    _fields_ = [("nf_wy", c_double), ("nf_wz", c_double), ("nf_dmax", c_double), ("s_max", c_double),
+                ("edge_margin", c_double), ("search_k", c_double), ("chi2_max", c_double),
+                ("max_miss", c_int), ("n_min", c_int), ("f_shared", c_double), ("n_refit", c_int),
+                ("sig_readout", c_double), ("sig_cathode", c_double), ("c_s", c_double),
+                ("c_t", c_double), ("c_qpt", c_double), ("c_yz_refit", c_double),
+                ("c_qpt_refit", c_double)]
+
+
+class Clusters(ctypes.Structure):
+    _fields_ = [("x", c_void_p), ("y", c_void_p), ("z", c_void_p), ("charge", c_void_p),
+                ("row", c_void_p), ("sector_offsets", c_void_p), ("n_instances", c_int32)]
+
+
+class TracksOut(ctypes.Structure):
+    _fields_ = [("capacity_tracks", c_int32), ("capacity_ids", c_int32), ("n_tracks", c_void_p),
+                ("n_ids", c_void_p), ("instance", c_void_p), ("n_cl", c_void_p), ("offset", c_void_p),
+                ("ndf", c_void_p), ("status", c_void_p), ("x_ref", c_void_p), ("param", c_void_p),
+                ("cov", c_void_p), ("chi2", c_void_p), ("cluster_ids", c_void_p)]
+
+
+class DebugOut(ctypes.Structure):
+    _fields_ = [("up", c_void_p), ("down", c_void_p), ("upc", c_void_p), ("downc", c_void_p),
+                ("weight", c_void_p), ("capacity_tracklets", c_int32), ("n_tracklets", c_void_p),
+                ("tl_start", c_void_p), ("tl_nhits", c_void_p), ("tl_hits", c_void_p),
+                ("tl_param", c_void_p), ("tl_row_ref", c_void_p), ("tr_tracklet", c_void_p)]
+
+
+EXPORTS = {
+    "tpct_default_cuts": (None, [ctypes.POINTER(Cuts)]),
+    "tpct_create": (c_int, [ctypes.POINTER(Geometry), c_double, ctypes.POINTER(Cuts), c_int,
+                            ctypes.POINTER(c_void_p)]),
+    "tpct_destroy": (None, [c_void_p]),
+    "tpct_set_tuning": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "tpct_workspace_bytes": (c_size_t, [c_void_p, c_int64, c_int32]),
+    "tpct_set_workspace": (c_int, [c_void_p, c_void_p, c_size_t, c_int64, c_int32]),
+    "tpct_track": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut), c_void_p]),
+    "tpct_track_batch": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut),
+                                 c_void_p]),
+    "tpct_debug_export": (c_int, [c_void_p, ctypes.POINTER(DebugOut), c_void_p]),
+    "tpct_last_device_status": (c_int, [c_void_p]),
+    "tpct_status_str": (ctypes.c_char_p, [c_int]),
+    "tpct_kernel_launches": (c_int64, [c_void_p]),
+    "tpct_probe_fma": (c_int, [c_int, c_int, c_int, c_void_p, ctypes.POINTER(ctypes.c_float)]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libtpct.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2502_09138_gb300/build.py "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class TpctError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = load().tpct_status_str(code).decode()
+        super().__init__(f"{where}: {msg} (status {code})")
+
+
+def check(code, where):
+    if code != TPCT_OK:
+        raise TpctError(code, where)

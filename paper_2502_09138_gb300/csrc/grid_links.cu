@@ -1,0 +1,457 @@
+// Steps 1-4 of sector track finding: row binning into y/z grids, neighbour
+// finding by the straight-line criterion, reciprocal cleaning, start hits.
+// (The paper's "TPC Processing (Tracking)" row, Tables 1-3.)
+#include "tpct_internal.cuh"
+
+namespace tpct {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+
+// ------------------------------------------------------------------ step 1: rows and grids
+__global__ void k_init_rows(const __grid_constant__ Params P) {
+  int nr = P.n_inst * P.n_rows;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nr; i += gridDim.x * blockDim.x) {
+    P.row_count[i] = 0;
+    P.row_tl_count[i] = 0;
+    if (i < nr) {
+      P.row_ext[4 * i + 0] = 0xffffffffu;
+      P.row_ext[4 * i + 1] = 0u;
+      P.row_ext[4 * i + 2] = 0xffffffffu;
+      P.row_ext[4 * i + 3] = 0u;
+    }
+  }
+}
+
+// instance of input cluster c: the largest i with inst_off[i] <= c
+__device__ __forceinline__ int instance_of(const Params& P, int c) {
+  int lo = 0, hi = P.n_inst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (P.inst_off[mid] <= (int64_t)c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// row whose x is nearest to xc (ties to the lower row)
+__device__ __forceinline__ int nearest_row(const Params& P, float xc) {
+  double x = (double)xc;
+  int lo = 0, hi = P.n_rows - 1;
+  while (lo < hi) {            // first row with rx >= x (or the last row)
+    int mid = (lo + hi) >> 1;
+    if (P.rx[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  if (lo > 0 && fabs(x - P.rx[lo - 1]) <= fabs(x - P.rx[lo])) lo = lo - 1;
+  return lo;
+}
+
+__global__ void k_rows(const __grid_constant__ Params P) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P.n; c += gridDim.x * blockDim.x) {
+    int inst = instance_of(P, c);
+    int r = P.row ? (int)P.row[c] : nearest_row(P, P.x[c]);
+    if (r >= P.n_rows) {
+      atomicOr(P.status, kDevCapacity);
+      r = P.n_rows - 1;
+    }
+    int ir = inst * P.n_rows + r;
+    P.c_ir[c] = ir;
+    atomicAdd(&P.row_count[ir], 1);
+    uint32_t ky = float_order_key(P.y[c]), kz = float_order_key(P.z[c]);
+    atomicMin(&P.row_ext[4 * ir + 0], ky);
+    atomicMax(&P.row_ext[4 * ir + 1], ky);
+    atomicMin(&P.row_ext[4 * ir + 2], kz);
+    atomicMax(&P.row_ext[4 * ir + 3], kz);
+  }
+}
+
+// Grid of each row: about clusters_per_bin clusters per bin, bins roughly
+// square in cm.  Bin arrays of row ir start at row_start/k + 2 ir, which
+// leaves room for max(1, n/k) bins plus the end entry without a scan.
+__global__ void k_grid_dims(const __grid_constant__ Params P) {
+  int nr = P.n_inst * P.n_rows;
+  int k = P.clusters_per_bin;
+  for (int ir = blockIdx.x * blockDim.x + threadIdx.x; ir < nr; ir += gridDim.x * blockDim.x) {
+    int n = P.row_count[ir];
+    int start = P.row_start[ir];
+    int nb = max(1, n / k);
+    float ymin = 0.f, ymax = 0.f, zmin = 0.f, zmax = 0.f;
+    if (n > 0) {
+      ymin = float_from_order_key(P.row_ext[4 * ir + 0]);
+      ymax = float_from_order_key(P.row_ext[4 * ir + 1]);
+      zmin = float_from_order_key(P.row_ext[4 * ir + 2]);
+      zmax = float_from_order_key(P.row_ext[4 * ir + 3]);
+    }
+    float ly = fmaxf(ymax - ymin, 1e-3f), lz = fmaxf(zmax - zmin, 1e-3f);
+    int ny = (int)rintf(sqrtf((float)nb * ly / lz));
+    ny = min(max(ny, 1), min(nb, 32767));
+    int nz = min(max(nb / ny, 1), 32767);
+    RowGrid g;
+    g.y0 = ymin;
+    g.z0 = zmin;
+    g.idy = (float)ny / ly;
+    g.idz = (float)nz / lz;
+    g.bin_base = start / k + 2 * ir;
+    g.ny = (int16_t)ny;
+    g.nz = (int16_t)nz;
+    P.grid[ir] = g;
+  }
+}
+
+__global__ void k_bin_count(const __grid_constant__ Params P) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P.n; c += gridDim.x * blockDim.x) {
+    int ir = P.c_ir[c];
+    RowGrid g = P.grid[ir];
+    int b = g.bin_base + bin_z(g, P.z[c]) * g.ny + bin_y(g, P.y[c]);
+    P.c_bin[c] = b;
+    atomicAdd(&P.bin_count[b], 1);
+  }
+}
+
+// bin_count is zero again here and serves as the fill cursor
+__global__ void k_scatter(const __grid_constant__ Params P) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P.n; c += gridDim.x * blockDim.x) {
+    int b = P.c_bin[c];
+    int pos = P.bin_start[b] + atomicAdd(&P.bin_count[b], 1);
+    P.sy[pos] = P.y[c];
+    P.sz[pos] = P.z[c];
+    P.sid[pos] = c;
+    P.srow[pos] = (uint8_t)(P.c_ir[c] % P.n_rows);
+    P.W[pos] = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ scans
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// exclusive block scan of one value per thread; *total receives the block sum
+template <class T>
+__device__ T block_excl_scan(T v, T* total) {
+  __shared__ T warp_sums[32];
+  __shared__ T block_total;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T inc = warp_incl_scan(v);
+  if (lane == 31) warp_sums[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const T s = lane < nw ? warp_sums[lane] : (T)0;
+    const T si = warp_incl_scan(s);
+    if (lane < nw) warp_sums[lane] = si - s;
+    if (lane == 31) block_total = si;
+  }
+  __syncthreads();
+  const T res = inc - v + warp_sums[w];
+  if (total) *total = block_total;
+  __syncthreads();
+  return res;
+}
+
+template <class Tin, class T>
+__global__ void k_scan_reduce(const Tin* in, int64_t m, T* tmp) {
+  int64_t base = (int64_t)blockIdx.x * kScanChunk;
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+    if (i < m) s += (T)in[i];
+  }
+  T total;
+  block_excl_scan<T>(s, &total);
+  if (threadIdx.x == 0) tmp[blockIdx.x] = total;
+}
+
+template <class T>
+__global__ void k_scan_top(T* tmp, int64_t nb) {
+  T carry = 0;
+  for (int64_t base = 0; base < nb; base += kScanThreads) {
+    int64_t i = base + threadIdx.x;
+    T v = i < nb ? tmp[i] : (T)0;
+    T total;
+    T e = block_excl_scan<T>(v, &total);
+    if (i < nb) tmp[i] = e + carry;
+    carry += total;
+    __syncthreads();
+  }
+}
+
+template <class Tin, class Tout, class T>
+__global__ void k_scan_down(const Tin* in, Tout* out, int64_t m, const T* tmp) {
+  int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k;
+    v[k] = i < m ? (T)in[i] : (T)0;
+    s += v[k];
+  }
+  T total;
+  T e = block_excl_scan<T>(s, &total) + tmp[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k;
+    if (i < m) out[i] = (Tout)e;
+    if (i == m - 1) out[m] = (Tout)(e + v[k]);
+    e += v[k];
+  }
+}
+
+__global__ void k_zero_total_i32(int32_t* out) { out[0] = 0; }
+__global__ void k_zero_total_u64(uint64_t* out) { out[0] = 0; }
+
+// ------------------------------------------------------------------ step 2: neighbours
+// Straight-line criterion: for hit h in row r and candidates u (row r+1),
+// d (row r-1) inside |dy| <= wy dx, |dz| <= wz dx, the pair minimising
+// D = (yhat - y_h)^2 + (zhat - z_h)^2, yhat = y_d + f (y_u - y_d),
+// f = (x_r - x_d) / (x_u - x_d), ties to the smaller (id_u, id_d); the pair
+// is kept iff D <= D_max.  Evaluated relative to the hit (differences
+// first) so that the FP32 variant keeps ~1e-7 relative accuracy in D.
+template <class E>
+struct NfRowSide {
+  RowGrid g;
+  E w_y, w_z;
+  int32_t bin0;   // absolute index of the row's first bin
+};
+
+template <class E>
+__device__ __forceinline__ void bin_range(const RowGrid& g, float c, float w, int& i0, int& i1, bool is_y) {
+  float lo = c - w * 1.00001f - 1e-5f, hi = c + w * 1.00001f + 1e-5f;
+  if (is_y) { i0 = bin_y(g, lo); i1 = bin_y(g, hi); }
+  else { i0 = bin_z(g, lo); i1 = bin_z(g, hi); }
+}
+
+template <int MODE>
+__global__ void k_neighbours(const __grid_constant__ Params P) {
+  using E = typename Prec<MODE>::E;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int nr = P.n_inst * P.n_rows;
+  for (int ir = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ir < nr; ir += warps) {
+    const int r = ir % P.n_rows;
+    const int beg = P.row_start[ir], end = P.row_start[ir + 1];
+    if (r == 0 || r == P.n_rows - 1) {
+      for (int p = beg + lane; p < end; p += 32) { P.up[p] = -1; P.down[p] = -1; }
+      continue;
+    }
+    const double xr = P.rx[r], xu = P.rx[r + 1], xd = P.rx[r - 1];
+    const E f = (E)((xr - xd) / (xu - xd));
+    const E wyu = (E)(P.nf_wy * (xu - xr)), wzu = (E)(P.nf_wz * (xu - xr));
+    const E wyd = (E)(P.nf_wy * (xr - xd)), wzd = (E)(P.nf_wz * (xr - xd));
+    const E dmax = (E)P.nf_dmax;
+    const RowGrid gu = P.grid[ir + 1], gd = P.grid[ir - 1];
+    for (int p = beg + lane; p < end; p += 32) {
+      const float yh = P.sy[p], zh = P.sz[p];
+      int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
+      bin_range<E>(gu, yh, (float)wyu, uy0, uy1, true);
+      bin_range<E>(gu, zh, (float)wzu, uz0, uz1, false);
+      bin_range<E>(gd, yh, (float)wyd, dy0, dy1, true);
+      bin_range<E>(gd, zh, (float)wzd, dz0, dz1, false);
+      E best = (E)0;
+      int bu = -1, bd = -1, idu = -1, idd = -1;
+      for (int iz = uz0; iz <= uz1; ++iz) {
+        const int q0 = P.bin_start[gu.bin_base + iz * gu.ny + uy0];
+        const int q1 = P.bin_start[gu.bin_base + iz * gu.ny + uy1 + 1];
+        for (int q = q0; q < q1; ++q) {
+          const E ayu = (E)P.sy[q] - (E)yh, azu = (E)P.sz[q] - (E)zh;
+          if (!(fabs(ayu) <= wyu && fabs(azu) <= wzu)) continue;
+          for (int jz = dz0; jz <= dz1; ++jz) {
+            const int s0 = P.bin_start[gd.bin_base + jz * gd.ny + dy0];
+            const int s1 = P.bin_start[gd.bin_base + jz * gd.ny + dy1 + 1];
+            for (int s = s0; s < s1; ++s) {
+              const E ayd = (E)P.sy[s] - (E)yh, azd = (E)P.sz[s] - (E)zh;
+              if (!(fabs(ayd) <= wyd && fabs(azd) <= wzd)) continue;
+              const E ry = ayd + f * (ayu - ayd);
+              const E rz = azd + f * (azu - azd);
+              const E D = ry * ry + rz * rz;
+              bool better;
+              if (bu < 0 || D < best) {
+                better = true;
+              } else if (D == best) {
+                if (idu < 0) { idu = P.sid[bu]; idd = P.sid[bd]; }
+                const int iu = P.sid[q], id = P.sid[s];
+                better = iu < idu || (iu == idu && id < idd);
+              } else {
+                better = false;
+              }
+              if (better) { best = D; bu = q; bd = s; idu = -1; idd = -1; }
+            }
+          }
+        }
+      }
+      const bool ok = bu >= 0 && best <= dmax;
+      P.up[p] = ok ? bu : -1;
+      P.down[p] = ok ? bd : -1;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ steps 3-4
+// upc[p] = up[p] if down[up[p]] == p; start iff no reciprocal down link and
+// a reciprocal chain p -> u -> uu.  Per row: count of start hits.
+__global__ void k_clean_start(const __grid_constant__ Params P) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int nr = P.n_inst * P.n_rows;
+  for (int ir = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ir < nr; ir += warps) {
+    const int beg = P.row_start[ir], end = P.row_start[ir + 1];
+    int count = 0;
+    for (int base = beg; base < end; base += 32) {
+      const int p = base + lane;
+      bool start = false;
+      if (p < end) {
+        const int u = P.up[p], d = P.down[p];
+        const int uc = (u >= 0 && P.down[u] == p) ? u : -1;
+        const bool dc = d >= 0 && P.up[d] == p;
+        bool chain = false;
+        if (uc >= 0) {
+          const int uu = P.up[uc];
+          chain = uu >= 0 && P.down[uu] == uc;
+        }
+        start = !dc && chain;
+        P.upc[p] = uc;
+        P.sflag[p] = start ? 1 : 0;
+      }
+      count += __popc(__ballot_sync(0xffffffffu, start));
+    }
+    if (lane == 0) P.row_tl_count[ir] = count;
+  }
+}
+
+// Tracklet index of a start hit: row base + number of start hits of the same
+// row with a smaller input id (start-hit order is (instance, row, id)).
+__global__ void k_start_fill(const __grid_constant__ Params P) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int nr = P.n_inst * P.n_rows;
+  for (int ir = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ir < nr; ir += warps) {
+    if (P.row_tl_count[ir] == 0) continue;
+    const int beg = P.row_start[ir], end = P.row_start[ir + 1];
+    const int tbase = P.row_tl_base[ir];
+    for (int base = beg; base < end; base += 32) {
+      const int p = base + lane;
+      const bool mine = p < end && P.sflag[p];
+      const int my_id = mine ? P.sid[p] : 0;
+      if (__ballot_sync(0xffffffffu, mine) == 0u) continue;
+      int rank = 0;
+      for (int b2 = beg; b2 < end; b2 += 32) {
+        const int q = b2 + lane;
+        const bool st = q < end && P.sflag[q];
+        const int qid = st ? P.sid[q] : 0x7fffffff;
+        uint32_t m = __ballot_sync(0xffffffffu, st);
+        while (m) {
+          const int k = __ffs(m) - 1;
+          m &= m - 1;
+          const int other = __shfl_sync(0xffffffffu, qid, k);
+          rank += (mine && other < my_id) ? 1 : 0;
+        }
+      }
+      if (mine) {
+        const int t = tbase + rank;
+        if (t < P.tcap) {
+          P.tl_start[t] = p;
+          P.tl_ir[t] = ir;
+        } else {
+          atomicOr(P.status, kDevTrackletCap);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ debug export of links
+__global__ void k_export_links(const __grid_constant__ Params P, tpct_debug_out D) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n; p += gridDim.x * blockDim.x) {
+    const int id = P.sid[p];
+    const int u = P.up[p], d = P.down[p];
+    if (D.up) D.up[id] = u >= 0 ? P.sid[u] : -1;
+    if (D.down) D.down[id] = d >= 0 ? P.sid[d] : -1;
+    if (D.upc) { const int uc = P.upc[p]; D.upc[id] = uc >= 0 ? P.sid[uc] : -1; }
+    if (D.downc) D.downc[id] = (d >= 0 && P.up[d] == p) ? P.sid[d] : -1;
+    if (D.weight) D.weight[id] = P.W[p];
+  }
+}
+
+int blocks_for(int64_t work, int block) {
+  int64_t b = (work + block - 1) / block;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (int)b;
+}
+
+}  // namespace
+
+int64_t scan_tmp_elems(int64_t m) { return (m + kScanChunk - 1) / kScanChunk + 1; }
+
+void launch_rows(const Params& P, cudaStream_t s) {
+  const int nr = P.n_inst * P.n_rows;
+  k_init_rows<<<blocks_for(nr + 1, kBlock), kBlock, 0, s>>>(P);
+  k_rows<<<blocks_for(P.n, kBlock), kBlock, 0, s>>>(P);
+}
+
+void launch_grid_dims(const Params& P, cudaStream_t s) {
+  k_grid_dims<<<blocks_for(P.n_inst * P.n_rows, kBlock), kBlock, 0, s>>>(P);
+}
+
+void launch_bin_count(const Params& P, cudaStream_t s) {
+  k_bin_count<<<blocks_for(P.n, kBlock), kBlock, 0, s>>>(P);
+}
+
+void launch_scatter(const Params& P, cudaStream_t s) {
+  k_scatter<<<blocks_for(P.n, kBlock), kBlock, 0, s>>>(P);
+}
+
+template <class Tin, class T>
+static void scan_impl(const Tin* in, Tin* out, int64_t m, T* tmp, cudaStream_t s) {
+  if (m <= 0) {
+    if constexpr (sizeof(Tin) == 4) k_zero_total_i32<<<1, 1, 0, s>>>((int32_t*)out);
+    else k_zero_total_u64<<<1, 1, 0, s>>>((uint64_t*)out);
+    return;
+  }
+  int64_t nb = (m + kScanChunk - 1) / kScanChunk;
+  k_scan_reduce<Tin, T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, m, tmp);
+  k_scan_top<T><<<1, kScanThreads, 0, s>>>(tmp, nb);
+  k_scan_down<Tin, Tin, T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, m, tmp);
+}
+
+void launch_scan_i32(const int32_t* in, int32_t* out, int64_t m, uint64_t* tmp, cudaStream_t s) {
+  scan_impl<int32_t, uint64_t>(in, out, m, tmp, s);
+}
+void launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t m, uint64_t* tmp, cudaStream_t s) {
+  scan_impl<uint64_t, uint64_t>(in, out, m, tmp, s);
+}
+
+void launch_neighbours(const Params& P, int mode, cudaStream_t s) {
+  const int warps = P.n_inst * P.n_rows;
+  const int blocks = blocks_for((int64_t)warps * 32, kBlock);
+  if (mode == 0) k_neighbours<0><<<blocks, kBlock, 0, s>>>(P);
+  else if (mode == 1) k_neighbours<1><<<blocks, kBlock, 0, s>>>(P);
+  else k_neighbours<2><<<blocks, kBlock, 0, s>>>(P);
+}
+
+void launch_clean_start(const Params& P, cudaStream_t s) {
+  k_clean_start<<<blocks_for((int64_t)P.n_inst * P.n_rows * 32, kBlock), kBlock, 0, s>>>(P);
+}
+
+void launch_start_fill(const Params& P, cudaStream_t s) {
+  k_start_fill<<<blocks_for((int64_t)P.n_inst * P.n_rows * 32, kBlock), kBlock, 0, s>>>(P);
+}
+
+void launch_export_links(const Params& P, const tpct_debug_out& d, cudaStream_t s) {
+  k_export_links<<<blocks_for(P.n, kBlock), kBlock, 0, s>>>(P, d);
+}
+
+}  // namespace tpct

@@ -1,0 +1,142 @@
+// Internal declarations of the GB300 sector tracker (not part of the ABI).
+//
+// Index spaces
+//   input id  c   position in the caller's cluster arrays
+//   sorted    p   position after the grid scatter: instance-major, row-major,
+//                 bin-major inside a row; every per-cluster work array
+//                 (links, flags, weights) lives in this space
+//   row key   ir  instance * n_rows + row
+//   tracklet  t   one per start hit, in (instance, row, start-hit id) order
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "tpct.h"
+
+namespace tpct {
+
+constexpr int kMaxRows = 256;
+constexpr int kRankBits = 20;                  // selection weight = nhits << 20 | (2^20-1-rank)
+constexpr uint32_t kRankMask = (1u << kRankBits) - 1u;
+constexpr double kKbPerTesla = 0.299792458e-2; // curvature [1/cm] per (q/pT [c/GeV]) per tesla
+
+enum StopReason { kStopEnd = 0, kStopProp = 1, kStopEdge = 2, kStopMiss = 3, kStopSinphi = 4 };
+enum DevStatus : uint32_t { kDevCapacity = 1u, kDevTimeout = 2u, kDevTrackletCap = 4u };
+
+// Per-row grid: bins cover [y0, y0 + ny/idy) x [z0, z0 + nz/idz); indices
+// outside are clamped to the border bins, so every cluster has a bin and the
+// bin index is monotonic in y and in z.
+struct RowGrid {
+  float y0, z0, idy, idz;
+  int32_t bin_base;   // first entry of this row in bin_start
+  int16_t ny, nz;
+};
+
+// Everything a kernel needs, passed by value (uniform, lives in the constant bank).
+struct Params {
+  // sizes
+  int32_t n_rows, n_inst, n, tcap, nbin_cap;
+  int32_t clusters_per_bin;
+  // geometry and cuts
+  double tan_half, z_max, kb;
+  double nf_wy, nf_wz, nf_dmax, s_max, edge_margin, search_k, chi2_max, f_shared;
+  double sig_readout, sig_cathode, c_s, c_t, c_qpt, c_yz_refit, c_qpt_refit;
+  int32_t max_miss, n_min, n_refit;
+  // input (device, caller-owned)
+  const float *x, *y, *z;
+  const uint8_t* row;
+  const int64_t* inst_off;
+  // workspace
+  const double* rx;            // [n_rows] row x (double)
+  const float* rxf;            // [n_rows] row x (float)
+  uint32_t* status;            // sticky device status bits
+  int32_t* row_count;          // [n_inst*n_rows + 1]
+  int32_t* row_start;          // [n_inst*n_rows + 1]
+  uint32_t* row_ext;           // [n_inst*n_rows*4] ordered-int min y, max y, min z, max z
+  RowGrid* grid;               // [n_inst*n_rows]
+  int32_t* c_bin;              // [n] bin of each input cluster
+  int32_t* c_ir;               // [n] row key of each input cluster
+  int32_t* bin_count;          // [nbin_cap + 1]
+  int32_t* bin_start;          // [nbin_cap + 1]
+  float *sy, *sz;              // [n] sorted positions
+  int32_t* sid;                // [n] input id of each sorted position
+  uint8_t* srow;               // [n] row of each sorted position
+  int32_t *up, *down, *upc;    // [n]
+  uint8_t* sflag;              // [n] start-hit flag
+  int32_t* row_tl_count;       // [n_inst*n_rows + 1]
+  int32_t* row_tl_base;        // [n_inst*n_rows + 1]; [n_inst*n_rows] = tracklet count
+  int32_t* tl_start;           // [tcap]
+  int32_t* tl_ir;              // [tcap]
+  int32_t* tl_hits;            // [n_rows * tcap], slot-major
+  int32_t* tl_nhits;           // [tcap]
+  int32_t* tl_rowref;          // [tcap]
+  double* tl_par;              // [5 * tcap]
+  uint32_t* W;                 // [n]
+  uint64_t* tl_sel;            // [tcap + 1]  (accepted << 32 | owned) then its exclusive scan
+  uint64_t* tl_sel_scan;       // [tcap + 1]
+  int32_t* trk_tl;             // [cap_tracks] tracklet of each output track
+  int32_t* trk_pos;            // [cap_ids]    sorted position of each output cluster
+  uint64_t* scan_tmp;          // block sums of the scans
+  // output (device, caller-owned)
+  tpct_tracks_out out;
+};
+
+// ------------------------------------------------------------------ precision
+// MODE 0: FP32; 1: mixed (float transport / neighbour / search arithmetic,
+// double state, covariance, update and refit); 2: FP64.
+template <int MODE> struct Prec;
+template <> struct Prec<0> { using S = float;  using E = float;  using C = float;  using R = float;  };
+template <> struct Prec<1> { using S = double; using E = float;  using C = double; using R = double; };
+template <> struct Prec<2> { using S = double; using E = double; using C = double; using R = double; };
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ uint32_t float_order_key(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float float_from_order_key(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+// Cluster resolution at measured z: linear in drift length clamp(z_max - |z|, 0, z_max).
+template <class T>
+__device__ __forceinline__ T sigma_of(const Params& P, T z) {
+  T d = (T)P.z_max - fabs(z);
+  d = d < (T)0 ? (T)0 : d;
+  d = d > (T)P.z_max ? (T)P.z_max : d;
+  return (T)P.sig_readout + ((T)P.sig_cathode - (T)P.sig_readout) * d / (T)P.z_max;
+}
+
+// Bin of (y, z) in a row grid (monotonic, clamped).
+__device__ __forceinline__ int bin_y(const RowGrid& g, float y) {
+  float t = (y - g.y0) * g.idy;
+  t = fminf(fmaxf(t, 0.0f), (float)(g.ny - 1));
+  return (int)t;
+}
+__device__ __forceinline__ int bin_z(const RowGrid& g, float z) {
+  float t = (z - g.z0) * g.idz;
+  t = fminf(fmaxf(t, 0.0f), (float)(g.nz - 1));
+  return (int)t;
+}
+
+// Launch wrappers (defined in the .cu files).
+void launch_rows(const Params& P, cudaStream_t s);
+void launch_grid_dims(const Params& P, cudaStream_t s);
+void launch_bin_count(const Params& P, cudaStream_t s);
+void launch_scatter(const Params& P, cudaStream_t s);
+void launch_scan_i32(const int32_t* in, int32_t* out, int64_t m, uint64_t* tmp, cudaStream_t s);
+void launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t m, uint64_t* tmp, cudaStream_t s);
+int64_t scan_tmp_elems(int64_t m);
+void launch_neighbours(const Params& P, int mode, cudaStream_t s);
+void launch_clean_start(const Params& P, cudaStream_t s);
+void launch_start_fill(const Params& P, cudaStream_t s);
+void launch_tracklets(const Params& P, int mode, int block, cudaStream_t s);
+void launch_weights(const Params& P, cudaStream_t s);
+void launch_own(const Params& P, cudaStream_t s);
+void launch_emit(const Params& P, cudaStream_t s);
+void launch_refit(const Params& P, int mode, int block, cudaStream_t s);
+void launch_export_links(const Params& P, const tpct_debug_out& d, cudaStream_t s);
+void launch_export_tracklets(const Params& P, const tpct_debug_out& d, cudaStream_t s);
+int kernels_per_track(void);
+
+}  // namespace tpct

@@ -1,0 +1,140 @@
+// Helix transport in x and Kalman-filter arithmetic shared by the tracklet
+// and refit kernels of the CUDA path.
+//
+// State p = (y, z, sin phi, tan lambda, q/pT) at a pad-row x; covariance in
+// packed lower-triangular order 00,10,11,20,21,22,30,31,32,33,40,41,42,43,44.
+#pragma once
+#include "tpct_internal.cuh"
+
+namespace tpct {
+
+// g(h) = asin(h)/h and g'(h).  Near 0 from the Taylor series of asin
+// (coefficients (2n)! / (4^n (n!)^2 (2n+1))); float uses it up to |h| = 0.25,
+// double up to |h| = 0.01 (truncation below 1e-9 and 1e-25 respectively).
+template <class E>
+__device__ __forceinline__ void asin_ratio(E h, E& g, E& gp) {
+  const E u = h * h;
+  const E lim = sizeof(E) == 4 ? (E)0.0625 : (E)1e-4;
+  if (u < lim) {
+    g = (E)1 + u * ((E)(1.0 / 6.0) + u * ((E)(3.0 / 40.0) + u * ((E)(5.0 / 112.0) +
+        u * ((E)(35.0 / 1152.0) + u * (E)(63.0 / 2816.0)))));
+    gp = h * ((E)(1.0 / 3.0) + u * ((E)(3.0 / 10.0) + u * ((E)(15.0 / 56.0) +
+         u * ((E)(35.0 / 144.0) + u * (E)(315.0 / 1408.0)))));
+  } else {
+    const E ih = (E)1 / h;
+    g = asin(h) * ih;
+    gp = ((E)1 / sqrt((E)1 - u) - g) * ih;
+  }
+}
+
+// Increments and Jacobian of one exact helix step of length dx in x.
+template <class E>
+struct Step {
+  E dy, dz, ds;                 // increments of y, z, sin phi
+  E j_ys, j_yq;                 // d y1 / d sin phi0, d y1 / d q/pT
+  E j_zs, j_zt, j_zq;           // d z1 / d sin phi0, d tan l, d q/pT
+  E j_sq;                       // d sin phi1 / d q/pT
+};
+
+// s1 = s0 + rho dx with rho = -kb q/pT; the chord has the slope of the mean
+// direction, (s0 + s1) / (c0 + c1); its signed length L (sign of dx) spans
+// an arc L g(rho L / 2); z advances by tan(lambda) times the arc.
+template <class E>
+__device__ __forceinline__ bool helix_step(E s0, E tl, E qpt, E dx, E kb, E smax, Step<E>& st) {
+  const E rho = -kb * qpt;
+  const E ds = rho * dx;
+  const E s1 = s0 + ds;
+  if (!(fabs(s0) < smax && fabs(s1) < smax)) return false;
+  const E c0 = sqrt((E)1 - s0 * s0), c1 = sqrt((E)1 - s1 * s1);
+  const E ib = (E)1 / (c0 + c1);
+  const E slope = (s0 + s1) * ib;
+  const E dy = dx * slope;
+  const E len = copysign(sqrt(dx * dx + dy * dy), dx);
+  const E h = (E)0.5 * rho * len;
+  E g, gp;
+  asin_ratio<E>(h, g, gp);
+  const E arc = len * g;
+  st.dy = dy;
+  st.dz = tl * arc;
+  st.ds = ds;
+  const E q0 = s0 / c0, q1 = s1 / c1;
+  st.j_ys = dx * ((E)2 + slope * (q0 + q1)) * ib;
+  st.j_yq = -kb * dx * dx * ((E)1 + slope * q1) * ib;
+  const E darc_ddy = len != (E)0 ? (g + h * gp) * dy / len : (E)0;
+  st.j_zs = tl * darc_ddy * st.j_ys;
+  st.j_zq = tl * (darc_ddy * st.j_yq - kb * (E)0.5 * len * len * gp);
+  st.j_zt = arc;
+  st.j_sq = -kb * dx;
+  return true;
+}
+
+// C <- F C F^T for F = I + a e02 + b e04 + c e12 + d e13 + e e14 + f e24.
+template <class C>
+__device__ __forceinline__ void cov_transport(C* m, C a, C b, C c, C d, C e, C f) {
+  const C m00 = m[0], m10 = m[1], m11 = m[2], m20 = m[3], m21 = m[4], m22 = m[5];
+  const C m30 = m[6], m31 = m[7], m32 = m[8], m33 = m[9];
+  const C m40 = m[10], m41 = m[11], m42 = m[12], m43 = m[13], m44 = m[14];
+  // rows of G = F C that differ from C
+  const C g00 = m00 + a * m20 + b * m40, g02 = m20 + a * m22 + b * m42, g04 = m40 + a * m42 + b * m44;
+  const C g10 = m10 + c * m20 + d * m30 + e * m40, g11 = m11 + c * m21 + d * m31 + e * m41;
+  const C g12 = m21 + c * m22 + d * m32 + e * m42, g13 = m31 + c * m32 + d * m33 + e * m43;
+  const C g14 = m41 + c * m42 + d * m43 + e * m44;
+  const C g20 = m20 + f * m40, g21 = m21 + f * m41, g22 = m22 + f * m42;
+  const C g23 = m32 + f * m43, g24 = m42 + f * m44;
+  // G F^T, lower triangle
+  m[0] = g00 + a * g02 + b * g04;
+  m[1] = g10 + a * g12 + b * g14;
+  m[2] = g11 + c * g12 + d * g13 + e * g14;
+  m[3] = g20 + a * g22 + b * g24;
+  m[4] = g21 + c * g22 + d * g23 + e * g24;
+  m[5] = g22 + f * g24;
+  m[6] = m30 + a * m32 + b * m43;
+  m[7] = m31 + c * m32 + d * m33 + e * m43;
+  m[8] = m32 + f * m43;
+  m[10] = m40 + a * m42 + b * m44;
+  m[11] = m41 + c * m42 + d * m43 + e * m44;
+  m[12] = m42 + f * m44;
+}
+
+template <class C, class E>
+__device__ __forceinline__ void cov_transport(C* m, const Step<E>& st) {
+  cov_transport<C>(m, (C)st.j_ys, (C)st.j_yq, (C)st.j_zs, (C)st.j_zt, (C)st.j_zq, (C)st.j_sq);
+}
+
+// chi2 of residual (r0, r1) against S = C[yz] + diag(vy, vz)
+template <class C>
+__device__ __forceinline__ C kf_chi2(const C* m, C r0, C r1, C vy, C vz) {
+  const C s00 = m[0] + vy, s01 = m[1], s11 = m[2] + vz;
+  return (r0 * (s11 * r0 - s01 * r1) + r1 * (s00 * r1 - s01 * r0)) / (s00 * s11 - s01 * s01);
+}
+
+// Gain K = C H^T S^-1; p += K r; C -= K H C (lower triangle).
+template <class C, class S>
+__device__ __forceinline__ void kf_update(S* p, C* m, C r0, C r1, C vy, C vz) {
+  const C s00 = m[0] + vy, s01 = m[1], s11 = m[2] + vz;
+  const C idet = (C)1 / (s00 * s11 - s01 * s01);
+  const C i00 = s11 * idet, i01 = -s01 * idet, i11 = s00 * idet;
+  const C c0[5] = {m[0], m[1], m[3], m[6], m[10]};
+  const C c1[5] = {m[1], m[2], m[4], m[7], m[11]};
+  C k0[5], k1[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    k0[i] = c0[i] * i00 + c1[i] * i01;
+    k1[i] = c0[i] * i01 + c1[i] * i11;
+    p[i] += (S)(k0[i] * r0 + k1[i] * r1);
+  }
+  int idx = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] -= k0[i] * c0[j] + k1[i] * c1[j];
+}
+
+template <class C>
+__device__ __forceinline__ void cov_diag(C* m, C vy, C vz, C vs, C vt, C vq) {
+#pragma unroll
+  for (int i = 0; i < 15; ++i) m[i] = (C)0;
+  m[0] = vy; m[2] = vz; m[5] = vs; m[9] = vt; m[14] = vq;
+}
+
+}  // namespace tpct

@@ -1,0 +1,68 @@
+"""The C ABI library loads and exports every declared entry point; host-side
+argument checks work without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2502_09138_gb300.build as b
+    b.build()
+    import paper_2502_09138_gb300.binding as B
+    return B.load()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(tpct_\w+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 10
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_create_and_workspace_without_gpu(lib):
+    import paper_2502_09138_gb300 as G
+    trk = G.Tracker(device="cpu")
+    nb = trk.workspace_bytes(1_400_000, 36)
+    assert 100e6 < nb < 2e9
+    assert trk.workspace_bytes(0, 1) > 0
+    assert trk.workspace_bytes(-1, 1) == 0
+
+
+def test_invalid_arguments(lib):
+    import paper_2502_09138_gb300 as G
+    B = G.B
+    c = G.default_cuts()
+    rx = np.array([1.0, 2.0, 1.5])      # not ascending
+    g = B.Geometry(3, rx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0.17, 250.0)
+    h = ctypes.c_void_p()
+    assert lib.tpct_create(ctypes.byref(g), 0.5, ctypes.byref(c), 1, ctypes.byref(h)) == B.TPCT_E_INVALID
+    bad = G.default_cuts(s_max=1.5)
+    rx = np.arange(10, dtype=np.float64) + 80
+    g = B.Geometry(10, rx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0.17, 250.0)
+    assert lib.tpct_create(ctypes.byref(g), 0.5, ctypes.byref(bad), 1, ctypes.byref(h)) == B.TPCT_E_INVALID
+    assert lib.tpct_create(ctypes.byref(g), 0.5, ctypes.byref(c), 7, ctypes.byref(h)) == B.TPCT_E_INVALID
+    assert lib.tpct_create(ctypes.byref(g), 0.5, ctypes.byref(c), 1, ctypes.byref(h)) == B.TPCT_OK
+    # tracking without a workspace is a state error, detected on the host
+    cl = B.Clusters()
+    cl.n_instances = 1
+    out = B.TracksOut()
+    assert lib.tpct_track(h, ctypes.byref(cl), 10, ctypes.byref(out), None) == B.TPCT_E_STATE
+    assert lib.tpct_set_tuning(h, 0, 33, 0) == B.TPCT_E_INVALID
+    lib.tpct_destroy(h)
+    assert lib.tpct_status_str(B.TPCT_E_CAPACITY) == b"output capacity exceeded"
