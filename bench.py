@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Throughput of GB300 TPC sector track finding (clusters/s).
+
+Default workload: 128 Pb-Pb-like collisions of uneven multiplicity
+(b uniform in 0-15 fm, N_tracks = max(10, 9000 (1 - b/15)^2), 36 sectors
+each; about 5.5e7 clusters), tracked by the batched form (graph-captured
+launch of the whole step chain) in the mixed precision.  A step is one
+pass of all tracking steps over the whole batch.  Inputs are resident in
+HBM when the timed region starts; they are larger than L2 (~0.8 GB), so no
+L2 flush is needed between steps.
+
+Also reported: per-step-boundary times from CUDA events recorded inside the
+graph, the roofline of the dominant kernel, the plain per-collision form on
+the same batch, end-to-end throughput through host buffers, SM clocks during
+the timed region, and the CPU oracle timed on a bounded sample.
+
+--impl reference times the CPU oracle (the only reference there is) on the
+host cores.  Multi-GPU: one process per GPU (torchrun); each rank tracks its
+own batch (independent collisions, no collective); value = all clusters / the
+slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STAGES = ["grid", "neighbours", "clean_start", "tracklets", "selection", "refit"]
+# FP64 flops of one helix step (covariance transport), one chi2 test and one
+# Kalman update in the mixed precision (see the flop count in the design notes)
+FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 113, 14, 104
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--collisions", type=int, default=128)
+    ap.add_argument("--workload", default="batch", choices=["batch", "central"],
+                    help="batch: the collisions above; central: one central Pb-Pb-like event (small case)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args, rank):
+    import synth
+    if args.workload == "central":
+        return synth.generate_config(1, instance=rank)
+    return synth.generate_config(3, instance=rank, n_collisions=args.collisions,
+                                 workers=min(16, os.cpu_count() or 1))
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(ev, gpu_out, gpu_dbg, budget_s=20.0):
+    """Oracle on a bounded sample of the workload's sector instances (rank 0,
+    N = 1); also checks the CUDA result on the same sample."""
+    import oracle
+    from oracle.check import compare
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from gpu_util import slice_instances
+    rng = np.random.default_rng(12345)
+    order = rng.permutation(ev.n_instances)
+    sizes = np.diff(ev.sector_offsets)
+    # about budget_s of single-thread work at ~2.5e5 clusters/s
+    target = int(budget_s * 2.5e5)
+    take, tot = [], 0
+    for i in order:
+        take.append(int(i))
+        tot += int(sizes[i])
+        if tot >= target:
+            break
+    idx = np.sort(np.array(take))
+    sub = ev.select_instances(idx)
+    t0 = time.perf_counter()
+    ores = oracle.track_event(sub)
+    dt = time.perf_counter() - t0
+    rep = None
+    if gpu_out is not None:
+        tr, dbg = slice_instances(ev, gpu_out, gpu_dbg, idx)
+        r = compare(sub, ores, dbg, tr)
+        rep = {k: r[k] for k in ("pass", "nf_mismatch", "nf_excused", "track_mismatch", "track_excused",
+                                 "tracks_oracle", "tracks_gpu", "eff_oracle", "eff_gpu", "cov_max_rel_err")}
+        rep["param_max_rel_err"] = max(r["param_max_rel_err"])
+    return {"value": sub.n / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(idx)} of {ev.n_instances} sector instances ({sub.n} clusters), "
+                      f"single-threaded FP64, {dt:.1f} s"}, rep
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    # a bounded sample of the same workload: the first collisions of the batch
+    ncoll = max(1, min(args.collisions, 4))
+    ev = synth.generate_config(3, instance=0, n_collisions=ncoll)
+    per_step = []
+    for s in range(args.warmup + args.steps):
+        k = s % ev.n_instances
+        idx = np.arange(k, min(ev.n_instances, k + 36))
+        sub = ev.select_instances(idx)
+        t0 = time.perf_counter()
+        oracle.track_event(sub)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            per_step.append((sub.n, dt))
+    n = sum(a for a, _ in per_step)
+    t = sum(b for _, b in per_step)
+    v = n / t
+    line = {"impl": "reference", "metric": "TPC clusters/s tracked", "value": v, "unit": "clusters/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(per_step),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.collisions} collisions, b uniform 0-15 fm (36 sector instances "
+                                   "of it per step)", "collisions": args.collisions},
+            "cpu_baseline": {"value": v, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(per_step)} steps of 36 sector instances ({n} clusters)"},
+            "e2e": {"value": v, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    # generate before any CUDA call (the generator uses a spawn process pool)
+    ev = workload(args, rank)
+    import torch
+    import paper_2502_09138_gb300 as G
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cuts = G.default_cuts(sig_readout=ev.sigma.at_readout, sig_cathode=ev.sigma.at_cathode)
+    trk = G.Tracker(precision=args.precision, bz=ev.bz, cuts=cuts, device=dev)
+    trk.reserve(ev.n, ev.n_instances)
+    dc = G.DeviceClusters.from_event(ev, device=dev)
+    out = trk.make_output(ev.n, cap_tracks=ev.n // 20 + 1024, cap_ids=ev.n)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also builds the graph)
+    for _ in range(args.warmup):
+        trk.track(dc, out, batched=True)
+    torch.cuda.synchronize()
+    st = trk.device_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after warm-up")
+    dbg = trk.debug(ev.n)
+    torch.cuda.synchronize()
+    gdbg = dbg.to_host()
+    gout = out.to_host()
+
+    # per-step boundary events, re-pointed on every replay
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    for row in evs:
+        for e in row:
+            e.record(stream)
+    trk.set_stage_events(evs[0])
+    trk.track(dc, out, batched=True)      # capture with event nodes (untimed)
+    torch.cuda.synchronize()
+
+    launches0 = trk.kernel_launches()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        trk.set_stage_events(evs[k])
+        trk.track(dc, out, batched=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = trk.kernel_launches() - launches0
+    ms = t0.elapsed_time(t1) / args.steps
+    stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
+                for i, name in enumerate(STAGES)}
+    trk.set_stage_events(None)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    n_total = ev.n * world
+    value = n_total / (ms * 1e-3)
+    n_tracks = int(gout["n_tracks"])
+
+    # roofline of the dominant kernel
+    peaks = measured_peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    steps, updates, tests = (int(v) for v in gdbg["counters"][:3])
+    fp64_flops = steps * FLOPS_STEP + tests * FLOPS_TEST + updates * FLOPS_UPDATE
+    fp64_probe = None
+    roofline = None
+    if dom == "tracklets" and args.precision != "fp32":
+        blocks = 152 * 16
+        pm = G.probe_fma(True, blocks, 2048)
+        fp64_probe = 2.0 * 8 * 2048 * blocks * 256 / (pm * 1e-3) / 1e12
+        ach = fp64_flops / (stage_ms["tracklets"] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": "k_tracklets (FP64 covariance arithmetic)", "achieved": ach,
+                    "peak": fp64_probe, "unit": "TFLOP/s", "frac": ach / fp64_probe, "traffic": None,
+                    "peak_source": "FP64 FMA probe in this run (152 SMs x 2 FMA/clk nominal)",
+                    "algorithmic_flops_per_launch": fp64_flops}
+    else:
+        bytes_alg = 90.0 * ev.n
+        ach = bytes_alg / (stage_ms[dom] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peaks.get("hbm_gbs", 6800.0),
+                    "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6800.0), "traffic": None}
+
+    line = {
+        "metric": "TPC clusters/s tracked (batched, mixed FP32/FP64)", "value": value, "unit": "clusters/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": (f"{args.collisions} collisions, b uniform 0-15 fm, 36 sectors each"
+                                if args.workload == "batch" else "one central Pb-Pb-like event, 9000 tracks"),
+                   "clusters_per_rank": ev.n, "sector_instances": ev.n_instances, "precision": args.precision,
+                   "form": "batched (graph-captured step chain)", "l2": "inputs 0.8 GB > L2, no flush",
+                   "parallelism": f"replicas x{world} (independent collisions)"},
+        "tracks_per_s": n_tracks * world / (ms * 1e-3), "tracks": n_tracks,
+        "stage_ms": stage_ms, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+        "counters": {"helix_steps": steps, "kalman_updates": updates, "chi2_tests": tests},
+    }
+
+    # plain per-collision form on the same batch
+    if not args.no_plain:
+        offs = ev.sector_offsets
+        spe = ev.sectors_per_event
+        parts = []
+        for c in range(ev.n_events):
+            a, b = int(offs[c * spe]), int(offs[(c + 1) * spe])
+            so = torch.from_numpy((offs[c * spe:(c + 1) * spe + 1] - a).astype(np.int64)).to(dev)
+            parts.append(G.DeviceClusters(dc.x[a:b], dc.y[a:b], dc.z[a:b], dc.charge[a:b], dc.row[a:b], so))
+        pout = trk.make_output(max(p.n for p in parts))
+        for p in parts[:3]:
+            trk.track(p, pout)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(3, args.steps))
+        a0.record(stream)
+        for _ in range(reps):
+            for p in parts:
+                trk.track(p, pout)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        pms = a0.elapsed_time(a1) / reps
+        line["plain"] = {"value": ev.n / (pms * 1e-3), "ms_per_step": pms, "unit": "clusters/s",
+                         "form": "one tpct_track call per collision (36 instances), plain launches",
+                         "batched_speedup": pms / ms}
+
+    # end to end through host buffers
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(np.ascontiguousarray(getattr(ev, k))).pin_memory()
+                for k in ("x", "y", "z", "charge", "row")}
+        host["sector_offsets"] = torch.from_numpy(ev.sector_offsets.astype(np.int64)).pin_memory()
+        res_host = {k: torch.empty(getattr(out, k).shape, dtype=getattr(out, k).dtype).pin_memory()
+                    for k in ("counts", "n_cl", "offset", "param", "cov", "chi2", "cluster_ids")}
+        d2h = sum(int(t.numel() * t.element_size()) for k, t in res_host.items())
+        h2d = sum(int(t.numel() * t.element_size()) for t in host.values())
+        def e2e_step():
+            for k in ("x", "y", "z", "charge", "row", "sector_offsets"):
+                getattr(dc, k).copy_(host[k], non_blocking=True)
+            trk.track(dc, out, batched=True)
+            for k, t in res_host.items():
+                t.copy_(getattr(out, k), non_blocking=True)
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(5, args.steps))
+        b0.record(stream)
+        for _ in range(reps):
+            e2e_step()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ems = b0.elapsed_time(b1) / reps
+        line["e2e"] = {"value": ev.n * world / (ems * 1e-3), "unit": "clusters/s", "ms_per_step": ems,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, par = cpu_baseline(ev, gout, gdbg)
+        line["cpu_baseline"] = cb
+        line["parity_on_sample"] = par
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

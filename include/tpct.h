@@ -136,6 +136,8 @@ typedef struct {
   double* tl_param;               /* [T*5] state at the innermost hit */
   int32_t* tl_row_ref;            /* [T] row of the innermost hit */
   int32_t* tr_tracklet;           /* [K] tracklet of each output track (K <= capacity_tracklets) */
+  int64_t* counters;              /* [4] totals over tracklets: helix steps, Kalman updates,
+                                     chi2 tests, grid candidates examined (added to) */
 } tpct_debug_out;
 
 /* ---------------------------------------------------------------- context */
@@ -148,7 +150,8 @@ tpct_status tpct_create(const tpct_geometry* geometry, double bz_tesla, const tp
 void tpct_destroy(tpct_ctx* ctx);
 
 /* Tuning knobs that never change results (only speed): clusters per grid
- * bin, threads per block of the tracklet and refit kernels.  0 = default. */
+ * bin (>= 1), threads per block of the tracklet and refit kernels (a
+ * multiple of 32, at most 256).  0 = default. */
 tpct_status tpct_set_tuning(tpct_ctx* ctx, int clusters_per_bin, int tracklet_block, int refit_block);
 
 /* ---------------------------------------------------------------- workspace */
@@ -171,6 +174,14 @@ tpct_status tpct_track(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n,
 tpct_status tpct_track_batch(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n,
                              tpct_tracks_out* out, tpct_stream stream);
 
+/* Timing hooks: n_events = 7 CUDA events (cudaEvent_t) recorded on the
+ * tracking stream at the step boundaries: before step 1, after the grid
+ * (step 1), neighbours (2), cleaning and start hits (3-4), tracklets (5),
+ * selection (6) and refit (7).  Inside the batched form's graph they are
+ * event-record nodes, re-pointed to the events given here on every call.
+ * n_events = 0 disables.  The events stay owned by the caller. */
+tpct_status tpct_set_stage_events(tpct_ctx* ctx, void* const* events, int n_events);
+
 /* Copy intermediate arrays of the last tpct_track / tpct_track_batch call on
  * this context (enqueued on `stream`). */
 tpct_status tpct_debug_export(tpct_ctx* ctx, tpct_debug_out* dbg, tpct_stream stream);
@@ -180,6 +191,9 @@ tpct_status tpct_debug_export(tpct_ctx* ctx, tpct_debug_out* dbg, tpct_stream st
 tpct_status tpct_last_device_status(tpct_ctx* ctx);
 
 const char* tpct_status_str(tpct_status s);
+
+/* Text of the CUDA error behind the context's last TPCT_E_CUDA (host-owned, static). */
+const char* tpct_last_cuda_error(const tpct_ctx* ctx);
 
 /* ---------------------------------------------------------------- diagnostics */
 /* Launch count of this context's kernels so far (each kernel launch and each

@@ -115,13 +115,14 @@ class Debug:
         self.tl_param = torch.empty(max(1, cap_tracklets) * 5, dtype=torch.float64, device=device)
         self.tl_row_ref = torch.empty(max(1, cap_tracklets), **i32)
         self.tr_tracklet = torch.full((max(1, cap_tracklets),), -1, **i32)
+        self.counters = torch.zeros(4, dtype=torch.int64, device=device)
         self._n = n
 
     def as_struct(self) -> B.DebugOut:
         return B.DebugOut(_ptr(self.up), _ptr(self.down), _ptr(self.upc), _ptr(self.downc),
                           _ptr(self.weight), self.cap, _ptr(self.n_tracklets), _ptr(self.tl_start),
                           _ptr(self.tl_nhits), _ptr(self.tl_hits), _ptr(self.tl_param), _ptr(self.tl_row_ref),
-                          _ptr(self.tr_tracklet))
+                          _ptr(self.tr_tracklet), _ptr(self.counters))
 
     def to_host(self):
         n = self._n
@@ -132,7 +133,7 @@ class Debug:
                     weight=g(self.weight, n).view(np.uint32), n_tracklets=T, tl_start=g(self.tl_start, Tc),
                     tl_nhits=g(self.tl_nhits, Tc), tl_hits=g(self.tl_hits, Tc * self.n_rows).reshape(Tc, self.n_rows),
                     tl_param=g(self.tl_param, Tc * 5).reshape(Tc, 5), tl_row_ref=g(self.tl_row_ref, Tc),
-                    tr_tracklet=self.tr_tracklet.cpu().numpy())
+                    tr_tracklet=self.tr_tracklet.cpu().numpy(), counters=self.counters.cpu().numpy())
 
 
 class Tracker:
@@ -205,8 +206,18 @@ class Tracker:
         cs, os_ = clusters.as_struct(), out.as_struct()
         fn = B.load().tpct_track_batch if batched else B.load().tpct_track
         B.check(fn(self._h, ctypes.byref(cs), n, ctypes.byref(os_), ctypes.c_void_p(s.cuda_stream)),
-                "tpct_track_batch" if batched else "tpct_track")
+                "tpct_track_batch" if batched else "tpct_track", self._h)
         return out
+
+    def set_stage_events(self, events):
+        """events: 7 torch.cuda.Event (created with enable_timing) or None to disable."""
+        if events is None:
+            B.check(B.load().tpct_set_stage_events(self._h, None, 0), "tpct_set_stage_events")
+            self._stage_events = None
+            return
+        arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+        self._stage_events = (events, arr)
+        B.check(B.load().tpct_set_stage_events(self._h, arr, len(events)), "tpct_set_stage_events")
 
     def debug(self, n, cap_tracklets=None, stream=None):
         cap_tracklets = n // 3 + 1 if cap_tracklets is None else cap_tracklets

@@ -45,7 +45,8 @@ class DebugOut(ctypes.Structure):
     _fields_ = [("up", c_void_p), ("down", c_void_p), ("upc", c_void_p), ("downc", c_void_p),
                 ("weight", c_void_p), ("capacity_tracklets", c_int32), ("n_tracklets", c_void_p),
                 ("tl_start", c_void_p), ("tl_nhits", c_void_p), ("tl_hits", c_void_p),
-                ("tl_param", c_void_p), ("tl_row_ref", c_void_p), ("tr_tracklet", c_void_p)]
+                ("tl_param", c_void_p), ("tl_row_ref", c_void_p), ("tr_tracklet", c_void_p),
+                ("counters", c_void_p)]
 
 
 EXPORTS = {
@@ -59,9 +60,11 @@ EXPORTS = {
     "tpct_track": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut), c_void_p]),
     "tpct_track_batch": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut),
                                  c_void_p]),
+    "tpct_set_stage_events": (c_int, [c_void_p, ctypes.POINTER(c_void_p), c_int]),
     "tpct_debug_export": (c_int, [c_void_p, ctypes.POINTER(DebugOut), c_void_p]),
     "tpct_last_device_status": (c_int, [c_void_p]),
     "tpct_status_str": (ctypes.c_char_p, [c_int]),
+    "tpct_last_cuda_error": (ctypes.c_char_p, [c_void_p]),
     "tpct_kernel_launches": (c_int64, [c_void_p]),
     "tpct_probe_fma": (c_int, [c_int, c_int, c_int, c_void_p, ctypes.POINTER(ctypes.c_float)]),
 }
@@ -86,12 +89,14 @@ def load():
 
 
 class TpctError(RuntimeError):
-    def __init__(self, code, where):
+    def __init__(self, code, where, ctx=None):
         self.code = code
         msg = load().tpct_status_str(code).decode()
+        if code == TPCT_E_CUDA and ctx is not None:
+            msg += ": " + load().tpct_last_cuda_error(ctx).decode()
         super().__init__(f"{where}: {msg} (status {code})")
 
 
-def check(code, where):
+def check(code, where, ctx=None):
     if code != TPCT_OK:
-        raise TpctError(code, where)
+        raise TpctError(code, where, ctx)

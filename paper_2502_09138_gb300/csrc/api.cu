@@ -23,10 +23,17 @@ struct tpct_ctx {
   bool have_last = false;
   cudaStream_t last_stream = nullptr;
   int64_t launches = 0;
+  // step-boundary events (caller-owned)
+  cudaEvent_t stage_ev[kStageEvents] = {};
+  bool stage_on = false;
   // graph cache of the batched form
   cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;   // kept alive: its nodes address the exec's event nodes
   Params gparams{};
+  bool gstage_on = false;
+  cudaGraphNode_t gev_nodes[kStageEvents] = {};
   int gkernels = 0;
+  cudaError_t last_err = cudaSuccess;
 };
 
 namespace {
@@ -91,6 +98,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   q.tl_par = (double*)take(8 * 5 * (size_t)pl.tcap);
   q.tl_sel = (uint64_t*)take(8 * (pl.tcap + 1));
   q.tl_sel_scan = (uint64_t*)take(8 * (pl.tcap + 1));
+  q.tl_cnt = (int32_t*)take(4 * 3 * (size_t)pl.tcap);
   q.trk_tl = (int32_t*)take(4 * pl.tcap);
   q.trk_pos = (int32_t*)take(4 * n);
   q.scan_tmp = (uint64_t*)take(8 * scan_tmp);
@@ -104,7 +112,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
     P->up = q.up; P->down = q.down; P->upc = q.upc; P->sflag = q.sflag; P->W = q.W;
     P->tl_start = q.tl_start; P->tl_ir = q.tl_ir; P->tl_nhits = q.tl_nhits; P->tl_rowref = q.tl_rowref;
     P->tl_hits = q.tl_hits; P->tl_par = q.tl_par; P->tl_sel = q.tl_sel; P->tl_sel_scan = q.tl_sel_scan;
-    P->trk_tl = q.trk_tl; P->trk_pos = q.trk_pos; P->scan_tmp = q.scan_tmp;
+    P->tl_cnt = q.tl_cnt; P->trk_tl = q.trk_tl; P->trk_pos = q.trk_pos; P->scan_tmp = q.scan_tmp;
   }
   return off;
 }
@@ -117,6 +125,18 @@ __global__ void k_set_tables_v(double* rx, float* rxf, int n_rows, const RowTabl
     rx[i] = tab.x[i];
     rxf[i] = (float)tab.x[i];
   }
+}
+
+void drop_graph(tpct_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->gexec = nullptr;
+  ctx->graph = nullptr;
+}
+
+tpct_status fail_cuda(tpct_ctx* ctx, cudaError_t e) {
+  if (ctx) ctx->last_err = e;
+  return e == cudaSuccess ? TPCT_OK : TPCT_E_CUDA;
 }
 
 bool valid_cuts(const tpct_cuts& c) {
@@ -159,22 +179,29 @@ tpct_status make_params(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const
   p.edge_margin = c.edge_margin; p.search_k = c.search_k; p.chi2_max = c.chi2_max;
   p.f_shared = c.f_shared; p.sig_readout = c.sig_readout; p.sig_cathode = c.sig_cathode;
   p.c_s = c.c_s; p.c_t = c.c_t; p.c_qpt = c.c_qpt; p.c_yz_refit = c.c_yz_refit;
-  p.c_qpt_refit = c.c_qpt_refit; p.max_miss = c.max_miss; p.n_min = c.n_min; p.n_refit = c.n_refit;
+  p.c_qpt_refit = c.c_qpt_refit; p.sig_slope = (c.sig_cathode - c.sig_readout) / ctx->z_max;
+  p.max_miss = c.max_miss; p.n_min = c.n_min; p.n_refit = c.n_refit;
   p.x = cl->x; p.y = cl->y; p.z = cl->z; p.row = cl->row; p.inst_off = cl->sector_offsets;
   p.out = *out;
   *P = p;
   return TPCT_OK;
 }
 
-// The step sequence; returns the number of kernels launched.
+// The step sequence; returns the number of kernels launched.  With stage
+// events on, an event is recorded at every step boundary.
 int enqueue_track(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
   int k = 0;
   const int mode = (int)ctx->prec;
+  // External records: inside a stream capture they become event-record nodes.
+  auto mark = [&](int b) {
+    if (ctx->stage_on) cudaEventRecordWithFlags(ctx->stage_ev[b], s, cudaEventRecordExternal);
+  };
   RowTable tab;
   for (int i = 0; i < ctx->n_rows; ++i) tab.x[i] = ctx->row_x[i];
-  k_set_tables_v<<<1, 256, 0, s>>>(const_cast<double*>(P.rx), const_cast<float*>(P.rxf), ctx->n_rows, tab); ++k;
   const int64_t nr = (int64_t)P.n_inst * P.n_rows;
   const int scan_k = 3;
+  mark(0);
+  k_set_tables_v<<<1, 256, 0, s>>>(const_cast<double*>(P.rx), const_cast<float*>(P.rxf), ctx->n_rows, tab); ++k;
   launch_rows(P, s); k += 2;
   launch_scan_i32(P.row_count, P.row_start, nr, P.scan_tmp, s); k += scan_k;
   launch_grid_dims(P, s); ++k;
@@ -183,16 +210,22 @@ int enqueue_track(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
   launch_scan_i32(P.bin_count, P.bin_start, P.nbin_cap, P.scan_tmp, s); k += scan_k;
   cudaMemsetAsync(P.bin_count, 0, sizeof(int32_t) * (size_t)(P.nbin_cap + 1), s);
   launch_scatter(P, s); ++k;
+  mark(1);
   launch_neighbours(P, mode, s); ++k;
+  mark(2);
   launch_clean_start(P, s); ++k;
   launch_scan_i32(P.row_tl_count, P.row_tl_base, nr, P.scan_tmp, s); k += scan_k;
   launch_start_fill(P, s); ++k;
+  mark(3);
   launch_tracklets(P, mode, ctx->tracklet_block, s); ++k;
+  mark(4);
   launch_weights(P, s); ++k;
   launch_own(P, s); ++k;
   launch_scan_u64(P.tl_sel, P.tl_sel_scan, P.tcap, P.scan_tmp, s); k += scan_k;
   launch_emit(P, s); ++k;
+  mark(5);
   launch_refit(P, mode, ctx->refit_block, s); ++k;
+  mark(6);
   return k;
 }
 
@@ -230,18 +263,18 @@ tpct_status tpct_create(const tpct_geometry* g, double bz, const tpct_cuts* cuts
 
 void tpct_destroy(tpct_ctx* ctx) {
   if (!ctx) return;
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  drop_graph(ctx);
   delete ctx;
 }
 
 tpct_status tpct_set_tuning(tpct_ctx* ctx, int cpb, int tl_block, int rf_block) {
   if (!ctx || cpb < 0 || tl_block < 0 || rf_block < 0) return TPCT_E_INVALID;
-  if (tl_block && (tl_block % 32 || tl_block > 1024)) return TPCT_E_INVALID;
-  if (rf_block && (rf_block % 32 || rf_block > 1024)) return TPCT_E_INVALID;
+  if (tl_block && (tl_block % 32 || tl_block > kMaxBlock)) return TPCT_E_INVALID;
+  if (rf_block && (rf_block % 32 || rf_block > kMaxBlock)) return TPCT_E_INVALID;
   ctx->clusters_per_bin = cpb ? cpb : 2;
   ctx->tracklet_block = tl_block ? tl_block : 128;
   ctx->refit_block = rf_block ? rf_block : 128;
-  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+  drop_graph(ctx);
   return TPCT_OK;
 }
 
@@ -262,7 +295,7 @@ tpct_status tpct_set_workspace(tpct_ctx* ctx, void* ptr, size_t bytes, int64_t m
   ctx->plan_n = max_clusters;
   ctx->plan_inst = max_instances;
   ctx->have_last = false;
-  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+  drop_graph(ctx);
   Params p{};
   carve(ctx->ws, make_plan(ctx->n_rows, max_clusters, max_instances, 1), ctx->n_rows, &p);
   if (cudaMemset(p.status, 0, sizeof(uint32_t) * 4) != cudaSuccess) return TPCT_E_CUDA;
@@ -279,7 +312,7 @@ tpct_status tpct_track(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, tpct_t
   ctx->last = P;
   ctx->have_last = true;
   ctx->last_stream = s;
-  return check_cuda(cudaGetLastError());
+  return fail_cuda(ctx, cudaGetLastError());
 }
 
 tpct_status tpct_track_batch(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, tpct_tracks_out* out,
@@ -288,29 +321,66 @@ tpct_status tpct_track_batch(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, 
   tpct_status st = make_params(ctx, cl, n, out, &P);
   if (st != TPCT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  if (!ctx->gexec || std::memcmp(&ctx->gparams, &P, sizeof(Params)) != 0) {
-    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+  if (!ctx->gexec || ctx->gstage_on != ctx->stage_on || std::memcmp(&ctx->gparams, &P, sizeof(Params)) != 0) {
+    drop_graph(ctx);
     cudaStream_t cap;
-    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return TPCT_E_CUDA;
-    cudaGraph_t graph;
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       ctx->gkernels = enqueue_track(ctx, P, cap);
       e = cudaStreamEndCapture(cap, &graph);
     }
-    if (e == cudaSuccess) {
-      e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
-      cudaGraphDestroy(graph);
+    for (int b = 0; b < kStageEvents; ++b) ctx->gev_nodes[b] = nullptr;
+    if (e == cudaSuccess && ctx->stage_on) {
+      // the event-record nodes in boundary order (matched by event handle)
+      size_t nn = 0;
+      e = cudaGraphGetNodes(graph, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (e == cudaSuccess) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+      for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess) continue;
+        for (int b = 0; b < kStageEvents; ++b)
+          if (ev == ctx->stage_ev[b]) ctx->gev_nodes[b] = nodes[i];
+      }
     }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
     cudaStreamDestroy(cap);
-    if (e != cudaSuccess) { ctx->gexec = nullptr; return TPCT_E_CUDA; }
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      ctx->gexec = nullptr;
+      return fail_cuda(ctx, e);
+    }
+    ctx->graph = graph;
     ctx->gparams = P;
+    ctx->gstage_on = ctx->stage_on;
+  } else if (ctx->stage_on) {
+    for (int b = 0; b < kStageEvents; ++b) {
+      if (!ctx->gev_nodes[b]) continue;
+      cudaError_t e = cudaGraphExecEventRecordNodeSetEvent(ctx->gexec, ctx->gev_nodes[b], ctx->stage_ev[b]);
+      if (e != cudaSuccess) return fail_cuda(ctx, e);
+    }
   }
-  if (cudaGraphLaunch(ctx->gexec, s) != cudaSuccess) return TPCT_E_CUDA;
+  cudaError_t le = cudaGraphLaunch(ctx->gexec, s);
+  if (le != cudaSuccess) return fail_cuda(ctx, le);
   ctx->launches += ctx->gkernels;
   ctx->last = P;
   ctx->have_last = true;
   ctx->last_stream = s;
+  return TPCT_OK;
+}
+
+tpct_status tpct_set_stage_events(tpct_ctx* ctx, void* const* events, int n_events) {
+  if (!ctx || (n_events != 0 && n_events != kStageEvents) || (n_events && !events)) return TPCT_E_INVALID;
+  for (int b = 0; b < kStageEvents; ++b) {
+    ctx->stage_ev[b] = n_events ? (cudaEvent_t)events[b] : nullptr;
+    if (n_events && !events[b]) return TPCT_E_INVALID;
+  }
+  ctx->stage_on = n_events != 0;
   return TPCT_OK;
 }
 
@@ -352,6 +422,10 @@ const char* tpct_status_str(tpct_status s) {
 }
 
 int64_t tpct_kernel_launches(const tpct_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+const char* tpct_last_cuda_error(const tpct_ctx* ctx) {
+  return ctx ? cudaGetErrorString(ctx->last_err) : "no context";
+}
 
 }  // extern "C"
 

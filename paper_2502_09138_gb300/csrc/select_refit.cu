@@ -98,7 +98,7 @@ __global__ void k_emit(const __grid_constant__ Params P) {
 // reference trajectory), and filters the deviation from it with a diffuse
 // prior; reference + deviation at the innermost cluster is the next estimate.
 template <int MODE>
-__global__ void __launch_bounds__(128) k_refit(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Params P) {
   using R = typename Prec<MODE>::R;
   const tpct_tracks_out& O = P.out;
   const uint64_t total = P.tl_sel_scan[P.tcap];
@@ -140,8 +140,7 @@ __global__ void __launch_bounds__(128) k_refit(const __grid_constant__ Params P)
         const R sg = sigma_of<R>(P, (R)P.sz[pj]);
         const R v = sg * sg;
         const R r0 = ((R)P.sy[pj] - ref[0]) - d[0], r1 = ((R)P.sz[pj] - ref[1]) - d[1];
-        chi2 += kf_chi2<R>(m, r0, r1, v, v);
-        kf_update<R, R>(d, m, r0, r1, v, v);
+        chi2 += kf_chi2_update<R, R>(d, m, r0, r1, v);
       }
       if (status) break;
 #pragma unroll
@@ -167,6 +166,17 @@ __global__ void k_export_tracklets(const __grid_constant__ Params P, tpct_debug_
     const int n_trk = min(min((int)(P.tl_sel_scan[P.tcap] >> 32), P.out.capacity_tracks), D.capacity_tracklets);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_trk; k += gridDim.x * blockDim.x)
       D.tr_tracklet[k] = P.trk_tl[k];
+  }
+  if (D.counters) {
+    long long c0 = 0, c1 = 0, c2 = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tl; t += gridDim.x * blockDim.x) {
+      c0 += P.tl_cnt[t];
+      c1 += P.tl_cnt[(int64_t)P.tcap + t];
+      c2 += P.tl_cnt[2 * (int64_t)P.tcap + t];
+    }
+    atomicAdd((unsigned long long*)&D.counters[0], (unsigned long long)c0);
+    atomicAdd((unsigned long long*)&D.counters[1], (unsigned long long)c1);
+    atomicAdd((unsigned long long*)&D.counters[2], (unsigned long long)c2);
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < lim; t += gridDim.x * blockDim.x) {
     const int nh = P.tl_nhits[t];
@@ -205,7 +215,7 @@ void launch_emit(const Params& P, cudaStream_t s) {
   k_emit<<<blocks_for(P.tcap, kBlock), kBlock, 0, s>>>(P);
 }
 void launch_refit(const Params& P, int mode, int block, cudaStream_t s) {
-  if (block <= 0) block = 128;
+  if (block <= 0 || block > kMaxBlock) block = 128;
   // tracks <= tracklets <= tcap; the kernel reads the count on the device
   const int blocks = blocks_for(P.tcap / 4 + 1, block);
   if (mode == 0) k_refit<0><<<blocks, block, 0, s>>>(P);

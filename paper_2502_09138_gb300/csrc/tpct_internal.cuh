@@ -17,6 +17,8 @@ namespace tpct {
 constexpr int kMaxRows = 256;
 constexpr int kRankBits = 20;                  // selection weight = nhits << 20 | (2^20-1-rank)
 constexpr uint32_t kRankMask = (1u << kRankBits) - 1u;
+constexpr int kStageEvents = 7;               // step boundaries timed by tpct_set_stage_events
+constexpr int kMaxBlock = 256;                 // largest tracklet / refit block
 constexpr double kKbPerTesla = 0.299792458e-2; // curvature [1/cm] per (q/pT [c/GeV]) per tesla
 
 enum StopReason { kStopEnd = 0, kStopProp = 1, kStopEdge = 2, kStopMiss = 3, kStopSinphi = 4 };
@@ -40,6 +42,7 @@ struct Params {
   double tan_half, z_max, kb;
   double nf_wy, nf_wz, nf_dmax, s_max, edge_margin, search_k, chi2_max, f_shared;
   double sig_readout, sig_cathode, c_s, c_t, c_qpt, c_yz_refit, c_qpt_refit;
+  double sig_slope;            // (sig_cathode - sig_readout) / z_max
   int32_t max_miss, n_min, n_refit;
   // input (device, caller-owned)
   const float *x, *y, *z;
@@ -73,6 +76,7 @@ struct Params {
   uint32_t* W;                 // [n]
   uint64_t* tl_sel;            // [tcap + 1]  (accepted << 32 | owned) then its exclusive scan
   uint64_t* tl_sel_scan;       // [tcap + 1]
+  int32_t* tl_cnt;             // [3 * tcap] helix steps, updates, chi2 tests of each tracklet
   int32_t* trk_tl;             // [cap_tracks] tracklet of each output track
   int32_t* trk_pos;            // [cap_ids]    sorted position of each output cluster
   uint64_t* scan_tmp;          // block sums of the scans
@@ -104,7 +108,7 @@ __device__ __forceinline__ T sigma_of(const Params& P, T z) {
   T d = (T)P.z_max - fabs(z);
   d = d < (T)0 ? (T)0 : d;
   d = d > (T)P.z_max ? (T)P.z_max : d;
-  return (T)P.sig_readout + ((T)P.sig_cathode - (T)P.sig_readout) * d / (T)P.z_max;
+  return (T)P.sig_readout + (T)P.sig_slope * d;
 }
 
 // Bin of (y, z) in a row grid (monotonic, clamped).

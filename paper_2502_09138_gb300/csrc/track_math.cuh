@@ -110,9 +110,7 @@ __device__ __forceinline__ C kf_chi2(const C* m, C r0, C r1, C vy, C vz) {
 
 // Gain K = C H^T S^-1; p += K r; C -= K H C (lower triangle).
 template <class C, class S>
-__device__ __forceinline__ void kf_update(S* p, C* m, C r0, C r1, C vy, C vz) {
-  const C s00 = m[0] + vy, s01 = m[1], s11 = m[2] + vz;
-  const C idet = (C)1 / (s00 * s11 - s01 * s01);
+__device__ __forceinline__ void kf_update_inv(S* p, C* m, C r0, C r1, C s00, C s01, C s11, C idet) {
   const C i00 = s11 * idet, i01 = -s01 * idet, i11 = s00 * idet;
   const C c0[5] = {m[0], m[1], m[3], m[6], m[10]};
   const C c1[5] = {m[1], m[2], m[4], m[7], m[11]};
@@ -128,6 +126,33 @@ __device__ __forceinline__ void kf_update(S* p, C* m, C r0, C r1, C vy, C vz) {
   for (int i = 0; i < 5; ++i)
 #pragma unroll
     for (int j = 0; j <= i; ++j, ++idx) m[idx] -= k0[i] * c0[j] + k1[i] * c1[j];
+}
+
+template <class C, class S>
+__device__ __forceinline__ void kf_update(S* p, C* m, C r0, C r1, C vy, C vz) {
+  const C s00 = m[0] + vy, s01 = m[1], s11 = m[2] + vz;
+  kf_update_inv<C, S>(p, m, r0, r1, s00, s01, s11, (C)1 / (s00 * s11 - s01 * s01));
+}
+
+// Update that also returns the chi2 of the residual (one reciprocal).
+template <class C, class S>
+__device__ __forceinline__ C kf_chi2_update(S* p, C* m, C r0, C r1, C v) {
+  const C s00 = m[0] + v, s01 = m[1], s11 = m[2] + v;
+  const C idet = (C)1 / (s00 * s11 - s01 * s01);
+  const C chi2 = (r0 * (s11 * r0 - s01 * r1) + r1 * (s00 * r1 - s01 * r0)) * idet;
+  kf_update_inv<C, S>(p, m, r0, r1, s00, s01, s11, idet);
+  return chi2;
+}
+
+// chi2 test and, if it passes, the update, sharing one reciprocal.
+template <class C, class S>
+__device__ __forceinline__ bool kf_test_update(S* p, C* m, C r0, C r1, C v, C chi2_max) {
+  const C s00 = m[0] + v, s01 = m[1], s11 = m[2] + v;
+  const C idet = (C)1 / (s00 * s11 - s01 * s01);
+  const C chi2 = (r0 * (s11 * r0 - s01 * r1) + r1 * (s00 * r1 - s01 * r0)) * idet;
+  if (!(chi2 <= chi2_max)) return false;
+  kf_update_inv<C, S>(p, m, r0, r1, s00, s01, s11, idet);
+  return true;
 }
 
 template <class C>

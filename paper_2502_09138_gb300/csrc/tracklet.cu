@@ -47,7 +47,7 @@ __device__ int search_row(const Params& P, int ir, S py, S pz, C cyy, C czz) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__ Params P) {
   using S = typename Prec<MODE>::S;
   using E = typename Prec<MODE>::E;
   using C = typename Prec<MODE>::C;
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Param
     }
     hits[0] = p0;
     int n_up = 1;
+    int n_step = 0, n_upd = 0, n_test = 0;
 
     // ---- upward
     int prev = p0, prev_row = r0, miss = 0, top_row = r0, top_hit = p0;
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Param
     for (int r = r0 + 1; r < R; ++r) {
       Step<E> st;
       if (!helix_step<E>((E)p[2], (E)p[3], (E)p[4], (E)(P.rx[r] - P.rx[r - 1]), kb, smax, st)) break;
+      ++n_step;
       p[0] += (S)st.dy; p[1] += (S)st.dz; p[2] += (S)st.ds;
       cov_transport<C, E>(m, st);
       if (fabs(p[0]) > (S)(P.rx[r] * P.tan_half + P.edge_margin)) break;
@@ -92,8 +94,9 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Param
         const C sg = sigma_of<C>(P, (C)P.sz[cand]);
         const C v = sg * sg;
         const C ry = (C)((S)P.sy[cand] - p[0]), rz = (C)((S)P.sz[cand] - p[1]);
-        if (kf_chi2<C>(m, ry, rz, v, v) <= chi2_max) {
-          kf_update<C, S>(p, m, ry, rz, v, v);
+        ++n_test;
+        if (kf_test_update<C, S>(p, m, ry, rz, v, chi2_max)) {
+          ++n_upd;
           ok = true;
         }
       }
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Param
     for (int r = top_row - 1; r >= 0; --r) {
       Step<E> st;
       if (!helix_step<E>((E)p[2], (E)p[3], (E)p[4], (E)(P.rx[r] - P.rx[r + 1]), kb, smax, st)) break;
+      ++n_step;
       p[0] += (S)st.dy; p[1] += (S)st.dz; p[2] += (S)st.ds;
       cov_transport<C, E>(m, st);
       if (fabs(p[0]) > (S)(P.rx[r] * P.tan_half + P.edge_margin)) break;
@@ -141,8 +145,9 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Param
         const C sg = sigma_of<C>(P, (C)P.sz[cand]);
         const C v = sg * sg;
         const C ry = (C)((S)P.sy[cand] - p[0]), rz = (C)((S)P.sz[cand] - p[1]);
-        if (kf_chi2<C>(m, ry, rz, v, v) <= chi2_max) {
-          kf_update<C, S>(p, m, ry, rz, v, v);
+        ++n_test;
+        if (kf_test_update<C, S>(p, m, ry, rz, v, chi2_max)) {
+          ++n_upd;
           ok = true;
         }
       }
@@ -160,6 +165,9 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Param
     }
     P.tl_nhits[t] = n_f;
     P.tl_rowref[t] = in_row;
+    P.tl_cnt[t] = n_step;
+    P.tl_cnt[ts + t] = n_upd;
+    P.tl_cnt[2 * ts + t] = n_test;
 #pragma unroll
     for (int i = 0; i < 5; ++i) P.tl_par[(int64_t)i * ts + t] = (double)in_p[i];
   }
@@ -168,7 +176,7 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Param
 }  // namespace
 
 void launch_tracklets(const Params& P, int mode, int block, cudaStream_t s) {
-  if (block <= 0) block = 128;
+  if (block <= 0 || block > kMaxBlock) block = 128;
   int64_t blocks = ((int64_t)P.tcap + block - 1) / block;
   if (blocks < 1) blocks = 1;
   if (blocks > 152 * 32) blocks = 152 * 32;

@@ -333,6 +333,12 @@ def concat_events(events) -> Event:
                                             n_tracks=[int(e.meta.get("n_tracks", 0)) for e in events]))
 
 
+def _collision(seed, over):
+    kw = dict(n_tracks=impact_tracks(seed), sigma=SigmaModel(0.08, 0.15))
+    kw.update(over)
+    return generate_event(seed, **kw)
+
+
 def impact_tracks(seed: int) -> int:
     """Multiplicity of a collision of the uneven-multiplicity workloads:
     b uniform in [0, 15] fm, N = max(10, 9000 (1 - b/15)^2)."""
@@ -369,12 +375,15 @@ def generate_config(index: int, instance: int = 0, *, n_collisions=None, **over)
         return ev
     if index == 3:
         nc = 128 if n_collisions is None else n_collisions
-        evs = []
-        for c in range(nc):
-            s = seed_for(3, instance * 100000 + c)
-            kw = dict(n_tracks=impact_tracks(s), sigma=SigmaModel(0.08, 0.15))
-            kw.update(over)
-            evs.append(generate_event(s, **kw))
+        seeds = [seed_for(3, instance * 100000 + c) for c in range(nc)]
+        workers = over.pop("workers", 1)
+        if workers and workers > 1 and nc > 1:
+            import multiprocessing as mp
+            from concurrent.futures import ProcessPoolExecutor
+            with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+                evs = list(ex.map(_collision, seeds, [over] * nc))
+        else:
+            evs = [_collision(s, over) for s in seeds]
         ev = concat_events(evs)
         ev.meta["workload"] = f"{nc} collisions, b uniform 0-15 fm"
         return ev
