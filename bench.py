@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64", "mixed_df"])
     ap.add_argument("--collisions", type=int, default=128)
     ap.add_argument("--workload", default="batch", choices=["batch", "central"],
                     help="batch: the collisions above; central: one central Pb-Pb-like event (small case)")
@@ -280,7 +280,7 @@ def main():
     fp64_flops = steps * FLOPS_STEP + tests * FLOPS_TEST + updates * FLOPS_UPDATE
     fp64_probe = None
     roofline = None
-    if dom == "tracklets" and args.precision != "fp32":
+    if dom == "tracklets" and args.precision in ("mixed", "fp64"):
         blocks = 152 * 16
         pm = G.probe_fma(True, blocks, 2048)
         fp64_probe = 2.0 * 8 * 2048 * blocks * 256 / (pm * 1e-3) / 1e12
@@ -299,7 +299,8 @@ def main():
         "metric": "TPC clusters/s tracked (batched, mixed FP32/FP64)", "value": value, "unit": "clusters/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
+        "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64", "mixed_df": "f32+df64"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": (f"{args.collisions} collisions, b uniform 0-15 fm, 36 sectors each"
                                 if args.workload == "batch" else "one central Pb-Pb-like event, 9000 tracks"),
                    "clusters_per_rank": ev.n, "sector_instances": ev.n_instances, "precision": args.precision,

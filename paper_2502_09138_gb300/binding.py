@@ -12,7 +12,7 @@ c_int, c_int32, c_int64, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_
 
 TPCT_OK, TPCT_E_INVALID, TPCT_E_NOMEM, TPCT_E_CAPACITY, TPCT_E_CUDA, TPCT_E_TIMEOUT, TPCT_E_BUDGET, \
     TPCT_E_STATE = range(8)
-PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
+PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2, "mixed_df": 3}
 
 
 class Geometry(ctypes.Structure):

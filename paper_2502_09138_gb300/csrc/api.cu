@@ -14,6 +14,7 @@ struct tpct_ctx {
   tpct_cuts cuts{};
   tpct_precision prec = TPCT_PREC_MIXED;
   int clusters_per_bin = 2, tracklet_block = 128, refit_block = 128;
+  int n_sm = 0, tl_blocks = 0, rf_blocks = 0;   // persistent grid sizes (0: not yet queried)
   // workspace
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -69,6 +70,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   const int64_t scan_tmp = scan_tmp_elems(std::max<int64_t>(std::max<int64_t>(nr1, pl.nbin), pl.tcap + 1)) + 32;
   Params q{};
   q.status = (uint32_t*)take(sizeof(uint32_t) * 4);
+  q.work = (uint32_t*)take(sizeof(uint32_t) * 4);
   q.rx = (const double*)take(sizeof(double) * n_rows);
   q.rxf = (const float*)take(sizeof(float) * n_rows);
   q.row_count = (int32_t*)take(4 * nr1);
@@ -103,7 +105,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   q.trk_pos = (int32_t*)take(4 * n);
   q.scan_tmp = (uint64_t*)take(8 * scan_tmp);
   if (P) {
-    P->status = q.status; P->rx = q.rx; P->rxf = q.rxf;
+    P->status = q.status; P->work = q.work; P->rx = q.rx; P->rxf = q.rxf;
     P->row_count = q.row_count; P->row_start = q.row_start;
     P->row_tl_count = q.row_tl_count; P->row_tl_base = q.row_tl_base;
     P->row_ext = q.row_ext; P->grid = q.grid; P->c_bin = q.c_bin; P->c_ir = q.c_ir;
@@ -161,6 +163,14 @@ tpct_status make_params(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const
                                    !out->status || !out->x_ref || !out->param || !out->cov || !out->chi2))
     return TPCT_E_INVALID;
   if (out->capacity_ids > 0 && !out->cluster_ids) return TPCT_E_INVALID;
+  if (ctx->tl_blocks == 0 || ctx->rf_blocks == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    ctx->tl_blocks = ctx->n_sm * tracklet_blocks_per_sm((int)ctx->prec, ctx->tracklet_block);
+    ctx->rf_blocks = ctx->n_sm * refit_blocks_per_sm((int)ctx->prec, ctx->refit_block);
+  }
   Params p{};
   Plan pl = make_plan(ctx->n_rows, n, cl->n_instances, ctx->clusters_per_bin);
   Plan plan_ws = make_plan(ctx->n_rows, ctx->plan_n, ctx->plan_inst, 1);
@@ -217,14 +227,15 @@ int enqueue_track(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
   launch_scan_i32(P.row_tl_count, P.row_tl_base, nr, P.scan_tmp, s); k += scan_k;
   launch_start_fill(P, s); ++k;
   mark(3);
-  launch_tracklets(P, mode, ctx->tracklet_block, s); ++k;
+  cudaMemsetAsync(P.work, 0, sizeof(uint32_t) * 4, s);
+  launch_tracklets(P, mode, ctx->tracklet_block, ctx->tl_blocks, s); ++k;
   mark(4);
   launch_weights(P, s); ++k;
   launch_own(P, s); ++k;
   launch_scan_u64(P.tl_sel, P.tl_sel_scan, P.tcap, P.scan_tmp, s); k += scan_k;
   launch_emit(P, s); ++k;
   mark(5);
-  launch_refit(P, mode, ctx->refit_block, s); ++k;
+  launch_refit(P, mode, ctx->refit_block, ctx->rf_blocks, s); ++k;
   mark(6);
   return k;
 }
@@ -247,7 +258,7 @@ tpct_status tpct_create(const tpct_geometry* g, double bz, const tpct_cuts* cuts
   if (!(g->tan_half_sector > 0) || !(g->z_max > 0)) return TPCT_E_INVALID;
   for (int i = 1; i < g->n_rows; ++i)
     if (!(g->row_x[i] > g->row_x[i - 1])) return TPCT_E_INVALID;
-  if (!valid_cuts(*cuts) || (int)prec < 0 || (int)prec > 2) return TPCT_E_INVALID;
+  if (!valid_cuts(*cuts) || (int)prec < 0 || (int)prec > 3) return TPCT_E_INVALID;
   tpct_ctx* c = new (std::nothrow) tpct_ctx();
   if (!c) return TPCT_E_NOMEM;
   c->n_rows = g->n_rows;
@@ -274,6 +285,7 @@ tpct_status tpct_set_tuning(tpct_ctx* ctx, int cpb, int tl_block, int rf_block) 
   ctx->clusters_per_bin = cpb ? cpb : 2;
   ctx->tracklet_block = tl_block ? tl_block : 128;
   ctx->refit_block = rf_block ? rf_block : 128;
+  ctx->tl_blocks = ctx->rf_blocks = 0;
   drop_graph(ctx);
   return TPCT_OK;
 }

@@ -1,0 +1,149 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi)/2, giving a 48-bit significand (relative
+// precision about 2^-48) on the FP32 pipes.  GB300 executes FP32 FMAs at 64x
+// the FP64 rate (128 vs 2 per SM per clock), so the covariance arithmetic of
+// the tracker runs faster in this form than in native FP64.
+//
+// Error-free transformations: TwoSum (Knuth, TAOCP vol. 2, 4.2.2),
+// Fast-TwoSum (Dekker 1971, "A floating-point technique for extending the
+// available precision"), TwoProd by one FMA.  Addition follows the accurate
+// two-part scheme of double-double libraries (Hida, Li, Bailey 2001), which
+// keeps the relative error bounded under cancellation.  All primitive steps
+// use the _rn intrinsics so the compiler neither contracts nor reorders them.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace tpct {
+
+// the float/double overloads stay visible next to the df64 ones below
+using ::fabs;
+using ::sqrt;
+
+struct df64 {
+  float hi, lo;
+  __host__ __device__ df64() : hi(0.f), lo(0.f) {}
+  __host__ __device__ df64(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ explicit df64(float a) : hi(a), lo(0.f) {}
+  __host__ __device__ explicit df64(int a) : hi((float)a), lo(0.f) {}
+  __host__ __device__ explicit df64(double a) {
+    hi = (float)a;
+    lo = (float)(a - (double)hi);
+  }
+  __host__ __device__ explicit operator float() const { return hi + lo; }
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ df64 fast_two_sum(float a, float b) {   // requires |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return df64(s, e);
+}
+
+__device__ __forceinline__ df64 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df64(s, e);
+}
+
+__device__ __forceinline__ df64 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  return df64(p, e);
+}
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  df64 s = two_sum(a.hi, b.hi);
+  const df64 t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  df64 p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df64 operator*(df64 a, float b) {
+  df64 p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df64 operator*(float b, df64 a) { return a * b; }
+
+// a / b: three float quotient digits, each from the running remainder.
+__device__ __forceinline__ df64 operator/(df64 a, df64 b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  df64 r = a - b * q1;
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  r = r - b * q2;
+  const float q3 = __fdiv_rn(r.hi, b.hi);
+  return fast_two_sum(q1, q2) + df64(q3);
+}
+
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
+
+__device__ __forceinline__ bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(df64 a, df64 b) { return b < a; }
+__device__ __forceinline__ bool operator<=(df64 a, df64 b) { return !(b < a); }
+__device__ __forceinline__ bool operator>=(df64 a, df64 b) { return !(a < b); }
+
+__device__ __forceinline__ df64 fabs(df64 a) { return a.hi < 0.f ? -a : a; }
+
+// sqrt by one Newton correction of the float root: x + (a - x^2) / (2x)
+__device__ __forceinline__ df64 sqrt(df64 a) {
+  if (!(a.hi > 0.f)) return df64(0.f);
+  const float x = sqrtf(a.hi);
+  const df64 r = a - two_prod(x, x);
+  return fast_two_sum(x, __fdiv_rn(r.hi, __fmul_rn(2.f, x)));
+}
+
+// ---------------------------------------------------------------- conversions used by the kernels
+__device__ __forceinline__ float to_float(float a) { return a; }
+__device__ __forceinline__ float to_float(double a) { return (float)a; }
+__device__ __forceinline__ float to_float(df64 a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ double to_double(float a) { return (double)a; }
+__device__ __forceinline__ double to_double(double a) { return a; }
+__device__ __forceinline__ double to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+template <class E> struct ToE;
+template <> struct ToE<float> {
+  template <class T> __device__ static float get(T a) { return to_float(a); }
+};
+template <> struct ToE<double> {
+  template <class T> __device__ static double get(T a) { return to_double(a); }
+};
+template <class E, class T> __device__ __forceinline__ E to_e(T a) { return ToE<E>::template get<T>(a); }
+
+// (c - p) converted to E, with c a float cluster coordinate and p a state entry
+__device__ __forceinline__ float diff_f(float c, float p) { return c - p; }
+__device__ __forceinline__ float diff_f(float c, double p) { return (float)((double)c - p); }
+__device__ __forceinline__ float diff_f(float c, df64 p) { return to_float(df64(c) - p); }
+template <class E, class S> struct DiffTo {
+  __device__ static E get(float c, S p) { return (E)diff_f(c, p); }
+};
+template <class S> struct DiffTo<double, S> {
+  __device__ static double get(float c, S p) { return (double)c - to_double(p); }
+};
+template <class E, class S> __device__ __forceinline__ E diff_to(float c, S p) { return DiffTo<E, S>::get(c, p); }
+
+// |a| > b (b a double threshold), evaluated in the precision of a
+__device__ __forceinline__ bool abs_exceeds(float a, double b) { return fabsf(a) > (float)b; }
+__device__ __forceinline__ bool abs_exceeds(double a, double b) { return fabs(a) > b; }
+__device__ __forceinline__ bool abs_exceeds(df64 a, double b) { return fabsf(to_float(a)) > (float)b; }
+
+// |a| < b (false for NaN), evaluated in the precision of a
+__device__ __forceinline__ bool abs_below(float a, double b) { return fabsf(a) < (float)b; }
+__device__ __forceinline__ bool abs_below(double a, double b) { return fabs(a) < b; }
+__device__ __forceinline__ bool abs_below(df64 a, double b) { return fabsf(to_float(a)) < (float)b; }
+
+template <class T> struct is_df64 { static constexpr bool value = false; };
+template <> struct is_df64<df64> { static constexpr bool value = true; };
+
+}  // namespace tpct

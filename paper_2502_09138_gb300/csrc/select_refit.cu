@@ -97,63 +97,110 @@ __global__ void k_emit(const __grid_constant__ Params P) {
 // the outermost owned cluster and along all owned clusters inward (the
 // reference trajectory), and filters the deviation from it with a diffuse
 // prior; reference + deviation at the innermost cluster is the next estimate.
+//
+// Persistent: every lane runs one track as a state machine, one cluster per
+// loop iteration, and takes the next track from a device work queue when it
+// finishes, so the covariance arithmetic runs with full warps.
 template <int MODE>
 __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Params P) {
-  using R = typename Prec<MODE>::R;
+  using S = typename Prec<MODE>::RS;
+  using E = typename Prec<MODE>::RE;
+  using C = typename Prec<MODE>::RC;
   const tpct_tracks_out& O = P.out;
   const uint64_t total = P.tl_sel_scan[P.tcap];
   const int n_trk = min((int)(total >> 32), O.capacity_tracks);
-  const R kb = (R)P.kb, smax = (R)P.s_max;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_trk; k += gridDim.x * blockDim.x) {
-    const int n = O.n_cl[k], off = O.offset[k];
-    if (n < 1 || off < 0 || off + n > O.capacity_ids) continue;
-    const int t = P.trk_tl[k];
-    const int* pos = P.trk_pos + off;
-    R est[5];
+  const E kb = (E)P.kb, smax = (E)P.s_max;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lanes_below = (1u << lane) - 1u;
+
+  int k = -1, n = 0, t = 0, pass = 0, j = 0, status = 0;
+  bool exhausted = false;
+  const int* pos = P.trk_pos;
+  double x_cur = 0.0, x_prev = 0.0;
+  S est[5], ref[5], d[5];
+  C m[15], chi2 = (C)0;
+
+  while (true) {
+    const bool need = k < 0 && !exhausted;
+    const uint32_t want = __ballot_sync(0xffffffffu, need);
+    if (want) {
+      const int leader = __ffs(want) - 1;
+      int base = 0;
+      if (lane == leader) base = (int)atomicAdd(P.work + 1, (uint32_t)__popc(want));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const int mine = base + __popc(want & lanes_below);
+        if (mine >= n_trk) {
+          exhausted = true;
+        } else {
+          const int nn = O.n_cl[mine], off = O.offset[mine];
+          if (nn >= 1 && off >= 0 && off + nn <= O.capacity_ids) {   // ids of overflowing tracks were not written
+            k = mine;
+            n = nn;
+            pos = P.trk_pos + off;
+            t = P.trk_tl[k];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) est[i] = (R)P.tl_par[(int64_t)i * P.tcap + t];
-    double x_cur = P.rx[P.tl_rowref[t]];
-    R m[15], d[5], ref[5], chi2 = (R)0;
-    int status = 0;
-    for (int pass = 0; pass < P.n_refit && !status; ++pass) {
-#pragma unroll
-      for (int i = 0; i < 5; ++i) { ref[i] = est[i]; d[i] = (R)0; }
-      int p_prev = pos[n - 1];
-      double x_prev = P.rx[P.srow[p_prev]];
-      Step<R> st;
-      if (!helix_step<R>(ref[2], ref[3], ref[4], (R)(x_prev - x_cur), kb, smax, st)) { status = 1; break; }
-      ref[0] += st.dy; ref[1] += st.dz; ref[2] += st.ds;
-      cov_diag<R>(m, (R)P.c_yz_refit, (R)P.c_yz_refit, (R)P.c_s, (R)P.c_t, (R)P.c_qpt_refit);
-      chi2 = (R)0;
-      for (int j = n - 1; j >= 0; --j) {
-        const int pj = pos[j];
-        const double xj = P.rx[P.srow[pj]];
-        if (j < n - 1) {
-          if (!helix_step<R>(ref[2], ref[3], ref[4], (R)(xj - x_prev), kb, smax, st)) { status = 1; break; }
-          ref[0] += st.dy; ref[1] += st.dz; ref[2] += st.ds;
-          d[0] += st.j_ys * d[2] + st.j_yq * d[4];
-          d[1] += st.j_zs * d[2] + st.j_zt * d[3] + st.j_zq * d[4];
-          d[2] += st.j_sq * d[4];
-          cov_transport<R, R>(m, st);
+            for (int i = 0; i < 5; ++i) est[i] = (S)P.tl_par[(int64_t)i * P.tcap + t];
+            x_cur = P.rx[P.tl_rowref[t]];
+            pass = 0;
+            j = n - 1;
+            status = 0;
+          }
         }
-        x_prev = xj;
-        const R sg = sigma_of<R>(P, (R)P.sz[pj]);
-        const R v = sg * sg;
-        const R r0 = ((R)P.sy[pj] - ref[0]) - d[0], r1 = ((R)P.sz[pj] - ref[1]) - d[1];
-        chi2 += kf_chi2_update<R, R>(d, m, r0, r1, v);
       }
-      if (status) break;
-#pragma unroll
-      for (int i = 0; i < 5; ++i) est[i] = ref[i] + d[i];
-      x_cur = P.rx[P.srow[pos[0]]];
     }
-    O.status[k] = status;
-    O.chi2[k] = status ? 0.0 : (double)chi2;
-    O.x_ref[k] = status ? P.rx[P.tl_rowref[t]] : x_cur;
+    if (__ballot_sync(0xffffffffu, k >= 0) == 0u) break;
+    if (k < 0) continue;
+
+    const int pj = pos[j];
+    const double xj = P.rx[P.srow[pj]];
+    Step<E> st;
+    if (j == n - 1) {
+      // pass start: reference = previous estimate at the outermost cluster
 #pragma unroll
-    for (int i = 0; i < 5; ++i) O.param[(int64_t)k * 5 + i] = status ? P.tl_par[(int64_t)i * P.tcap + t] : (double)est[i];
+      for (int i = 0; i < 5; ++i) { ref[i] = est[i]; d[i] = (S)0; }
+      if (!helix_step<E>(to_e<E>(ref[2]), to_e<E>(ref[3]), to_e<E>(ref[4]), (E)(xj - x_cur), kb, smax, st)) {
+        status = 1;
+      } else {
+        ref[0] += (S)st.dy; ref[1] += (S)st.dz; ref[2] += (S)st.ds;
+        cov_diag<C>(m, (C)P.c_yz_refit, (C)P.c_yz_refit, (C)P.c_s, (C)P.c_t, (C)P.c_qpt_refit);
+        chi2 = (C)0;
+      }
+    } else {
+      if (!helix_step<E>(to_e<E>(ref[2]), to_e<E>(ref[3]), to_e<E>(ref[4]), (E)(xj - x_prev), kb, smax, st)) {
+        status = 1;
+      } else {
+        ref[0] += (S)st.dy; ref[1] += (S)st.dz; ref[2] += (S)st.ds;
+        d[0] += st.j_ys * d[2] + st.j_yq * d[4];
+        d[1] += st.j_zs * d[2] + st.j_zt * d[3] + st.j_zq * d[4];
+        d[2] += st.j_sq * d[4];
+        cov_transport<C, E>(m, st);
+      }
+    }
+    bool done = status != 0;
+    if (!done) {
+      x_prev = xj;
+      const C sg = sigma_of<C>(P, (C)P.sz[pj]);
+      const C r0 = ((C)(S)P.sy[pj] - ref[0]) - d[0], r1 = ((C)(S)P.sz[pj] - ref[1]) - d[1];
+      chi2 += kf_chi2_update<C, S>(d, m, r0, r1, sg * sg);
+      if (--j < 0) {
 #pragma unroll
-    for (int i = 0; i < 15; ++i) O.cov[(int64_t)k * 15 + i] = status ? 0.0 : (double)m[i];
+        for (int i = 0; i < 5; ++i) est[i] = ref[i] + d[i];
+        x_cur = P.rx[P.srow[pos[0]]];
+        if (++pass < P.n_refit) j = n - 1; else done = true;
+      }
+    }
+    if (done) {
+      O.status[k] = status;
+      O.chi2[k] = status ? 0.0 : to_double(chi2);
+      O.x_ref[k] = status ? P.rx[P.tl_rowref[t]] : x_cur;
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+        O.param[(int64_t)k * 5 + i] = status ? P.tl_par[(int64_t)i * P.tcap + t] : to_double(est[i]);
+#pragma unroll
+      for (int i = 0; i < 15; ++i) O.cov[(int64_t)k * 15 + i] = status ? 0.0 : to_double(m[i]);
+      k = -1;
+    }
   }
 }
 
@@ -214,14 +261,29 @@ void launch_own(const Params& P, cudaStream_t s) {
 void launch_emit(const Params& P, cudaStream_t s) {
   k_emit<<<blocks_for(P.tcap, kBlock), kBlock, 0, s>>>(P);
 }
-void launch_refit(const Params& P, int mode, int block, cudaStream_t s) {
+void launch_refit(const Params& P, int mode, int block, int blocks, cudaStream_t s) {
   if (block <= 0 || block > kMaxBlock) block = 128;
-  // tracks <= tracklets <= tcap; the kernel reads the count on the device
-  const int blocks = blocks_for(P.tcap / 4 + 1, block);
-  if (mode == 0) k_refit<0><<<blocks, block, 0, s>>>(P);
-  else if (mode == 1) k_refit<1><<<blocks, block, 0, s>>>(P);
-  else k_refit<2><<<blocks, block, 0, s>>>(P);
+  if (blocks < 1) blocks = 1;
+  switch (mode) {
+    case 0: k_refit<0><<<blocks, block, 0, s>>>(P); break;
+    case 1: k_refit<1><<<blocks, block, 0, s>>>(P); break;
+    case 2: k_refit<2><<<blocks, block, 0, s>>>(P); break;
+    default: k_refit<3><<<blocks, block, 0, s>>>(P); break;
+  }
 }
+
+int refit_blocks_per_sm(int mode, int block) {
+  int nb = 0;
+  cudaError_t e;
+  switch (mode) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<0>, block, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<1>, block, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<2>, block, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<3>, block, 0); break;
+  }
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
 void launch_export_tracklets(const Params& P, const tpct_debug_out& d, cudaStream_t s) {
   k_export_tracklets<<<blocks_for(P.tcap, kBlock), kBlock, 0, s>>>(P, d);
 }

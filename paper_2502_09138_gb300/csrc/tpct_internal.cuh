@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "tpct.h"
+#include "df64.cuh"
 
 namespace tpct {
 
@@ -52,6 +53,7 @@ struct Params {
   const double* rx;            // [n_rows] row x (double)
   const float* rxf;            // [n_rows] row x (float)
   uint32_t* status;            // sticky device status bits
+  uint32_t* work;              // [2] work-queue heads of the tracklet and refit kernels
   int32_t* row_count;          // [n_inst*n_rows + 1]
   int32_t* row_start;          // [n_inst*n_rows + 1]
   uint32_t* row_ext;           // [n_inst*n_rows*4] ordered-int min y, max y, min z, max z
@@ -85,12 +87,20 @@ struct Params {
 };
 
 // ------------------------------------------------------------------ precision
-// MODE 0: FP32; 1: mixed (float transport / neighbour / search arithmetic,
-// double state, covariance, update and refit); 2: FP64.
+// S: track state, E: helix-transport / neighbour / search arithmetic,
+// C: covariance, Kalman update; RS/RE/RC: the same for the refit.
+// MODE 0 FP32; 1 mixed (float E, double S/C and an all-double refit);
+// 2 FP64; 3 mixed double-float (float E, double-float S/C, refit with float
+// transport and double-float state/covariance).
 template <int MODE> struct Prec;
-template <> struct Prec<0> { using S = float;  using E = float;  using C = float;  using R = float;  };
-template <> struct Prec<1> { using S = double; using E = float;  using C = double; using R = double; };
-template <> struct Prec<2> { using S = double; using E = double; using C = double; using R = double; };
+template <> struct Prec<0> { using S = float;  using E = float;  using C = float;
+                             using RS = float;  using RE = float;  using RC = float; };
+template <> struct Prec<1> { using S = double; using E = float;  using C = double;
+                             using RS = double; using RE = double; using RC = double; };
+template <> struct Prec<2> { using S = double; using E = double; using C = double;
+                             using RS = double; using RE = double; using RC = double; };
+template <> struct Prec<3> { using S = df64;   using E = float;  using C = df64;
+                             using RS = df64;   using RE = float;  using RC = df64; };
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ uint32_t float_order_key(float f) {
@@ -134,11 +144,13 @@ int64_t scan_tmp_elems(int64_t m);
 void launch_neighbours(const Params& P, int mode, cudaStream_t s);
 void launch_clean_start(const Params& P, cudaStream_t s);
 void launch_start_fill(const Params& P, cudaStream_t s);
-void launch_tracklets(const Params& P, int mode, int block, cudaStream_t s);
+void launch_tracklets(const Params& P, int mode, int block, int blocks, cudaStream_t s);
+int tracklet_blocks_per_sm(int mode, int block);
+int refit_blocks_per_sm(int mode, int block);
 void launch_weights(const Params& P, cudaStream_t s);
 void launch_own(const Params& P, cudaStream_t s);
 void launch_emit(const Params& P, cudaStream_t s);
-void launch_refit(const Params& P, int mode, int block, cudaStream_t s);
+void launch_refit(const Params& P, int mode, int block, int blocks, cudaStream_t s);
 void launch_export_links(const Params& P, const tpct_debug_out& d, cudaStream_t s);
 void launch_export_tracklets(const Params& P, const tpct_debug_out& d, cudaStream_t s);
 int kernels_per_track(void);

@@ -4,6 +4,7 @@
 // State p = (y, z, sin phi, tan lambda, q/pT) at a pad-row x; covariance in
 // packed lower-triangular order 00,10,11,20,21,22,30,31,32,33,40,41,42,43,44.
 #pragma once
+#include <type_traits>
 #include "tpct_internal.cuh"
 
 namespace tpct {
@@ -69,8 +70,8 @@ __device__ __forceinline__ bool helix_step(E s0, E tl, E qpt, E dx, E kb, E smax
 }
 
 // C <- F C F^T for F = I + a e02 + b e04 + c e12 + d e13 + e e14 + f e24.
-template <class C>
-__device__ __forceinline__ void cov_transport(C* m, C a, C b, C c, C d, C e, C f) {
+template <class C, class J>
+__device__ __forceinline__ void cov_transport(C* m, J a, J b, J c, J d, J e, J f) {
   const C m00 = m[0], m10 = m[1], m11 = m[2], m20 = m[3], m21 = m[4], m22 = m[5];
   const C m30 = m[6], m31 = m[7], m32 = m[8], m33 = m[9];
   const C m40 = m[10], m41 = m[11], m42 = m[12], m43 = m[13], m44 = m[14];
@@ -96,9 +97,12 @@ __device__ __forceinline__ void cov_transport(C* m, C a, C b, C c, C d, C e, C f
   m[12] = m42 + f * m44;
 }
 
+// Jacobian entries enter as C, except for double-float C where the float
+// entries multiply directly (a cheaper mixed product).
 template <class C, class E>
 __device__ __forceinline__ void cov_transport(C* m, const Step<E>& st) {
-  cov_transport<C>(m, (C)st.j_ys, (C)st.j_yq, (C)st.j_zs, (C)st.j_zt, (C)st.j_zq, (C)st.j_sq);
+  using J = typename std::conditional<is_df64<C>::value, E, C>::type;
+  cov_transport<C, J>(m, (J)st.j_ys, (J)st.j_yq, (J)st.j_zs, (J)st.j_zt, (J)st.j_zq, (J)st.j_sq);
 }
 
 // chi2 of residual (r0, r1) against S = C[yz] + diag(vy, vz)

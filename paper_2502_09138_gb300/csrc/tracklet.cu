@@ -1,12 +1,19 @@
 // Step 5 of sector track finding: tracklet growth with a Kalman filter.
-// One thread per tracklet (start hit).  Upward pass: follow reciprocal links
-// while the previous accepted cluster is in the row below and has one, else
-// search the row's grid around the prediction; accept a cluster iff its chi2
-// passes; stop on a failed transport, the sector edge, too many consecutive
-// misses, or |sin phi| at its limit.  Downward pass: from the outermost
-// accepted cluster, covariance reset, to row 0, reusing the upward clusters
-// at their rows and searching elsewhere.  (The paper's "TPC Processing
-// (Tracking)", Tables 1-3.)
+//
+// Upward pass: follow reciprocal links while the previous accepted cluster is
+// in the row below and has one, else search the row's grid around the
+// prediction; accept a cluster iff its chi2 passes; stop on a failed
+// transport, the sector edge (plus margin), too many consecutive misses, or
+// |sin phi| at its limit.  Downward pass: from the outermost accepted cluster,
+// covariance reset, to row 0, reusing the upward clusters at their rows and
+// searching elsewhere.  (The paper's "TPC Processing (Tracking)", Tables 1-3.)
+//
+// GB300 mapping: a persistent kernel in which every lane runs one tracklet as
+// a state machine advancing one pad row per loop iteration.  A lane whose
+// tracklet ends takes the next one from a device work queue (warp-aggregated
+// atomic), so the FP64 (or double-float) covariance arithmetic of each
+// iteration runs with full warps instead of idling lanes of finished
+// tracklets.  Results do not depend on which lane or order runs a tracklet.
 #include "track_math.cuh"
 
 namespace tpct {
@@ -15,13 +22,13 @@ namespace {
 // Best cluster of row key ir around (py, pz): inside |dy|^2 <= k^2 (Cyy + s_c^2)
 // and |dz|^2 <= k^2 (Czz + s_c^2) with s_c the cluster's sigma; minimal
 // dy^2/(Cyy+s_c^2) + dz^2/(Czz+s_c^2), ties to the smaller input id.
-template <class E, class S, class C>
-__device__ int search_row(const Params& P, int ir, S py, S pz, C cyy, C czz) {
+template <class E, class S>
+__device__ int search_row(const Params& P, int ir, S py, S pz, E cyy, E czz) {
   const RowGrid g = P.grid[ir];
   const E k = (E)P.search_k, k2 = k * k;
   const E sig_hi = (E)fmax(P.sig_readout, P.sig_cathode);
-  const E wy = k * sqrt((E)cyy + sig_hi * sig_hi), wz = k * sqrt((E)czz + sig_hi * sig_hi);
-  const float fy = (float)py, fz = (float)pz;
+  const E wy = k * sqrt(cyy + sig_hi * sig_hi), wz = k * sqrt(czz + sig_hi * sig_hi);
+  const float fy = to_float(py), fz = to_float(pz);
   const float wyf = (float)wy * 1.0001f + 1e-4f, wzf = (float)wz * 1.0001f + 1e-4f;
   const int iy0 = bin_y(g, fy - wyf), iy1 = bin_y(g, fy + wyf);
   const int iz0 = bin_z(g, fz - wzf), iz1 = bin_z(g, fz + wzf);
@@ -32,9 +39,9 @@ __device__ int search_row(const Params& P, int ir, S py, S pz, C cyy, C czz) {
     const int q1 = P.bin_start[g.bin_base + iz * g.ny + iy1 + 1];
     for (int q = q0; q < q1; ++q) {
       const float cz = P.sz[q];
-      const E dy = (E)((S)P.sy[q] - py), dz = (E)((S)cz - pz);
+      const E dy = diff_to<E>(P.sy[q], py), dz = diff_to<E>(cz, pz);
       const E sg = sigma_of<E>(P, (E)cz);
-      const E vy = (E)cyy + sg * sg, vz = (E)czz + sg * sg;
+      const E vy = cyy + sg * sg, vz = czz + sg * sg;
       if (!(dy * dy <= k2 * vy && dz * dz <= k2 * vz)) continue;
       const E d = dy * dy / vy + dz * dz / vz;
       if (best < 0 || d <= best_d) {
@@ -55,134 +62,167 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
   const int n_tl = min(P.row_tl_base[P.n_inst * R], P.tcap);
   const E kb = (E)P.kb, smax = (E)P.s_max;
   const C chi2_max = (C)P.chi2_max;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tl; t += gridDim.x * blockDim.x) {
-    const int p0 = P.tl_start[t], ir0 = P.tl_ir[t];
-    const int r0 = ir0 % R, row0 = ir0 - r0;
-    const int h1 = P.upc[p0];
-    int* hits = P.tl_hits + t;
-    const int64_t ts = P.tcap;
+  const int64_t ts = P.tcap;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lanes_below = (1u << lane) - 1u;
 
-    // init from the first link of the chain: y, z of the start hit, direction of the link
-    S p[5];
-    C m[15];
-    {
-      const S dx = (S)(P.rx[r0 + 1] - P.rx[r0]);
-      const S dy = (S)P.sy[h1] - (S)P.sy[p0], dz = (S)P.sz[h1] - (S)P.sz[p0];
-      const S len = sqrt(dx * dx + dy * dy);
-      p[0] = (S)P.sy[p0]; p[1] = (S)P.sz[p0]; p[2] = dy / len; p[3] = dz / len; p[4] = (S)0;
-      const C sg = sigma_of<C>(P, (C)P.sz[p0]);
-      cov_diag<C>(m, sg * sg, sg * sg, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
+  // lane state
+  int t = -1;                   // current tracklet (-1: none)
+  bool exhausted = false;       // the queue had nothing left for this lane
+  bool up = true;               // pass
+  int r = 0, row0 = 0;          // next row; row key of row 0 of the instance
+  int prev = 0, prev_row = 0, miss = 0, top_row = 0, top_hit = 0, n_up = 0, j_up = 0, n_f = 0, in_row = 0;
+  int n_step = 0, n_upd = 0, n_test = 0;
+  S p[5], top[5], in_p[5];
+  C m[15];
+  int* hits = P.tl_hits;
+
+  while (true) {
+    // ---- refill lanes without a tracklet from the work queue
+    const bool need = t < 0 && !exhausted;
+    const uint32_t want = __ballot_sync(0xffffffffu, need);
+    if (want) {
+      const int leader = __ffs(want) - 1;
+      int base = 0;
+      if (lane == leader) base = (int)atomicAdd(P.work, (uint32_t)__popc(want));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const int mine = base + __popc(want & lanes_below);
+        if (mine < n_tl) {
+          t = mine;
+          // init from the first link of the chain
+          const int p0 = P.tl_start[t], ir0 = P.tl_ir[t];
+          const int r0 = ir0 % R;
+          row0 = ir0 - r0;
+          const int h1 = P.upc[p0];
+          const S dx = (S)(P.rx[r0 + 1] - P.rx[r0]);
+          const S dy = (S)P.sy[h1] - (S)P.sy[p0], dz = (S)P.sz[h1] - (S)P.sz[p0];
+          const S len = sqrt(dx * dx + dy * dy);
+          p[0] = (S)P.sy[p0]; p[1] = (S)P.sz[p0]; p[2] = dy / len; p[3] = dz / len; p[4] = (S)0;
+          const C sg = sigma_of<C>(P, (C)P.sz[p0]);
+          cov_diag<C>(m, sg * sg, sg * sg, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
+          hits = P.tl_hits + t;
+          hits[0] = p0;
+          n_up = 1;
+          prev = p0; prev_row = r0; miss = 0; top_row = r0; top_hit = p0;
+#pragma unroll
+          for (int i = 0; i < 5; ++i) top[i] = p[i];
+          n_step = n_upd = n_test = 0;
+          up = true;
+          r = r0 + 1;
+        } else {
+          exhausted = true;
+        }
+      }
     }
-    hits[0] = p0;
-    int n_up = 1;
-    int n_step = 0, n_upd = 0, n_test = 0;
+    if (__ballot_sync(0xffffffffu, t >= 0) == 0u) break;
+    if (t < 0) continue;
 
-    // ---- upward
-    int prev = p0, prev_row = r0, miss = 0, top_row = r0, top_hit = p0;
-    S top[5] = {p[0], p[1], p[2], p[3], p[4]};
-    for (int r = r0 + 1; r < R; ++r) {
-      Step<E> st;
-      if (!helix_step<E>((E)p[2], (E)p[3], (E)p[4], (E)(P.rx[r] - P.rx[r - 1]), kb, smax, st)) break;
+    // ---- one row of the current pass
+    bool go = true;   // pass continues after this row
+    Step<E> st;
+    const double x_from = up ? P.rx[r - 1] : P.rx[r + 1];
+    if (!helix_step<E>(to_e<E>(p[2]), to_e<E>(p[3]), to_e<E>(p[4]), (E)(P.rx[r] - x_from), kb, smax, st)) {
+      go = false;
+    } else {
       ++n_step;
       p[0] += (S)st.dy; p[1] += (S)st.dz; p[2] += (S)st.ds;
       cov_transport<C, E>(m, st);
-      if (fabs(p[0]) > (S)(P.rx[r] * P.tan_half + P.edge_margin)) break;
-      int cand = prev_row == r - 1 ? P.upc[prev] : -1;
-      if (cand < 0) cand = search_row<E, S, C>(P, row0 + r, p[0], p[1], m[0], m[2]);
-      bool ok = false;
-      if (cand >= 0) {
-        const C sg = sigma_of<C>(P, (C)P.sz[cand]);
-        const C v = sg * sg;
-        const C ry = (C)((S)P.sy[cand] - p[0]), rz = (C)((S)P.sz[cand] - p[1]);
-        ++n_test;
-        if (kf_test_update<C, S>(p, m, ry, rz, v, chi2_max)) {
-          ++n_upd;
-          ok = true;
+      if (abs_exceeds(p[0], P.rx[r] * P.tan_half + P.edge_margin)) {
+        go = false;
+      } else {
+        int cand = -1;
+        if (up) {
+          if (prev_row == r - 1) cand = P.upc[prev];
+        } else if (j_up >= 0) {
+          const int h = hits[(int64_t)j_up * ts];
+          if ((int)P.srow[h] == r) { cand = h; --j_up; }
+        }
+        if (cand < 0) cand = search_row<E, S>(P, row0 + r, p[0], p[1], to_e<E>(m[0]), to_e<E>(m[2]));
+        bool ok = false;
+        if (cand >= 0) {
+          const C sg = sigma_of<C>(P, (C)P.sz[cand]);
+          const C ry = (C)((S)P.sy[cand] - p[0]), rz = (C)((S)P.sz[cand] - p[1]);
+          ++n_test;
+          if (kf_test_update<C, S>(p, m, ry, rz, sg * sg, chi2_max)) { ++n_upd; ok = true; }
+        }
+        if (ok) {
+          miss = 0;
+          if (up) {
+            hits[(int64_t)n_up * ts] = cand;
+            ++n_up;
+            prev = cand; prev_row = r; top_row = r; top_hit = cand;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) top[i] = p[i];
+          } else {
+            hits[(int64_t)(R - 1 - n_f) * ts] = cand;
+            ++n_f;
+            in_row = r;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) in_p[i] = p[i];
+          }
+          if (!abs_below(p[2], P.s_max)) go = false;
+        } else if (++miss > P.max_miss) {
+          go = false;
         }
       }
-      if (ok) {
-        hits[(int64_t)n_up * ts] = cand;
-        ++n_up;
-        prev = cand; prev_row = r; miss = 0;
-        top_row = r; top_hit = cand;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) top[i] = p[i];
-        if (!(fabs(p[2]) < (S)P.s_max)) break;
-      } else if (++miss > P.max_miss) {
-        break;
-      }
     }
-
-    // ---- downward from the outermost accepted cluster, covariance reset.
-    // Final clusters go to slots R-1, R-2, ... (never over an unread upward entry).
+    if (go) {
+      r += up ? 1 : -1;
+      go = up ? r < R : r >= 0;
+    }
+    if (!go && up) {
+      // switch to the downward pass from the outermost accepted cluster.
+      // Final clusters go to slots R-1, R-2, ... (never over an unread upward entry).
+      up = false;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) p[i] = top[i];
-    {
+      for (int i = 0; i < 5; ++i) { p[i] = top[i]; in_p[i] = top[i]; }
       const C sg = sigma_of<C>(P, (C)P.sz[top_hit]);
       cov_diag<C>(m, sg * sg, sg * sg, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
+      j_up = n_up - 2;
+      n_f = 1;
+      hits[(int64_t)(R - 1) * ts] = top_hit;
+      in_row = top_row;
+      miss = 0;
+      r = top_row - 1;
+      go = r >= 0;
     }
-    int j_up = n_up - 2;
-    int n_f = 1;
-    hits[(int64_t)(R - 1) * ts] = top_hit;
-    int in_row = top_row;
-    S in_p[5] = {p[0], p[1], p[2], p[3], p[4]};
-    miss = 0;
-    for (int r = top_row - 1; r >= 0; --r) {
-      Step<E> st;
-      if (!helix_step<E>((E)p[2], (E)p[3], (E)p[4], (E)(P.rx[r] - P.rx[r + 1]), kb, smax, st)) break;
-      ++n_step;
-      p[0] += (S)st.dy; p[1] += (S)st.dz; p[2] += (S)st.ds;
-      cov_transport<C, E>(m, st);
-      if (fabs(p[0]) > (S)(P.rx[r] * P.tan_half + P.edge_margin)) break;
-      int cand = -1;
-      if (j_up >= 0) {
-        const int h = hits[(int64_t)j_up * ts];
-        if ((int)P.srow[h] == r) { cand = h; --j_up; }
-      }
-      if (cand < 0) cand = search_row<E, S, C>(P, row0 + r, p[0], p[1], m[0], m[2]);
-      bool ok = false;
-      if (cand >= 0) {
-        const C sg = sigma_of<C>(P, (C)P.sz[cand]);
-        const C v = sg * sg;
-        const C ry = (C)((S)P.sy[cand] - p[0]), rz = (C)((S)P.sz[cand] - p[1]);
-        ++n_test;
-        if (kf_test_update<C, S>(p, m, ry, rz, v, chi2_max)) {
-          ++n_upd;
-          ok = true;
-        }
-      }
-      if (ok) {
-        hits[(int64_t)(R - 1 - n_f) * ts] = cand;
-        ++n_f;
-        in_row = r;
-        miss = 0;
+    if (!go) {
+      P.tl_nhits[t] = n_f;
+      P.tl_rowref[t] = in_row;
+      P.tl_cnt[t] = n_step;
+      P.tl_cnt[ts + t] = n_upd;
+      P.tl_cnt[2 * ts + t] = n_test;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) in_p[i] = p[i];
-        if (!(fabs(p[2]) < (S)P.s_max)) break;
-      } else if (++miss > P.max_miss) {
-        break;
-      }
+      for (int i = 0; i < 5; ++i) P.tl_par[(int64_t)i * ts + t] = to_double(in_p[i]);
+      t = -1;
     }
-    P.tl_nhits[t] = n_f;
-    P.tl_rowref[t] = in_row;
-    P.tl_cnt[t] = n_step;
-    P.tl_cnt[ts + t] = n_upd;
-    P.tl_cnt[2 * ts + t] = n_test;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) P.tl_par[(int64_t)i * ts + t] = (double)in_p[i];
   }
 }
 
 }  // namespace
 
-void launch_tracklets(const Params& P, int mode, int block, cudaStream_t s) {
+void launch_tracklets(const Params& P, int mode, int block, int blocks, cudaStream_t s) {
   if (block <= 0 || block > kMaxBlock) block = 128;
-  int64_t blocks = ((int64_t)P.tcap + block - 1) / block;
   if (blocks < 1) blocks = 1;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  if (mode == 0) k_tracklets<0><<<(unsigned)blocks, block, 0, s>>>(P);
-  else if (mode == 1) k_tracklets<1><<<(unsigned)blocks, block, 0, s>>>(P);
-  else k_tracklets<2><<<(unsigned)blocks, block, 0, s>>>(P);
+  switch (mode) {
+    case 0: k_tracklets<0><<<blocks, block, 0, s>>>(P); break;
+    case 1: k_tracklets<1><<<blocks, block, 0, s>>>(P); break;
+    case 2: k_tracklets<2><<<blocks, block, 0, s>>>(P); break;
+    default: k_tracklets<3><<<blocks, block, 0, s>>>(P); break;
+  }
+}
+
+int tracklet_blocks_per_sm(int mode, int block) {
+  int n = 0;
+  cudaError_t e;
+  switch (mode) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tracklets<0>, block, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tracklets<1>, block, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tracklets<2>, block, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tracklets<3>, block, 0); break;
+  }
+  return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 }  // namespace tpct

@@ -23,7 +23,7 @@ def _assert_pass(rep):
     assert rep["pass"], rep
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "fp64", "mixed_df"])
 def test_single_sector_parity(event0, oracle0, precision):
     gtr, gdbg, st, _ = run_gpu(event0, precision)
     assert st == 0
@@ -46,7 +46,7 @@ def oracle1(event1):
     return oracle.track_event(event1)
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "fp64", "mixed_df"])
 def test_central_event_parity(event1, oracle1, precision):
     gtr, gdbg, st, _ = run_gpu(event1, precision)
     assert st == 0
@@ -112,9 +112,10 @@ def test_empty_and_sparse_instances():
     _assert_pass(compare(ev, ores, gdbg, gtr))
 
 
-def test_batch_of_collisions_sampled_parity():
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
+def test_batch_of_collisions_sampled_parity(precision):
     ev = synth.generate_config(3, n_collisions=12)
-    gtr, gdbg, st, _ = run_gpu(ev, "mixed", batched=True)
+    gtr, gdbg, st, _ = run_gpu(ev, precision, batched=True)
     assert st == 0
     rng = np.random.default_rng(5)
     idx = np.sort(rng.choice(ev.n_instances, 24, replace=False))
