@@ -437,9 +437,10 @@ void launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t m, uint64_t* tmp
 void launch_neighbours(const Params& P, int mode, cudaStream_t s) {
   const int warps = P.n_inst * P.n_rows;
   const int blocks = blocks_for((int64_t)warps * 32, kBlock);
+  // the neighbour arithmetic is float in every mode but FP64
   if (mode == 0) k_neighbours<0><<<blocks, kBlock, 0, s>>>(P);
-  else if (mode == 1) k_neighbours<1><<<blocks, kBlock, 0, s>>>(P);
-  else k_neighbours<2><<<blocks, kBlock, 0, s>>>(P);
+  else if (mode == 2) k_neighbours<2><<<blocks, kBlock, 0, s>>>(P);
+  else k_neighbours<1><<<blocks, kBlock, 0, s>>>(P);
 }
 
 void launch_clean_start(const Params& P, cudaStream_t s) {

@@ -115,37 +115,47 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
         }
       }
     }
-    if (__ballot_sync(0xffffffffu, t >= 0) == 0u) break;
+    const uint32_t active = __ballot_sync(0xffffffffu, t >= 0);
+    if (active == 0u) break;
     if (t < 0) continue;
 
-    // ---- one row of the current pass
+    // ---- one row of the current pass.  Every lane with a tracklet runs the
+    // same straight-line sequence (transport, candidate, test/update); the
+    // __syncwarp calls rejoin the lanes after the divergent candidate search so
+    // that the covariance arithmetic issues once per warp.
     bool go = true;   // pass continues after this row
     Step<E> st;
     const double x_from = up ? P.rx[r - 1] : P.rx[r + 1];
-    if (!helix_step<E>(to_e<E>(p[2]), to_e<E>(p[3]), to_e<E>(p[4]), (E)(P.rx[r] - x_from), kb, smax, st)) {
-      go = false;
-    } else {
+    const bool stepped = helix_step<E>(to_e<E>(p[2]), to_e<E>(p[3]), to_e<E>(p[4]), (E)(P.rx[r] - x_from),
+                                       kb, smax, st);
+    if (stepped) {
       ++n_step;
       p[0] += (S)st.dy; p[1] += (S)st.dz; p[2] += (S)st.ds;
       cov_transport<C, E>(m, st);
-      if (abs_exceeds(p[0], P.rx[r] * P.tan_half + P.edge_margin)) {
-        go = false;
-      } else {
-        int cand = -1;
-        if (up) {
-          if (prev_row == r - 1) cand = P.upc[prev];
-        } else if (j_up >= 0) {
-          const int h = hits[(int64_t)j_up * ts];
-          if ((int)P.srow[h] == r) { cand = h; --j_up; }
-        }
-        if (cand < 0) cand = search_row<E, S>(P, row0 + r, p[0], p[1], to_e<E>(m[0]), to_e<E>(m[2]));
-        bool ok = false;
-        if (cand >= 0) {
-          const C sg = sigma_of<C>(P, (C)P.sz[cand]);
-          const C ry = (C)((S)P.sy[cand] - p[0]), rz = (C)((S)P.sz[cand] - p[1]);
-          ++n_test;
-          if (kf_test_update<C, S>(p, m, ry, rz, sg * sg, chi2_max)) { ++n_upd; ok = true; }
-        }
+    }
+    const bool inside = stepped && !abs_exceeds(p[0], P.rx[r] * P.tan_half + P.edge_margin);
+    go = inside;
+    int cand = -1;
+    if (inside) {
+      if (up) {
+        if (prev_row == r - 1) cand = P.upc[prev];
+      } else if (j_up >= 0) {
+        const int h = hits[(int64_t)j_up * ts];
+        if ((int)P.srow[h] == r) { cand = h; --j_up; }
+      }
+      if (cand < 0) cand = search_row<E, S>(P, row0 + r, p[0], p[1], to_e<E>(m[0]), to_e<E>(m[2]));
+    }
+    __syncwarp(active);
+    bool ok = false;
+    if (cand >= 0) {
+      const C sg = sigma_of<C>(P, (C)P.sz[cand]);
+      const C ry = (C)((S)P.sy[cand] - p[0]), rz = (C)((S)P.sz[cand] - p[1]);
+      ++n_test;
+      if (kf_test_update<C, S>(p, m, ry, rz, sg * sg, chi2_max)) { ++n_upd; ok = true; }
+    }
+    __syncwarp(active);
+    if (inside) {
+      {
         if (ok) {
           miss = 0;
           if (up) {

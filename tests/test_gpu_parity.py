@@ -1,4 +1,6 @@
 """CUDA path against the oracle, element by element, through the C ABI."""
+import json
+
 import numpy as np
 import pytest
 
@@ -20,7 +22,8 @@ def _built():
 
 
 def _assert_pass(rep):
-    assert rep["pass"], rep
+    if not rep["pass"]:
+        pytest.fail("parity failed: " + json.dumps(rep, default=str))
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64", "mixed_df"])
