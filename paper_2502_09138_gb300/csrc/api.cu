@@ -73,6 +73,10 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   q.work = (uint32_t*)take(sizeof(uint32_t) * 4);
   q.rx = (const double*)take(sizeof(double) * n_rows);
   q.rxf = (const float*)take(sizeof(float) * n_rows);
+  q.rdx = (const double*)take(sizeof(double) * n_rows);
+  q.rdxf = (const float*)take(sizeof(float) * n_rows);
+  q.edge = (const double*)take(sizeof(double) * n_rows);
+  q.edgef = (const float*)take(sizeof(float) * n_rows);
   q.row_count = (int32_t*)take(4 * nr1);
   q.row_start = (int32_t*)take(4 * nr1);
   q.row_tl_count = (int32_t*)take(4 * nr1);
@@ -106,6 +110,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   q.scan_tmp = (uint64_t*)take(8 * scan_tmp);
   if (P) {
     P->status = q.status; P->work = q.work; P->rx = q.rx; P->rxf = q.rxf;
+    P->rdx = q.rdx; P->rdxf = q.rdxf; P->edge = q.edge; P->edgef = q.edgef;
     P->row_count = q.row_count; P->row_start = q.row_start;
     P->row_tl_count = q.row_tl_count; P->row_tl_base = q.row_tl_base;
     P->row_ext = q.row_ext; P->grid = q.grid; P->c_bin = q.c_bin; P->c_ir = q.c_ir;
@@ -122,10 +127,19 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
 struct RowTable {
   double x[kMaxRows];
 };
-__global__ void k_set_tables_v(double* rx, float* rxf, int n_rows, const RowTable tab) {
-  for (int i = threadIdx.x; i < n_rows; i += blockDim.x) {
-    rx[i] = tab.x[i];
-    rxf[i] = (float)tab.x[i];
+// Row tables: x, the step to the previous row, the sector edge plus margin,
+// in double and float.
+__global__ void k_set_tables_v(const Params P, const RowTable tab) {
+  for (int i = threadIdx.x; i < P.n_rows; i += blockDim.x) {
+    const double x = tab.x[i];
+    const double dx = i > 0 ? x - tab.x[i - 1] : 0.0;
+    const double e = x * P.tan_half + P.edge_margin;
+    const_cast<double*>(P.rx)[i] = x;
+    const_cast<float*>(P.rxf)[i] = (float)x;
+    const_cast<double*>(P.rdx)[i] = dx;
+    const_cast<float*>(P.rdxf)[i] = (float)dx;
+    const_cast<double*>(P.edge)[i] = e;
+    const_cast<float*>(P.edgef)[i] = (float)e;
   }
 }
 
@@ -190,6 +204,7 @@ tpct_status make_params(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const
   p.f_shared = c.f_shared; p.sig_readout = c.sig_readout; p.sig_cathode = c.sig_cathode;
   p.c_s = c.c_s; p.c_t = c.c_t; p.c_qpt = c.c_qpt; p.c_yz_refit = c.c_yz_refit;
   p.c_qpt_refit = c.c_qpt_refit; p.sig_slope = (c.sig_cathode - c.sig_readout) / ctx->z_max;
+  p.s_max_f = (float)c.s_max;
   p.max_miss = c.max_miss; p.n_min = c.n_min; p.n_refit = c.n_refit;
   p.x = cl->x; p.y = cl->y; p.z = cl->z; p.row = cl->row; p.inst_off = cl->sector_offsets;
   p.out = *out;
@@ -211,7 +226,7 @@ int enqueue_track(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
   const int64_t nr = (int64_t)P.n_inst * P.n_rows;
   const int scan_k = 3;
   mark(0);
-  k_set_tables_v<<<1, 256, 0, s>>>(const_cast<double*>(P.rx), const_cast<float*>(P.rxf), ctx->n_rows, tab); ++k;
+  k_set_tables_v<<<1, 256, 0, s>>>(P, tab); ++k;
   launch_rows(P, s); k += 2;
   launch_scan_i32(P.row_count, P.row_start, nr, P.scan_tmp, s); k += scan_k;
   launch_grid_dims(P, s); ++k;

@@ -18,6 +18,7 @@ namespace tpct {
 // the float/double overloads stay visible next to the df64 ones below
 using ::fabs;
 using ::sqrt;
+using ::copysign;
 
 struct df64 {
   float hi, lo;
@@ -94,7 +95,10 @@ __device__ __forceinline__ bool operator>(df64 a, df64 b) { return b < a; }
 __device__ __forceinline__ bool operator<=(df64 a, df64 b) { return !(b < a); }
 __device__ __forceinline__ bool operator>=(df64 a, df64 b) { return !(a < b); }
 
+__device__ __forceinline__ bool operator!=(df64 a, df64 b) { return a.hi != b.hi || a.lo != b.lo; }
+
 __device__ __forceinline__ df64 fabs(df64 a) { return a.hi < 0.f ? -a : a; }
+__device__ __forceinline__ df64 copysign(df64 a, df64 s) { return (a.hi < 0.f) != (s.hi < 0.f) ? -a : a; }
 
 // sqrt by one Newton correction of the float root: x + (a - x^2) / (2x)
 __device__ __forceinline__ df64 sqrt(df64 a) {
@@ -119,7 +123,13 @@ template <> struct ToE<float> {
 template <> struct ToE<double> {
   template <class T> __device__ static double get(T a) { return to_double(a); }
 };
-template <class E, class T> __device__ __forceinline__ E to_e(T a) { return ToE<E>::template get<T>(a); }
+struct df64;
+template <> struct ToE<df64> {
+  __device__ static df64 get(df64 a) { return a; }
+  __device__ static df64 get(double a) { return df64(a); }
+  __device__ static df64 get(float a) { return df64(a); }
+};
+template <class E, class T> __device__ __forceinline__ E to_e(T a) { return ToE<E>::get(a); }
 
 // (c - p) converted to E, with c a float cluster coordinate and p a state entry
 __device__ __forceinline__ float diff_f(float c, float p) { return c - p; }
@@ -133,15 +143,15 @@ template <class S> struct DiffTo<double, S> {
 };
 template <class E, class S> __device__ __forceinline__ E diff_to(float c, S p) { return DiffTo<E, S>::get(c, p); }
 
-// |a| > b (b a double threshold), evaluated in the precision of a
-__device__ __forceinline__ bool abs_exceeds(float a, double b) { return fabsf(a) > (float)b; }
+// |a| > b, evaluated in the precision of a (the threshold comes in that precision)
+__device__ __forceinline__ bool abs_exceeds(float a, float b) { return fabsf(a) > b; }
 __device__ __forceinline__ bool abs_exceeds(double a, double b) { return fabs(a) > b; }
-__device__ __forceinline__ bool abs_exceeds(df64 a, double b) { return fabsf(to_float(a)) > (float)b; }
+__device__ __forceinline__ bool abs_exceeds(df64 a, float b) { return fabsf(to_float(a)) > b; }
 
 // |a| < b (false for NaN), evaluated in the precision of a
-__device__ __forceinline__ bool abs_below(float a, double b) { return fabsf(a) < (float)b; }
+__device__ __forceinline__ bool abs_below(float a, float b) { return fabsf(a) < b; }
 __device__ __forceinline__ bool abs_below(double a, double b) { return fabs(a) < b; }
-__device__ __forceinline__ bool abs_below(df64 a, double b) { return fabsf(to_float(a)) < (float)b; }
+__device__ __forceinline__ bool abs_below(df64 a, float b) { return fabsf(to_float(a)) < b; }
 
 template <class T> struct is_df64 { static constexpr bool value = false; };
 template <> struct is_df64<df64> { static constexpr bool value = true; };

@@ -52,6 +52,11 @@ struct Params {
   // workspace
   const double* rx;            // [n_rows] row x (double)
   const float* rxf;            // [n_rows] row x (float)
+  const double* rdx;           // [n_rows] rx[r] - rx[r-1] (0 at r = 0)
+  const float* rdxf;           // [n_rows] the same rounded to float
+  const double* edge;          // [n_rows] rx[r] * tan_half + edge_margin
+  const float* edgef;          // [n_rows] the same rounded to float
+  float s_max_f;               // s_max rounded to float
   uint32_t* status;            // sticky device status bits
   uint32_t* work;              // [2] work-queue heads of the tracklet and refit kernels
   int32_t* row_count;          // [n_inst*n_rows + 1]
@@ -90,8 +95,9 @@ struct Params {
 // S: track state, E: helix-transport / neighbour / search arithmetic,
 // C: covariance, Kalman update; RS/RE/RC: the same for the refit.
 // MODE 0 FP32; 1 mixed (float E, double S/C and an all-double refit);
-// 2 FP64; 3 mixed double-float (float E, double-float S/C, refit with float
-// transport and double-float state/covariance).
+// 2 FP64; 3 mixed double-float (float E, double-float S/C, and an all
+// double-float refit: its diffuse prior amplifies Jacobian rounding, so the
+// refit transport needs more than float, exactly as the mixed refit uses double).
 template <int MODE> struct Prec;
 template <> struct Prec<0> { using S = float;  using E = float;  using C = float;
                              using RS = float;  using RE = float;  using RC = float; };
@@ -100,7 +106,7 @@ template <> struct Prec<1> { using S = double; using E = float;  using C = doubl
 template <> struct Prec<2> { using S = double; using E = double; using C = double;
                              using RS = double; using RE = double; using RC = double; };
 template <> struct Prec<3> { using S = df64;   using E = float;  using C = df64;
-                             using RS = df64;   using RE = float;  using RC = df64; };
+                             using RS = df64;   using RE = df64;   using RC = df64; };
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ uint32_t float_order_key(float f) {
@@ -120,6 +126,15 @@ __device__ __forceinline__ T sigma_of(const Params& P, T z) {
   d = d > (T)P.z_max ? (T)P.z_max : d;
   return (T)P.sig_readout + (T)P.sig_slope * d;
 }
+
+// Row-table access in the precision of the caller.
+template <class E> __device__ __forceinline__ E row_dx(const Params& P, int r);
+template <> __device__ __forceinline__ float row_dx<float>(const Params& P, int r) { return P.rdxf[r]; }
+template <> __device__ __forceinline__ double row_dx<double>(const Params& P, int r) { return P.rdx[r]; }
+template <class S> struct EdgeOf { __device__ static float get(const Params& P, int r) { return P.edgef[r]; } };
+template <> struct EdgeOf<double> { __device__ static double get(const Params& P, int r) { return P.edge[r]; } };
+template <class S> struct SmaxOf { __device__ static float get(const Params& P) { return P.s_max_f; } };
+template <> struct SmaxOf<double> { __device__ static double get(const Params& P) { return P.s_max; } };
 
 // Bin of (y, z) in a row grid (monotonic, clamped).
 __device__ __forceinline__ int bin_y(const RowGrid& g, float y) {

@@ -10,8 +10,8 @@
 namespace tpct {
 
 // g(h) = asin(h)/h and g'(h).  Near 0 from the Taylor series of asin
-// (coefficients (2n)! / (4^n (n!)^2 (2n+1))); float uses it up to |h| = 0.25,
-// double up to |h| = 0.01 (truncation below 1e-9 and 1e-25 respectively).
+// (coefficients a_n = (2n)! / (4^n (n!)^2 (2n+1))); float uses it up to
+// |h| = 0.25, double up to |h| = 0.01 (truncation below 1e-9 and 1e-25).
 template <class E>
 __device__ __forceinline__ void asin_ratio(E h, E& g, E& gp) {
   const E u = h * h;
@@ -25,6 +25,40 @@ __device__ __forceinline__ void asin_ratio(E h, E& g, E& gp) {
     const E ih = (E)1 / h;
     g = asin(h) * ih;
     gp = ((E)1 / sqrt((E)1 - u) - g) * ih;
+  }
+}
+
+// Double-float version: the series to u^11 below |h| = 0.25 (truncation
+// ~2e-17; 4 terms suffice below |h| = 0.01), else g, g' from double asin.
+// a_n = binom(2n, n) / (4^n (2n + 1)) as double-float pairs: series of g and of g'/h
+constexpr int kAsinTerms = 12;
+__constant__ float kAsinG[kAsinTerms][2] = {
+#define TPCT_DF(v) {(float)(v), (float)((v) - (double)(float)(v))}
+    TPCT_DF(1.0), TPCT_DF(1.0 / 6.0), TPCT_DF(3.0 / 40.0), TPCT_DF(5.0 / 112.0), TPCT_DF(35.0 / 1152.0),
+    TPCT_DF(63.0 / 2816.0), TPCT_DF(231.0 / 13312.0), TPCT_DF(143.0 / 10240.0), TPCT_DF(6435.0 / 557056.0),
+    TPCT_DF(12155.0 / 1245184.0), TPCT_DF(46189.0 / 5505024.0), TPCT_DF(88179.0 / 12058624.0)};
+__constant__ float kAsinD[kAsinTerms][2] = {
+    TPCT_DF(0.0), TPCT_DF(2.0 / 6.0), TPCT_DF(12.0 / 40.0), TPCT_DF(30.0 / 112.0), TPCT_DF(280.0 / 1152.0),
+    TPCT_DF(630.0 / 2816.0), TPCT_DF(2772.0 / 13312.0), TPCT_DF(2002.0 / 10240.0), TPCT_DF(102960.0 / 557056.0),
+    TPCT_DF(218790.0 / 1245184.0), TPCT_DF(923780.0 / 5505024.0), TPCT_DF(1939938.0 / 12058624.0)};
+#undef TPCT_DF
+
+__device__ __forceinline__ void asin_ratio(df64 h, df64& g, df64& gp) {
+  const df64 u = h * h;
+  if (u.hi < 0.0625f) {
+    const int top = u.hi < 1e-4f ? 4 : kAsinTerms - 1;
+    df64 sg(kAsinG[top][0], kAsinG[top][1]), sd(kAsinD[top][0], kAsinD[top][1]);
+    for (int n = top - 1; n >= 1; --n) {
+      sg = sg * u + df64(kAsinG[n][0], kAsinG[n][1]);
+      sd = sd * u + df64(kAsinD[n][0], kAsinD[n][1]);
+    }
+    g = sg * u + df64(1.0f);
+    gp = h * sd;
+  } else {
+    const double hd = to_double(h);
+    const double gd = asin(hd) / hd;
+    g = df64(gd);
+    gp = df64((1.0 / sqrt(1.0 - hd * hd) - gd) / hd);
   }
 }
 
@@ -53,7 +87,7 @@ __device__ __forceinline__ bool helix_step(E s0, E tl, E qpt, E dx, E kb, E smax
   const E len = copysign(sqrt(dx * dx + dy * dy), dx);
   const E h = (E)0.5 * rho * len;
   E g, gp;
-  asin_ratio<E>(h, g, gp);
+  asin_ratio(h, g, gp);
   const E arc = len * g;
   st.dy = dy;
   st.dz = tl * arc;

@@ -28,7 +28,8 @@ __device__ int search_row(const Params& P, int ir, S py, S pz, E cyy, E czz) {
   const E k = (E)P.search_k, k2 = k * k;
   const E sig_hi = (E)fmax(P.sig_readout, P.sig_cathode);
   const E wy = k * sqrt(cyy + sig_hi * sig_hi), wz = k * sqrt(czz + sig_hi * sig_hi);
-  const float fy = to_float(py), fz = to_float(pz);
+  const E ey = to_e<E>(py), ez = to_e<E>(pz);
+  const float fy = (float)ey, fz = (float)ez;
   const float wyf = (float)wy * 1.0001f + 1e-4f, wzf = (float)wz * 1.0001f + 1e-4f;
   const int iy0 = bin_y(g, fy - wyf), iy1 = bin_y(g, fy + wyf);
   const int iz0 = bin_z(g, fz - wzf), iz1 = bin_z(g, fz + wzf);
@@ -39,7 +40,7 @@ __device__ int search_row(const Params& P, int ir, S py, S pz, E cyy, E czz) {
     const int q1 = P.bin_start[g.bin_base + iz * g.ny + iy1 + 1];
     for (int q = q0; q < q1; ++q) {
       const float cz = P.sz[q];
-      const E dy = diff_to<E>(P.sy[q], py), dz = diff_to<E>(cz, pz);
+      const E dy = (E)P.sy[q] - ey, dz = (E)cz - ez;
       const E sg = sigma_of<E>(P, (E)cz);
       const E vy = cyy + sg * sg, vz = czz + sg * sg;
       if (!(dy * dy <= k2 * vy && dz * dz <= k2 * vz)) continue;
@@ -125,15 +126,14 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
     // that the covariance arithmetic issues once per warp.
     bool go = true;   // pass continues after this row
     Step<E> st;
-    const double x_from = up ? P.rx[r - 1] : P.rx[r + 1];
-    const bool stepped = helix_step<E>(to_e<E>(p[2]), to_e<E>(p[3]), to_e<E>(p[4]), (E)(P.rx[r] - x_from),
-                                       kb, smax, st);
+    const E dx = up ? row_dx<E>(P, r) : -row_dx<E>(P, r + 1);
+    const bool stepped = helix_step<E>(to_e<E>(p[2]), to_e<E>(p[3]), to_e<E>(p[4]), dx, kb, smax, st);
     if (stepped) {
       ++n_step;
       p[0] += (S)st.dy; p[1] += (S)st.dz; p[2] += (S)st.ds;
       cov_transport<C, E>(m, st);
     }
-    const bool inside = stepped && !abs_exceeds(p[0], P.rx[r] * P.tan_half + P.edge_margin);
+    const bool inside = stepped && !abs_exceeds(p[0], EdgeOf<S>::get(P, r));
     go = inside;
     int cand = -1;
     if (inside) {
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
 #pragma unroll
             for (int i = 0; i < 5; ++i) in_p[i] = p[i];
           }
-          if (!abs_below(p[2], P.s_max)) go = false;
+          if (!abs_below(p[2], SmaxOf<S>::get(P))) go = false;
         } else if (++miss > P.max_miss) {
           go = false;
         }
