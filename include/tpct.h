@@ -88,9 +88,9 @@ typedef struct {
 /* Arithmetic of steps 2-7.  FP32: everything in float.  MIXED (default):
  * neighbour tests, grid search and helix-transport arithmetic in float; track
  * state, covariance, Kalman update and the whole refit in double.  FP64: all
- * double.  MIXED_DF: as MIXED, but the double parts are double-float pairs
- * (48-bit significand) on the FP32 pipes, and the refit's helix transport is
- * float; GB300 runs FP32 at 64x its FP64 rate. */
+ * double.  MIXED_DF: as MIXED, but the tracklet state and covariance are
+ * double-float pairs (48-bit significand) on the FP32 pipes, which GB300 runs
+ * at 64x its FP64 rate; the refit stays double. */
 typedef enum { TPCT_PREC_FP32 = 0, TPCT_PREC_MIXED = 1, TPCT_PREC_FP64 = 2, TPCT_PREC_MIXED_DF = 3 } tpct_precision;
 
 /* Input clusters (device, caller-owned, read-only). */

@@ -95,9 +95,9 @@ struct Params {
 // S: track state, E: helix-transport / neighbour / search arithmetic,
 // C: covariance, Kalman update; RS/RE/RC: the same for the refit.
 // MODE 0 FP32; 1 mixed (float E, double S/C and an all-double refit);
-// 2 FP64; 3 mixed double-float (float E, double-float S/C, and an all
-// double-float refit: its diffuse prior amplifies Jacobian rounding, so the
-// refit transport needs more than float, exactly as the mixed refit uses double).
+// 2 FP64; 3 mixed double-float (float E, double-float S/C in the tracklets;
+// the refit stays all-double: its covariance starts from a diffuse prior and
+// amplifies rounding by ~1e12, beyond what the 48-bit double-float keeps).
 template <int MODE> struct Prec;
 template <> struct Prec<0> { using S = float;  using E = float;  using C = float;
                              using RS = float;  using RE = float;  using RC = float; };
@@ -106,7 +106,7 @@ template <> struct Prec<1> { using S = double; using E = float;  using C = doubl
 template <> struct Prec<2> { using S = double; using E = double; using C = double;
                              using RS = double; using RE = double; using RC = double; };
 template <> struct Prec<3> { using S = df64;   using E = float;  using C = df64;
-                             using RS = df64;   using RE = df64;   using RC = df64; };
+                             using RS = double; using RE = double; using RC = double; };
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ uint32_t float_order_key(float f) {
