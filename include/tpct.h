@@ -185,6 +185,29 @@ tpct_status tpct_track_batch(tpct_ctx* ctx, const tpct_clusters* clusters, int64
  * n_events = 0 disables.  The events stay owned by the caller. */
 tpct_status tpct_set_stage_events(tpct_ctx* ctx, void* const* events, int n_events);
 
+/* Allocation-free variant of tpct_track (no counterpart in the paper).  For
+ * callers that cannot allocate device memory -- a plug-in that receives only
+ * its input and output buffers from a host framework that owns all device
+ * memory, a process whose memory is fully planned at start-up, or a latency-
+ * critical path where a cudaMalloc would synchronise the device -- and so
+ * cannot attach a workspace.  The scratch is a fixed 18 MiB array inside this
+ * library, held on every GPU that loads the library until the process exits;
+ * it fits ONE sector instance of at most 65536 clusters (n_instances must be
+ * 1).  Larger requests return TPCT_E_NOMEM, more instances too; contexts with
+ * more pad rows than fit return TPCT_E_NOMEM.  The caller still owns
+ * `clusters` and `out`.  The call allocates nothing (no cudaMalloc, no
+ * cudaFree) and enqueues the same kernels as tpct_track on `stream`.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * outside any stream capture.  All calls share the one array and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU (other streams,
+ * other threads, other contexts) race and corrupt each other -- serialise
+ * them.  The device status of such a call is not kept: an output overflow
+ * shows as *n_tracks > capacity_tracks or *n_ids > capacity_ids, and
+ * tpct_last_device_status / tpct_debug_export do not describe it. */
+tpct_status tpct_track_static(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n,
+                              tpct_tracks_out* out, tpct_stream stream);
+
 /* Copy intermediate arrays of the last tpct_track / tpct_track_batch call on
  * this context (enqueued on `stream`). */
 tpct_status tpct_debug_export(tpct_ctx* ctx, tpct_debug_out* dbg, tpct_stream stream);

@@ -61,6 +61,8 @@ EXPORTS = {
     "tpct_track_batch": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut),
                                  c_void_p]),
     "tpct_set_stage_events": (c_int, [c_void_p, ctypes.POINTER(c_void_p), c_int]),
+    "tpct_track_static": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut),
+                                  c_void_p]),
     "tpct_debug_export": (c_int, [c_void_p, ctypes.POINTER(DebugOut), c_void_p]),
     "tpct_last_device_status": (c_int, [c_void_p]),
     "tpct_status_str": (ctypes.c_char_p, [c_int]),

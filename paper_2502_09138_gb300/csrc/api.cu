@@ -490,3 +490,96 @@ extern "C" tpct_status tpct_probe_fma(int use_fp64, int blocks, int iters, tpct_
   cudaEventDestroy(e1);
   return check_cuda(e == cudaSuccess ? cudaGetLastError() : e);
 }
+
+// ------------------------------------------------------------------ allocation-free entry point
+// tpct_track_static: the tracking chain of tpct_track with its scratch in a
+// fixed device array of this library instead of a caller-attached workspace,
+// for callers that cannot allocate device memory.  Host code must not pass
+// g_static_ws itself to a kernel (on the host it is only a stand-in for the
+// symbol); the device address comes from cudaGetSymbolAddress, looked up once
+// per device on the first call made with that device current.
+#include <mutex>
+
+namespace {
+constexpr int64_t kStaticMaxClusters = 65536;
+constexpr int32_t kStaticMaxInstances = 1;
+constexpr size_t kStaticBytes = (size_t)18 << 20;   // 18 MiB; the plan above needs 17.6 MiB at 152 rows
+constexpr int kStaticMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_static_ws[kStaticBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+// Device address of g_static_ws on the current device (looked up once per device).
+cudaError_t static_ws_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_ws);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" tpct_status tpct_track_static(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n,
+                                         tpct_tracks_out* out, tpct_stream stream) {
+  if (!ctx || !cl || !out || n < 0) return TPCT_E_INVALID;
+  if (n > kStaticMaxClusters || cl->n_instances > kStaticMaxInstances) return TPCT_E_NOMEM;
+  if (cl->n_instances < 1 || !cl->sector_offsets) return TPCT_E_INVALID;
+  if (n > 0 && (!cl->y || !cl->z || (!cl->row && !cl->x))) return TPCT_E_INVALID;
+  if (!out->n_tracks || !out->n_ids || out->capacity_tracks < 0 || out->capacity_ids < 0) return TPCT_E_INVALID;
+  if (out->capacity_tracks > 0 && (!out->instance || !out->n_cl || !out->offset || !out->ndf ||
+                                   !out->status || !out->x_ref || !out->param || !out->cov || !out->chi2))
+    return TPCT_E_INVALID;
+  if (out->capacity_ids > 0 && !out->cluster_ids) return TPCT_E_INVALID;
+  const Plan plan_ws = make_plan(ctx->n_rows, kStaticMaxClusters, kStaticMaxInstances, 1);
+  if (carve(nullptr, plan_ws, ctx->n_rows, nullptr) > kStaticBytes) return TPCT_E_NOMEM;   // too many rows
+  void* base = nullptr;
+  cudaError_t e = static_ws_address(&base);
+  if (e != cudaSuccess) return fail_cuda(ctx, e);
+  if (ctx->tl_blocks == 0 || ctx->rf_blocks == 0) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    ctx->tl_blocks = ctx->n_sm * tracklet_blocks_per_sm((int)ctx->prec, ctx->tracklet_block);
+    ctx->rf_blocks = ctx->n_sm * refit_blocks_per_sm((int)ctx->prec, ctx->refit_block);
+  }
+  Params p{};
+  carve((char*)base, plan_ws, ctx->n_rows, &p);
+  const Plan pl = make_plan(ctx->n_rows, n, cl->n_instances, ctx->clusters_per_bin);
+  p.n_rows = ctx->n_rows;
+  p.n_inst = cl->n_instances;
+  p.n = (int32_t)n;
+  p.tcap = (int32_t)pl.tcap;
+  p.nbin_cap = (int32_t)pl.nbin;
+  p.clusters_per_bin = ctx->clusters_per_bin;
+  p.tan_half = ctx->tan_half;
+  p.z_max = ctx->z_max;
+  p.kb = kKbPerTesla * ctx->bz;
+  const tpct_cuts& c = ctx->cuts;
+  p.nf_wy = c.nf_wy; p.nf_wz = c.nf_wz; p.nf_dmax = c.nf_dmax; p.s_max = c.s_max;
+  p.edge_margin = c.edge_margin; p.search_k = c.search_k; p.chi2_max = c.chi2_max;
+  p.f_shared = c.f_shared; p.sig_readout = c.sig_readout; p.sig_cathode = c.sig_cathode;
+  p.c_s = c.c_s; p.c_t = c.c_t; p.c_qpt = c.c_qpt; p.c_yz_refit = c.c_yz_refit;
+  p.c_qpt_refit = c.c_qpt_refit; p.sig_slope = (c.sig_cathode - c.sig_readout) / ctx->z_max;
+  p.s_max_f = (float)c.s_max;
+  p.max_miss = c.max_miss; p.n_min = c.n_min; p.n_refit = c.n_refit;
+  p.x = cl->x; p.y = cl->y; p.z = cl->z; p.row = cl->row; p.inst_off = cl->sector_offsets;
+  p.out = *out;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: the status word starts at zero;
+  // every other array the chain reads is written earlier in the same chain
+  e = cudaMemsetAsync(p.status, 0, sizeof(uint32_t) * 4, s);
+  if (e != cudaSuccess) return fail_cuda(ctx, e);
+  ctx->launches += enqueue_track(ctx, p, s);
+  return fail_cuda(ctx, cudaGetLastError());
+}
