@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--frames", type=int, default=40, help="time frames of the serving leg")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-load", type=float, default=0.7, help="arrival rate / measured capacity")
     return ap.parse_args()
 
 
@@ -162,6 +166,65 @@ def cpu_baseline(ev, gpu_out, gpu_dbg, budget_s=20.0):
     return {"value": sub.n / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(idx)} of {ev.n_instances} sector instances ({sub.n} clusters), "
                       f"single-threaded FP64, {dt:.1f} s"}, rep
+
+
+def serving_leg(args, ev, G, capacity_cps):
+    """Time frames of k collisions (k uniform in [16, min(256, batch size)]) cut
+    from the batch, arriving as a Poisson process at serve_load x the measured
+    batched capacity, tracked by the serving runtime with one slot (frames one
+    after another: the plain per-frame form) and with three slots (continuous
+    batching).  Latency = submission -> results ready."""
+    import torch
+    ne, spe, offs = ev.n_events, ev.sectors_per_event, ev.sector_offsets
+    rng = np.random.default_rng(4000)
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(ev, k))).pin_memory()
+           for k in ("x", "y", "z", "charge", "row")}
+    frames = []
+    kmax = min(256, ne)
+    for _ in range(args.frames):
+        k = int(rng.integers(min(16, kmax), kmax + 1))
+        c0 = int(rng.integers(0, ne - k + 1))
+        a, b = int(offs[c0 * spe]), int(offs[(c0 + k) * spe])
+        so = torch.from_numpy((offs[c0 * spe:(c0 + k) * spe + 1] - a).astype(np.int64)).pin_memory()
+        frames.append(dict(x=pin["x"][a:b], y=pin["y"][a:b], z=pin["z"][a:b], charge=pin["charge"][a:b],
+                           row=pin["row"][a:b], sector_offsets=so, collisions=k))
+    sizes = np.array([f["y"].shape[0] for f in frames], np.float64)
+    rate = args.serve_load * capacity_cps / sizes.mean()
+    gaps = rng.exponential(1.0 / rate, len(frames))
+    arrive = np.cumsum(gaps) - gaps[0]
+    cuts = G.default_cuts(sig_readout=ev.sigma.at_readout, sig_cathode=ev.sigma.at_cathode)
+    out = {"frames": len(frames), "collisions_per_frame": [int(min(f["collisions"] for f in frames)),
+                                                           int(max(f["collisions"] for f in frames))],
+           "mean_frame_clusters": float(sizes.mean()), "arrival_rate_hz": rate, "load": args.serve_load,
+           "budget_gb": args.serve_budget_gb}
+    for slots, name in ((1, "plain_per_frame"), (3, "continuous_batching")):
+        srv = G.Server(n_slots=slots, budget_bytes=int(args.serve_budget_gb * (1 << 30)), precision=args.precision,
+                       bz=ev.bz, cuts=cuts)
+        for f in frames[:2]:                      # warm-up
+            srv.wait(srv.submit(f))
+        for tk in list(srv._frames):
+            srv.release(tk)
+        t0 = time.perf_counter()
+        tks = []
+        for f, ta in zip(frames, arrive):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tks.append(srv.submit(f))
+        for tk in tks:
+            srv.wait(tk)
+        lat = np.array([srv.poll(tk)["latency_us"] for tk in tks]) / 1e3
+        end = max(ta * 1e3 + l for ta, l in zip(arrive, lat))
+        st = srv.stats()
+        out[name] = {"slots": slots, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "sustained_clusters_per_s": float(sizes.sum() / (end * 1e-3)),
+                     "peak_in_flight": st["peak_in_flight"], "peak_gb": st["peak_bytes"] / 2 ** 30,
+                     "retries": st["retries"]}
+        for tk in tks:
+            srv.release(tk)
+        srv.close()
+        del srv
+    return out
 
 
 def run_reference(args):
@@ -367,6 +430,9 @@ def main():
         ems = b0.elapsed_time(b1) / reps
         line["e2e"] = {"value": ev.n * world / (ems * 1e-3), "unit": "clusters/s", "ms_per_step": ems,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if not args.no_serving and args.workload == "batch":
+        line["serving"] = serving_leg(args, ev, G, value / world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, par = cpu_baseline(ev, gout, gdbg)

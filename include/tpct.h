@@ -221,6 +221,76 @@ const char* tpct_status_str(tpct_status s);
 /* Text of the CUDA error behind the context's last TPCT_E_CUDA (host-owned, static). */
 const char* tpct_last_cuda_error(const tpct_ctx* ctx);
 
+/* ---------------------------------------------------------------- serving */
+/* A serving runtime: time frames (batches of sector instances) submitted from
+ * host memory are tracked concurrently in up to n_slots streams.  A frame is
+ * admitted, in arrival order, when a slot is idle and the caller's device
+ * arena has room for its inputs, workspace and outputs; inputs and workspace
+ * are returned to the arena the moment the frame finishes, so frames queued
+ * behind it start while others are still running (continuous batching).  A
+ * scheduler thread of the library does the admission.  Outputs stay in the
+ * arena until tpct_server_release.  A frame's results do not depend on what
+ * else runs: every frame has its own context, workspace and outputs. */
+typedef struct tpct_server tpct_server;
+
+typedef struct {
+  int n_slots;                 /* frames on the device at once, 1..64 (one stream + context each) */
+  void* arena;                 /* device memory budget, caller-owned, 256-byte aligned */
+  size_t arena_bytes;
+} tpct_server_config;
+
+typedef struct {
+  /* HOST pointers, caller-owned, read until the frame has finished; pinned
+   * (page-locked) memory lets the copies overlap other frames' work */
+  const float *x, *y, *z;
+  const uint16_t* charge;          /* may be NULL */
+  const uint8_t* row;              /* may be NULL (then x gives the row) */
+  const int64_t* sector_offsets;   /* [n_instances+1] */
+  int32_t n_instances;
+  int64_t n;
+} tpct_host_frame;
+
+typedef struct {
+  int32_t state;                   /* 0 queued, 1 running, 2 done, 3 failed */
+  tpct_status status;              /* of a finished or failed frame */
+  int32_t n_tracks, n_ids;         /* of a finished frame */
+  double queue_us;                 /* submit -> admission (-1 while queued) */
+  double latency_us;               /* submit -> finish observed by the scheduler (-1 before) */
+} tpct_frame_info;
+
+typedef struct {
+  /* HOST arrays, caller-owned; same layout as tpct_tracks_out */
+  int32_t capacity_tracks, capacity_ids;
+  int32_t n_tracks, n_ids;         /* written by tpct_server_fetch */
+  int32_t *instance, *n_cl, *offset, *ndf, *status;
+  double *x_ref, *param, *cov, *chi2;
+  int32_t* cluster_ids;
+} tpct_host_tracks;
+
+typedef struct {
+  int64_t submitted, completed, retries, clusters_completed;
+  int32_t queued, in_flight, peak_in_flight;
+  uint64_t bytes_in_use, peak_bytes, budget_bytes;
+} tpct_server_stats;
+
+tpct_status tpct_server_create(const tpct_geometry* geometry, double bz_tesla, const tpct_cuts* cuts,
+                               tpct_precision precision, const tpct_server_config* config,
+                               tpct_server** out);
+/* Stops the scheduler after the frames on the device finish; outstanding
+ * tickets become invalid. */
+void tpct_server_destroy(tpct_server* server);
+/* Queue a frame; TPCT_E_BUDGET if it could never fit the arena. */
+tpct_status tpct_server_submit(tpct_server* server, const tpct_host_frame* frame, uint64_t* ticket);
+tpct_status tpct_server_poll(tpct_server* server, uint64_t ticket, tpct_frame_info* info);
+/* Blocks until the frame is done or failed (TPCT_E_TIMEOUT after timeout_s seconds). */
+tpct_status tpct_server_wait(tpct_server* server, uint64_t ticket, double timeout_s);
+/* Copy a finished frame's tracks to host arrays (TPCT_E_CAPACITY if they do
+ * not fit; n_tracks and n_ids are written either way). */
+tpct_status tpct_server_fetch(tpct_server* server, uint64_t ticket, tpct_host_tracks* out);
+/* Return a finished frame's outputs to the arena and forget the ticket. */
+tpct_status tpct_server_release(tpct_server* server, uint64_t ticket);
+tpct_status tpct_server_get_stats(tpct_server* server, tpct_server_stats* out);
+
 /* ---------------------------------------------------------------- diagnostics */
 /* Launch count of this context's kernels so far (each kernel launch and each
  * graph kernel node replay counts one). */

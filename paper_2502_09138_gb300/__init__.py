@@ -241,3 +241,98 @@ def probe_fma(use_fp64, blocks, iters, stream=None):
     B.check(B.load().tpct_probe_fma(int(use_fp64), int(blocks), int(iters), ctypes.c_void_p(s.cuda_stream),
                                     ctypes.byref(ms)), "tpct_probe_fma")
     return float(ms.value)
+
+
+class Server:
+    """Serving runtime of the library (continuous batching of time frames
+    under a device-memory budget).  Frames are host arrays; the arena is one
+    torch allocation of ``budget_bytes``."""
+
+    def __init__(self, n_slots=3, budget_bytes=8 << 30, precision="mixed", bz=0.5, cuts=None, row_x=None,
+                 tan_half_sector=None, z_max=250.0, device="cuda"):
+        import math
+        L = B.load()
+        if row_x is None:
+            from synth.geometry import row_radii
+            row_x = row_radii()
+        self.row_x = np.ascontiguousarray(row_x, dtype=np.float64)
+        tan_half_sector = math.tan(math.radians(10.0)) if tan_half_sector is None else tan_half_sector
+        g = B.Geometry(int(self.row_x.shape[0]), self.row_x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       float(tan_half_sector), float(z_max))
+        self.cuts = cuts if cuts is not None else default_cuts()
+        self.device = torch.device(device)
+        self.arena = torch.empty(int(budget_bytes) + 256, dtype=torch.uint8, device=self.device)
+        base = (self.arena.data_ptr() + 255) // 256 * 256
+        cfg = B.ServerConfig(int(n_slots), ctypes.c_void_p(base), int(budget_bytes))
+        h = ctypes.c_void_p()
+        B.check(L.tpct_server_create(ctypes.byref(g), float(bz), ctypes.byref(self.cuts), B.PRECISION[precision],
+                                     ctypes.byref(cfg), ctypes.byref(h)), "tpct_server_create")
+        self._h = h
+        self._frames = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.load().tpct_server_destroy(self._h)
+            self._h = None
+            self._frames.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def host_frame(x, y, z, charge, row, sector_offsets):
+        """Pinned host copies of one frame's arrays (numpy in, torch pinned out)."""
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return dict(x=pin(x), y=pin(y), z=pin(z), charge=None if charge is None else pin(charge),
+                    row=None if row is None else pin(row), sector_offsets=pin(np.asarray(sector_offsets, np.int64)))
+
+    def submit(self, frame):
+        """frame: dict of host tensors/arrays (x, y, z, charge, row, sector_offsets); kept alive until release."""
+        p = lambda t: ctypes.c_void_p(0) if t is None else ctypes.c_void_p(
+            t.data_ptr() if hasattr(t, "data_ptr") else t.ctypes.data)
+        n = int(frame["y"].shape[0])
+        ni = int(frame["sector_offsets"].shape[0] - 1)
+        hf = B.HostFrame(p(frame["x"]), p(frame["y"]), p(frame["z"]), p(frame.get("charge")), p(frame.get("row")),
+                         p(frame["sector_offsets"]), ni, n)
+        tk = ctypes.c_uint64()
+        B.check(B.load().tpct_server_submit(self._h, ctypes.byref(hf), ctypes.byref(tk)), "tpct_server_submit")
+        self._frames[tk.value] = frame
+        return tk.value
+
+    def poll(self, ticket):
+        info = B.FrameInfo()
+        B.check(B.load().tpct_server_poll(self._h, ticket, ctypes.byref(info)), "tpct_server_poll")
+        return dict(state=info.state, status=info.status, n_tracks=info.n_tracks, n_ids=info.n_ids,
+                    queue_us=info.queue_us, latency_us=info.latency_us)
+
+    def wait(self, ticket, timeout_s=600.0):
+        B.check(B.load().tpct_server_wait(self._h, ticket, float(timeout_s)), "tpct_server_wait")
+
+    def fetch(self, ticket):
+        info = self.poll(ticket)
+        nt, ni = max(1, info["n_tracks"]), max(1, info["n_ids"])
+        arr = dict(instance=np.empty(nt, np.int32), n_cl=np.empty(nt, np.int32), offset=np.empty(nt, np.int32),
+                   ndf=np.empty(nt, np.int32), status=np.empty(nt, np.int32), x_ref=np.empty(nt),
+                   param=np.empty((nt, 5)), cov=np.empty((nt, 15)), chi2=np.empty(nt),
+                   cluster_ids=np.empty(ni, np.int32))
+        q = lambda a: ctypes.c_void_p(a.ctypes.data)
+        ht = B.HostTracks(nt, ni, 0, 0, q(arr["instance"]), q(arr["n_cl"]), q(arr["offset"]), q(arr["ndf"]),
+                          q(arr["status"]), q(arr["x_ref"]), q(arr["param"]), q(arr["cov"]), q(arr["chi2"]),
+                          q(arr["cluster_ids"]))
+        B.check(B.load().tpct_server_fetch(self._h, ticket, ctypes.byref(ht)), "tpct_server_fetch")
+        out = {k: v[:ht.n_tracks] for k, v in arr.items() if k != "cluster_ids"}
+        out["cluster_ids"] = arr["cluster_ids"][:ht.n_ids]
+        out["n_tracks"], out["n_ids"] = ht.n_tracks, ht.n_ids
+        return out
+
+    def release(self, ticket):
+        B.check(B.load().tpct_server_release(self._h, ticket), "tpct_server_release")
+        self._frames.pop(ticket, None)
+
+    def stats(self):
+        st = B.ServerStats()
+        B.check(B.load().tpct_server_get_stats(self._h, ctypes.byref(st)), "tpct_server_get_stats")
+        return {f: getattr(st, f) for f, _ in B.ServerStats._fields_}

@@ -49,6 +49,34 @@ class DebugOut(ctypes.Structure):
                 ("counters", c_void_p)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("n_slots", c_int), ("arena", c_void_p), ("arena_bytes", c_size_t)]
+
+
+class HostFrame(ctypes.Structure):
+    _fields_ = [("x", c_void_p), ("y", c_void_p), ("z", c_void_p), ("charge", c_void_p), ("row", c_void_p),
+                ("sector_offsets", c_void_p), ("n_instances", c_int32), ("n", c_int64)]
+
+
+class FrameInfo(ctypes.Structure):
+    _fields_ = [("state", c_int32), ("status", c_int), ("n_tracks", c_int32), ("n_ids", c_int32),
+                ("queue_us", c_double), ("latency_us", c_double)]
+
+
+class HostTracks(ctypes.Structure):
+    _fields_ = [("capacity_tracks", c_int32), ("capacity_ids", c_int32), ("n_tracks", c_int32),
+                ("n_ids", c_int32), ("instance", c_void_p), ("n_cl", c_void_p), ("offset", c_void_p),
+                ("ndf", c_void_p), ("status", c_void_p), ("x_ref", c_void_p), ("param", c_void_p),
+                ("cov", c_void_p), ("chi2", c_void_p), ("cluster_ids", c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("retries", c_int64),
+                ("clusters_completed", c_int64), ("queued", c_int32), ("in_flight", c_int32),
+                ("peak_in_flight", c_int32), ("bytes_in_use", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("budget_bytes", ctypes.c_uint64)]
+
+
 EXPORTS = {
     "tpct_default_cuts": (None, [ctypes.POINTER(Cuts)]),
     "tpct_create": (c_int, [ctypes.POINTER(Geometry), c_double, ctypes.POINTER(Cuts), c_int,
@@ -68,6 +96,15 @@ EXPORTS = {
     "tpct_status_str": (ctypes.c_char_p, [c_int]),
     "tpct_last_cuda_error": (ctypes.c_char_p, [c_void_p]),
     "tpct_kernel_launches": (c_int64, [c_void_p]),
+    "tpct_server_create": (c_int, [ctypes.POINTER(Geometry), c_double, ctypes.POINTER(Cuts), c_int,
+                                   ctypes.POINTER(ServerConfig), ctypes.POINTER(c_void_p)]),
+    "tpct_server_destroy": (None, [c_void_p]),
+    "tpct_server_submit": (c_int, [c_void_p, ctypes.POINTER(HostFrame), ctypes.POINTER(ctypes.c_uint64)]),
+    "tpct_server_poll": (c_int, [c_void_p, ctypes.c_uint64, ctypes.POINTER(FrameInfo)]),
+    "tpct_server_wait": (c_int, [c_void_p, ctypes.c_uint64, c_double]),
+    "tpct_server_fetch": (c_int, [c_void_p, ctypes.c_uint64, ctypes.POINTER(HostTracks)]),
+    "tpct_server_release": (c_int, [c_void_p, ctypes.c_uint64]),
+    "tpct_server_get_stats": (c_int, [c_void_p, ctypes.POINTER(ServerStats)]),
     "tpct_probe_fma": (c_int, [c_int, c_int, c_int, c_void_p, ctypes.POINTER(ctypes.c_float)]),
 }
 
