@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--tuning-cache", default=None, help="autotuner cache file (default: a fresh temp file)")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--frames", type=int, default=40, help="time frames of the serving leg")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-load", type=float, default=0.7, help="arrival rate / measured capacity")
@@ -286,6 +288,11 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
+    tuning = None
+    if not args.no_autotune:
+        import tempfile
+        cache = args.tuning_cache or os.path.join(tempfile.gettempdir(), f"tpct_tuning_{os.getpid()}.cache")
+        tuning = trk.autotune(dc, out, cache_path=cache)
     # warm-up (also builds the graph)
     for _ in range(args.warmup):
         trk.track(dc, out, batched=True)
@@ -369,7 +376,7 @@ def main():
                    "clusters_per_rank": ev.n, "sector_instances": ev.n_instances, "precision": args.precision,
                    "form": "batched (graph-captured step chain)", "l2": "inputs 0.8 GB > L2, no flush",
                    "parallelism": f"replicas x{world} (independent collisions)"},
-        "tracks_per_s": n_tracks * world / (ms * 1e-3), "tracks": n_tracks,
+        "tracks_per_s": n_tracks * world / (ms * 1e-3), "tracks": n_tracks, "tuning": tuning,
         "stage_ms": stage_ms, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
         "counters": {"helix_steps": steps, "kalman_updates": updates, "chi2_tests": tests},
     }

@@ -157,6 +157,26 @@ void tpct_destroy(tpct_ctx* ctx);
  * multiple of 32, at most 256).  0 = default. */
 tpct_status tpct_set_tuning(tpct_ctx* ctx, int clusters_per_bin, int tracklet_block, int refit_block);
 
+/* Launch shapes of a context. */
+typedef struct {
+  int clusters_per_bin, tracklet_block, refit_block;
+  int precision, n_rows;          /* of the context (read-only here) */
+  float ms;                       /* autotuner: median time of the chosen shapes */
+  int from_cache;                 /* autotuner: 1 if read from the cache file */
+} tpct_tuning;
+tpct_status tpct_get_tuning(const tpct_ctx* ctx, tpct_tuning* out);
+
+/* Autotuner: times tpct_track on the given workload for candidate launch
+ * shapes (coordinate descent over clusters per bin 1/2/4/8 and tracklet and
+ * refit blocks of 64/128/256 threads), keeps the fastest in the context and
+ * appends it to the text file cache_path (may be NULL) under a key of device
+ * name, precision, rows and the size class (log2 clusters per instance, log2
+ * instances).  A cached key is reused without timing.  Synchronises `stream`;
+ * needs an attached workspace; overwrites `out`.  The shapes never change
+ * results. */
+tpct_status tpct_autotune(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n, tpct_tracks_out* out,
+                          tpct_stream stream, const char* cache_path, tpct_tuning* result);
+
 /* ---------------------------------------------------------------- workspace */
 /* Device bytes needed to track up to max_clusters clusters in up to
  * max_instances sector instances in one call. */

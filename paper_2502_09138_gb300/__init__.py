@@ -176,6 +176,25 @@ class Tracker:
         B.check(B.load().tpct_set_tuning(self._h, clusters_per_bin, tracklet_block, refit_block),
                 "tpct_set_tuning")
 
+    def tuning(self):
+        t = B.Tuning()
+        B.check(B.load().tpct_get_tuning(self._h, ctypes.byref(t)), "tpct_get_tuning")
+        return {f: getattr(t, f) for f, _ in B.Tuning._fields_}
+
+    def autotune(self, clusters: "DeviceClusters", out: "Tracks" = None, cache_path=None, stream=None):
+        """Time candidate launch shapes on this workload, keep the fastest (cached in cache_path)."""
+        n, ni = clusters.n, clusters.n_instances
+        if self._ws is None or n > self._plan[0] or ni > self._plan[1]:
+            self.reserve(max(n, self._plan[0]), max(ni, self._plan[1]))
+        out = out if out is not None else self.make_output(n)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        t = B.Tuning()
+        cs, os_ = clusters.as_struct(), out.as_struct()
+        B.check(B.load().tpct_autotune(self._h, ctypes.byref(cs), n, ctypes.byref(os_), ctypes.c_void_p(s.cuda_stream),
+                                       cache_path.encode() if cache_path else None, ctypes.byref(t)),
+                "tpct_autotune", self._h)
+        return {f: getattr(t, f) for f, _ in B.Tuning._fields_}
+
     def workspace_bytes(self, max_clusters, max_instances):
         return int(B.load().tpct_workspace_bytes(self._h, int(max_clusters), int(max_instances)))
 

@@ -77,6 +77,11 @@ class ServerStats(ctypes.Structure):
                 ("budget_bytes", ctypes.c_uint64)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("clusters_per_bin", c_int), ("tracklet_block", c_int), ("refit_block", c_int),
+                ("precision", c_int), ("n_rows", c_int), ("ms", ctypes.c_float), ("from_cache", c_int)]
+
+
 EXPORTS = {
     "tpct_default_cuts": (None, [ctypes.POINTER(Cuts)]),
     "tpct_create": (c_int, [ctypes.POINTER(Geometry), c_double, ctypes.POINTER(Cuts), c_int,
@@ -96,6 +101,9 @@ EXPORTS = {
     "tpct_status_str": (ctypes.c_char_p, [c_int]),
     "tpct_last_cuda_error": (ctypes.c_char_p, [c_void_p]),
     "tpct_kernel_launches": (c_int64, [c_void_p]),
+    "tpct_get_tuning": (c_int, [c_void_p, ctypes.POINTER(Tuning)]),
+    "tpct_autotune": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut), c_void_p,
+                              ctypes.c_char_p, ctypes.POINTER(Tuning)]),
     "tpct_server_create": (c_int, [ctypes.POINTER(Geometry), c_double, ctypes.POINTER(Cuts), c_int,
                                    ctypes.POINTER(ServerConfig), ctypes.POINTER(c_void_p)]),
     "tpct_server_destroy": (None, [c_void_p]),

@@ -450,6 +450,18 @@ const char* tpct_status_str(tpct_status s) {
 
 int64_t tpct_kernel_launches(const tpct_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+tpct_status tpct_get_tuning(const tpct_ctx* ctx, tpct_tuning* t) {
+  if (!ctx || !t) return TPCT_E_INVALID;
+  t->clusters_per_bin = ctx->clusters_per_bin;
+  t->tracklet_block = ctx->tracklet_block;
+  t->refit_block = ctx->refit_block;
+  t->precision = (int)ctx->prec;
+  t->n_rows = ctx->n_rows;
+  t->ms = 0.f;
+  t->from_cache = 0;
+  return TPCT_OK;
+}
+
 const char* tpct_last_cuda_error(const tpct_ctx* ctx) {
   return ctx ? cudaGetErrorString(ctx->last_err) : "no context";
 }

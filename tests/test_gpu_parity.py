@@ -126,3 +126,21 @@ def test_batch_of_collisions_sampled_parity(precision):
     ores = oracle.track_event(sub)
     tr, dbg = slice_instances(ev, gtr, gdbg, idx)
     _assert_pass(compare(sub, ores, dbg, tr))
+
+
+def test_autotune_keeps_results_and_caches(event0, tmp_path):
+    import paper_2502_09138_gb300 as G
+    ref, _, _, trk = run_gpu(event0, "mixed")
+    dc = G.DeviceClusters.from_event(event0)
+    cache = str(tmp_path / "tuning.cache")
+    t1 = trk.autotune(dc, cache_path=cache)
+    assert t1["from_cache"] == 0 and t1["ms"] > 0
+    assert t1["clusters_per_bin"] in (1, 2, 4, 8) and t1["tracklet_block"] in (64, 128, 256)
+    got, _, st, _ = run_gpu(event0, "mixed", tracker=trk)
+    assert st == 0
+    for k in ("cluster_ids", "param", "cov", "chi2"):
+        assert np.array_equal(ref[k], got[k]), k
+    t2 = G.Tracker(precision="mixed", bz=event0.bz, cuts=trk.cuts).autotune(dc, cache_path=cache)
+    assert t2["from_cache"] == 1
+    assert (t2["clusters_per_bin"], t2["tracklet_block"], t2["refit_block"]) == \
+        (t1["clusters_per_bin"], t1["tracklet_block"], t1["refit_block"])
