@@ -154,23 +154,25 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
 
     const int pj = pos[j];
     const double xj = P.rx[P.srow[pj]];
-    Step<E> st;
-    if (j == n - 1) {
-      // pass start: reference = previous estimate at the outermost cluster
+    // One transport per iteration for every lane: at a pass start the
+    // reference restarts from the previous estimate at x_cur, otherwise it
+    // continues from the previous cluster.  Keeping both cases in one code
+    // path issues the FP64 transport once per warp.
+    const bool start = j == n - 1;
+    if (start) {
 #pragma unroll
       for (int i = 0; i < 5; ++i) { ref[i] = est[i]; d[i] = (S)0; }
-      if (!helix_step<E>(to_e<E>(ref[2]), to_e<E>(ref[3]), to_e<E>(ref[4]), (E)(xj - x_cur), kb, smax, st)) {
-        status = 1;
-      } else {
-        ref[0] += (S)st.dy; ref[1] += (S)st.dz; ref[2] += (S)st.ds;
+    }
+    Step<E> st;
+    if (!helix_step<E>(to_e<E>(ref[2]), to_e<E>(ref[3]), to_e<E>(ref[4]), (E)(xj - (start ? x_cur : x_prev)),
+                       kb, smax, st)) {
+      status = 1;
+    } else {
+      ref[0] += (S)st.dy; ref[1] += (S)st.dz; ref[2] += (S)st.ds;
+      if (start) {
         cov_diag<C>(m, (C)P.c_yz_refit, (C)P.c_yz_refit, (C)P.c_s, (C)P.c_t, (C)P.c_qpt_refit);
         chi2 = (C)0;
-      }
-    } else {
-      if (!helix_step<E>(to_e<E>(ref[2]), to_e<E>(ref[3]), to_e<E>(ref[4]), (E)(xj - x_prev), kb, smax, st)) {
-        status = 1;
       } else {
-        ref[0] += (S)st.dy; ref[1] += (S)st.dz; ref[2] += (S)st.ds;
         d[0] += st.j_ys * d[2] + st.j_yq * d[4];
         d[1] += st.j_zs * d[2] + st.j_zt * d[3] + st.j_zq * d[4];
         d[2] += st.j_sq * d[4];

@@ -74,17 +74,27 @@ struct Step {
 // s1 = s0 + rho dx with rho = -kb q/pT; the chord has the slope of the mean
 // direction, (s0 + s1) / (c0 + c1); its signed length L (sign of dx) spans
 // an arc L g(rho L / 2); z advances by tan(lambda) times the arc.
+template <class E> __device__ __forceinline__ E rsqrt_of(E v) { return rsqrt(v); }
+template <> __device__ __forceinline__ float rsqrt_of<float>(float v) { return rsqrtf(v); }
+__device__ __forceinline__ df64 rsqrt_of(df64 v) { return df64(1.0f) / sqrt(v); }
+
 template <class E>
 __device__ __forceinline__ bool helix_step(E s0, E tl, E qpt, E dx, E kb, E smax, Step<E>& st) {
   const E rho = -kb * qpt;
   const E ds = rho * dx;
   const E s1 = s0 + ds;
   if (!(fabs(s0) < smax && fabs(s1) < smax)) return false;
-  const E c0 = sqrt((E)1 - s0 * s0), c1 = sqrt((E)1 - s1 * s1);
+  // cos phi and tan phi from reciprocal square roots (no divisions)
+  const E u0 = (E)1 - s0 * s0, u1 = (E)1 - s1 * s1;
+  const E ir0 = rsqrt_of(u0), ir1 = rsqrt_of(u1);
+  const E c0 = u0 * ir0, c1 = u1 * ir1;
+  const E q0 = s0 * ir0, q1 = s1 * ir1;
   const E ib = (E)1 / (c0 + c1);
   const E slope = (s0 + s1) * ib;
   const E dy = dx * slope;
-  const E len = copysign(sqrt(dx * dx + dy * dy), dx);
+  const E l2 = dx * dx + dy * dy;
+  const E il = l2 > (E)0 ? rsqrt_of(l2) : (E)0;
+  const E len = copysign(l2 * il, dx);
   const E h = (E)0.5 * rho * len;
   E g, gp;
   asin_ratio(h, g, gp);
@@ -92,10 +102,11 @@ __device__ __forceinline__ bool helix_step(E s0, E tl, E qpt, E dx, E kb, E smax
   st.dy = dy;
   st.dz = tl * arc;
   st.ds = ds;
-  const E q0 = s0 / c0, q1 = s1 / c1;
   st.j_ys = dx * ((E)2 + slope * (q0 + q1)) * ib;
   st.j_yq = -kb * dx * dx * ((E)1 + slope * q1) * ib;
-  const E darc_ddy = len != (E)0 ? (g + h * gp) * dy / len : (E)0;
+  // dL/d(dy) = dy / L with the signed L, i.e. sign(dx) * dy / |L|
+  const E dy_l = dy * il;
+  const E darc_ddy = (g + h * gp) * (dx < (E)0 ? -dy_l : dy_l);
   st.j_zs = tl * darc_ddy * st.j_ys;
   st.j_zq = tl * (darc_ddy * st.j_yq - kb * (E)0.5 * len * len * gp);
   st.j_zt = arc;
