@@ -205,6 +205,9 @@ tpct_status make_params(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const
   p.c_s = c.c_s; p.c_t = c.c_t; p.c_qpt = c.c_qpt; p.c_yz_refit = c.c_yz_refit;
   p.c_qpt_refit = c.c_qpt_refit; p.sig_slope = (c.sig_cathode - c.sig_readout) / ctx->z_max;
   p.s_max_f = (float)c.s_max;
+  p.sig_readout_f = (float)c.sig_readout;
+  p.sig_slope_f = (float)p.sig_slope;
+  p.z_max_f = (float)ctx->z_max;
   p.max_miss = c.max_miss; p.n_min = c.n_min; p.n_refit = c.n_refit;
   p.x = cl->x; p.y = cl->y; p.z = cl->z; p.row = cl->row; p.inst_off = cl->sector_offsets;
   p.out = *out;
@@ -584,6 +587,9 @@ extern "C" tpct_status tpct_track_static(tpct_ctx* ctx, const tpct_clusters* cl,
   p.c_s = c.c_s; p.c_t = c.c_t; p.c_qpt = c.c_qpt; p.c_yz_refit = c.c_yz_refit;
   p.c_qpt_refit = c.c_qpt_refit; p.sig_slope = (c.sig_cathode - c.sig_readout) / ctx->z_max;
   p.s_max_f = (float)c.s_max;
+  p.sig_readout_f = (float)c.sig_readout;
+  p.sig_slope_f = (float)p.sig_slope;
+  p.z_max_f = (float)ctx->z_max;
   p.max_miss = c.max_miss; p.n_min = c.n_min; p.n_refit = c.n_refit;
   p.x = cl->x; p.y = cl->y; p.z = cl->z; p.row = cl->row; p.inst_off = cl->sector_offsets;
   p.out = *out;

@@ -44,6 +44,7 @@ struct Params {
   double nf_wy, nf_wz, nf_dmax, s_max, edge_margin, search_k, chi2_max, f_shared;
   double sig_readout, sig_cathode, c_s, c_t, c_qpt, c_yz_refit, c_qpt_refit;
   double sig_slope;            // (sig_cathode - sig_readout) / z_max
+  float sig_readout_f, sig_slope_f, z_max_f;
   int32_t max_miss, n_min, n_refit;
   // input (device, caller-owned)
   const float *x, *y, *z;
@@ -125,6 +126,19 @@ __device__ __forceinline__ T sigma_of(const Params& P, T z) {
   d = d < (T)0 ? (T)0 : d;
   d = d > (T)P.z_max ? (T)P.z_max : d;
   return (T)P.sig_readout + (T)P.sig_slope * d;
+}
+template <>
+__device__ __forceinline__ float sigma_of<float>(const Params& P, float z) {
+  float d = P.z_max_f - fabsf(z);
+  d = fminf(fmaxf(d, 0.f), P.z_max_f);
+  return P.sig_readout_f + P.sig_slope_f * d;
+}
+
+// Double-float callers take sigma in float: it enters only as the cluster
+// variance, where 1e-7 relative is far below every tolerance.
+template <>
+__device__ __forceinline__ df64 sigma_of<df64>(const Params& P, df64 z) {
+  return df64(sigma_of<float>(P, to_float(z)));
 }
 
 // Row-table access in the precision of the caller.
