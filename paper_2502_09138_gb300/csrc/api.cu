@@ -105,6 +105,9 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   q.tl_sel = (uint64_t*)take(8 * (pl.tcap + 1));
   q.tl_sel_scan = (uint64_t*)take(8 * (pl.tcap + 1));
   q.tl_cnt = (int32_t*)take(4 * 3 * (size_t)pl.tcap);
+  q.trk_est = (double*)take(8 * 5 * (size_t)pl.tcap);
+  q.trk_x = (double*)take(8 * (size_t)pl.tcap);
+  q.trk_st = (int32_t*)take(4 * (size_t)pl.tcap);
   q.trk_tl = (int32_t*)take(4 * pl.tcap);
   q.trk_pos = (int32_t*)take(4 * n);
   q.scan_tmp = (uint64_t*)take(8 * scan_tmp);
@@ -119,7 +122,8 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
     P->up = q.up; P->down = q.down; P->upc = q.upc; P->sflag = q.sflag; P->W = q.W;
     P->tl_start = q.tl_start; P->tl_ir = q.tl_ir; P->tl_nhits = q.tl_nhits; P->tl_rowref = q.tl_rowref;
     P->tl_hits = q.tl_hits; P->tl_par = q.tl_par; P->tl_sel = q.tl_sel; P->tl_sel_scan = q.tl_sel_scan;
-    P->tl_cnt = q.tl_cnt; P->trk_tl = q.trk_tl; P->trk_pos = q.trk_pos; P->scan_tmp = q.scan_tmp;
+    P->tl_cnt = q.tl_cnt; P->trk_tl = q.trk_tl;
+    P->trk_est = q.trk_est; P->trk_x = q.trk_x; P->trk_st = q.trk_st; P->trk_pos = q.trk_pos; P->scan_tmp = q.scan_tmp;
   }
   return off;
 }
@@ -253,7 +257,13 @@ int enqueue_track(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
   launch_scan_u64(P.tl_sel, P.tl_sel_scan, P.tcap, P.scan_tmp, s); k += scan_k;
   launch_emit(P, s); ++k;
   mark(5);
-  launch_refit(P, mode, ctx->refit_block, ctx->rf_blocks, s); ++k;
+  if (mode == 3 && P.n_refit >= 2) {
+    // leading passes in double-float, the last pass in double
+    launch_refit(P, mode, 1, ctx->refit_block, ctx->rf_blocks, s); ++k;
+    launch_refit(P, mode, 2, ctx->refit_block, ctx->rf_blocks, s); ++k;
+  } else {
+    launch_refit(P, mode, 0, ctx->refit_block, ctx->rf_blocks, s); ++k;
+  }
   mark(6);
   return k;
 }

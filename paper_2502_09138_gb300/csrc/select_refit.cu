@@ -101,11 +101,20 @@ __global__ void k_emit(const __grid_constant__ Params P) {
 // Persistent: every lane runs one track as a state machine, one cluster per
 // loop iteration, and takes the next track from a device work queue when it
 // finishes, so the covariance arithmetic runs with full warps.
-template <int MODE>
+template <int MODE, int STAGE> struct RefitTypes {
+  using S = typename Prec<MODE>::RS; using E = typename Prec<MODE>::RE; using C = typename Prec<MODE>::RC;
+};
+template <int MODE> struct RefitTypes<MODE, 1> {
+  using S = typename Prec<MODE>::PS; using E = typename Prec<MODE>::PE; using C = typename Prec<MODE>::PC;
+};
+
+template <int MODE, int STAGE>
 __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Params P) {
-  using S = typename Prec<MODE>::RS;
-  using E = typename Prec<MODE>::RE;
-  using C = typename Prec<MODE>::RC;
+  using S = typename RefitTypes<MODE, STAGE>::S;
+  using E = typename RefitTypes<MODE, STAGE>::E;
+  using C = typename RefitTypes<MODE, STAGE>::C;
+  const int pass_begin = STAGE == 2 ? P.n_refit - 1 : 0;
+  const int pass_end = STAGE == 1 ? P.n_refit - 1 : P.n_refit;
   const tpct_tracks_out& O = P.out;
   const uint64_t total = P.tl_sel_scan[P.tcap];
   const int n_trk = min((int)(total >> 32), O.capacity_tracks);
@@ -126,7 +135,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
     if (want) {
       const int leader = __ffs(want) - 1;
       int base = 0;
-      if (lane == leader) base = (int)atomicAdd(P.work + 1, (uint32_t)__popc(want));
+      if (lane == leader) base = (int)atomicAdd(P.work + 1 + (STAGE == 2 ? 1 : 0), (uint32_t)__popc(want));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
         const int mine = base + __popc(want & lanes_below);
@@ -139,12 +148,19 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
             n = nn;
             pos = P.trk_pos + off;
             t = P.trk_tl[k];
+            if (STAGE == 2) {
 #pragma unroll
-            for (int i = 0; i < 5; ++i) est[i] = (S)P.tl_par[(int64_t)i * P.tcap + t];
-            x_cur = P.rx[P.tl_rowref[t]];
-            pass = 0;
+              for (int i = 0; i < 5; ++i) est[i] = (S)P.trk_est[(int64_t)i * P.tcap + k];
+              x_cur = P.trk_x[k];
+              status = P.trk_st[k];
+            } else {
+#pragma unroll
+              for (int i = 0; i < 5; ++i) est[i] = (S)P.tl_par[(int64_t)i * P.tcap + t];
+              x_cur = P.rx[P.tl_rowref[t]];
+              status = 0;
+            }
+            pass = pass_begin;
             j = n - 1;
-            status = 0;
           }
         }
       }
@@ -179,7 +195,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
         cov_transport<C, E>(m, st);
       }
     }
-    bool done = status != 0;
+    bool done = status != 0 || pass >= pass_end;
     if (!done) {
       x_prev = xj;
       const C sg = sigma_of<C>(P, (C)P.sz[pj]);
@@ -189,10 +205,16 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
 #pragma unroll
         for (int i = 0; i < 5; ++i) est[i] = ref[i] + d[i];
         x_cur = P.rx[P.srow[pos[0]]];
-        if (++pass < P.n_refit) j = n - 1; else done = true;
+        if (++pass < pass_end) j = n - 1; else done = true;
       }
     }
-    if (done) {
+    if (done && STAGE == 1) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) P.trk_est[(int64_t)i * P.tcap + k] = to_double(est[i]);
+      P.trk_x[k] = x_cur;
+      P.trk_st[k] = status;
+      k = -1;
+    } else if (done) {
       O.status[k] = status;
       O.chi2[k] = status ? 0.0 : to_double(chi2);
       O.x_ref[k] = status ? P.rx[P.tl_rowref[t]] : x_cur;
@@ -263,14 +285,17 @@ void launch_own(const Params& P, cudaStream_t s) {
 void launch_emit(const Params& P, cudaStream_t s) {
   k_emit<<<blocks_for(P.tcap, kBlock), kBlock, 0, s>>>(P);
 }
-void launch_refit(const Params& P, int mode, int block, int blocks, cudaStream_t s) {
+void launch_refit(const Params& P, int mode, int stage, int block, int blocks, cudaStream_t s) {
   if (block <= 0 || block > kMaxBlock) block = 128;
   if (blocks < 1) blocks = 1;
-  switch (mode) {
-    case 0: k_refit<0><<<blocks, block, 0, s>>>(P); break;
-    case 1: k_refit<1><<<blocks, block, 0, s>>>(P); break;
-    case 2: k_refit<2><<<blocks, block, 0, s>>>(P); break;
-    default: k_refit<3><<<blocks, block, 0, s>>>(P); break;
+  switch (mode * 4 + stage) {
+    case 0: k_refit<0, 0><<<blocks, block, 0, s>>>(P); break;
+    case 4: k_refit<1, 0><<<blocks, block, 0, s>>>(P); break;
+    case 8: k_refit<2, 0><<<blocks, block, 0, s>>>(P); break;
+    case 12: k_refit<3, 0><<<blocks, block, 0, s>>>(P); break;
+    case 13: k_refit<3, 1><<<blocks, block, 0, s>>>(P); break;
+    case 14: k_refit<3, 2><<<blocks, block, 0, s>>>(P); break;
+    default: break;
   }
 }
 
@@ -278,10 +303,16 @@ int refit_blocks_per_sm(int mode, int block) {
   int nb = 0;
   cudaError_t e;
   switch (mode) {
-    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<0>, block, 0); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<1>, block, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<2>, block, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<3>, block, 0); break;
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<0, 0>, block, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<1, 0>, block, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<2, 0>, block, 0); break;
+    default: {
+      int nb1 = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<3, 2>, block, 0);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_refit<3, 1>, block, 0);
+      if (nb1 < nb) nb = nb1;
+      break;
+    }
   }
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }

@@ -85,6 +85,9 @@ struct Params {
   uint64_t* tl_sel;            // [tcap + 1]  (accepted << 32 | owned) then its exclusive scan
   uint64_t* tl_sel_scan;       // [tcap + 1]
   int32_t* tl_cnt;             // [3 * tcap] helix steps, updates, chi2 tests of each tracklet
+  double* trk_est;             // [5 * tcap] refit estimate after the leading passes (mode 3)
+  double* trk_x;               // [tcap] its x
+  int32_t* trk_st;             // [tcap] transport failure in the leading passes
   int32_t* trk_tl;             // [cap_tracks] tracklet of each output track
   int32_t* trk_pos;            // [cap_ids]    sorted position of each output cluster
   uint64_t* scan_tmp;          // block sums of the scans
@@ -100,14 +103,21 @@ struct Params {
 // the refit stays all-double: its covariance starts from a diffuse prior and
 // amplifies rounding by ~1e12, beyond what the 48-bit double-float keeps).
 template <int MODE> struct Prec;
+// PS/PE/PC: the refit passes before the last, which only move the
+// linearisation point (mode 3 runs them in double-float with float transport;
+// the last pass, which gives the estimate and the covariance, in double).
 template <> struct Prec<0> { using S = float;  using E = float;  using C = float;
-                             using RS = float;  using RE = float;  using RC = float; };
+                             using RS = float;  using RE = float;  using RC = float;
+                             using PS = float;  using PE = float;  using PC = float; };
 template <> struct Prec<1> { using S = double; using E = float;  using C = double;
-                             using RS = double; using RE = double; using RC = double; };
+                             using RS = double; using RE = double; using RC = double;
+                             using PS = double; using PE = double; using PC = double; };
 template <> struct Prec<2> { using S = double; using E = double; using C = double;
-                             using RS = double; using RE = double; using RC = double; };
+                             using RS = double; using RE = double; using RC = double;
+                             using PS = double; using PE = double; using PC = double; };
 template <> struct Prec<3> { using S = df64;   using E = float;  using C = df64;
-                             using RS = double; using RE = double; using RC = double; };
+                             using RS = double; using RE = double; using RC = double;
+                             using PS = df64;   using PE = float;  using PC = df64; };
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ uint32_t float_order_key(float f) {
@@ -179,7 +189,8 @@ int refit_blocks_per_sm(int mode, int block);
 void launch_weights(const Params& P, cudaStream_t s);
 void launch_own(const Params& P, cudaStream_t s);
 void launch_emit(const Params& P, cudaStream_t s);
-void launch_refit(const Params& P, int mode, int block, int blocks, cudaStream_t s);
+// stage 0: all refit passes; 1: all but the last (PS/PE/PC types); 2: the last
+void launch_refit(const Params& P, int mode, int stage, int block, int blocks, cudaStream_t s);
 void launch_export_links(const Params& P, const tpct_debug_out& d, cudaStream_t s);
 void launch_export_tracklets(const Params& P, const tpct_debug_out& d, cudaStream_t s);
 int kernels_per_track(void);

@@ -142,12 +142,42 @@ __device__ __forceinline__ void cov_transport(C* m, J a, J b, J c, J d, J e, J f
   m[12] = m42 + f * m44;
 }
 
+// Double-float covariance with float Jacobian entries: the same products,
+// each term a fused float x double-float multiply-add.
+__device__ __forceinline__ void cov_transport(df64* m, float a, float b, float c, float d, float e, float f) {
+  const df64 m00 = m[0], m10 = m[1], m11 = m[2], m20 = m[3], m21 = m[4], m22 = m[5];
+  const df64 m30 = m[6], m31 = m[7], m32 = m[8], m33 = m[9];
+  const df64 m40 = m[10], m41 = m[11], m42 = m[12], m43 = m[13], m44 = m[14];
+  const df64 g00 = fma_df(b, m40, fma_df(a, m20, m00));
+  const df64 g02 = fma_df(b, m42, fma_df(a, m22, m20));
+  const df64 g04 = fma_df(b, m44, fma_df(a, m42, m40));
+  const df64 g10 = fma_df(e, m40, fma_df(d, m30, fma_df(c, m20, m10)));
+  const df64 g11 = fma_df(e, m41, fma_df(d, m31, fma_df(c, m21, m11)));
+  const df64 g12 = fma_df(e, m42, fma_df(d, m32, fma_df(c, m22, m21)));
+  const df64 g13 = fma_df(e, m43, fma_df(d, m33, fma_df(c, m32, m31)));
+  const df64 g14 = fma_df(e, m44, fma_df(d, m43, fma_df(c, m42, m41)));
+  const df64 g20 = fma_df(f, m40, m20), g21 = fma_df(f, m41, m21), g22 = fma_df(f, m42, m22);
+  const df64 g23 = fma_df(f, m43, m32), g24 = fma_df(f, m44, m42);
+  m[0] = fma_df(b, g04, fma_df(a, g02, g00));
+  m[1] = fma_df(b, g14, fma_df(a, g12, g10));
+  m[2] = fma_df(e, g14, fma_df(d, g13, fma_df(c, g12, g11)));
+  m[3] = fma_df(b, g24, fma_df(a, g22, g20));
+  m[4] = fma_df(e, g24, fma_df(d, g23, fma_df(c, g22, g21)));
+  m[5] = fma_df(f, g24, g22);
+  m[6] = fma_df(b, m43, fma_df(a, m32, m30));
+  m[7] = fma_df(e, m43, fma_df(d, m33, fma_df(c, m32, m31)));
+  m[8] = fma_df(f, m43, m32);
+  m[10] = fma_df(b, m44, fma_df(a, m42, m40));
+  m[11] = fma_df(e, m44, fma_df(d, m43, fma_df(c, m42, m41)));
+  m[12] = fma_df(f, m44, m42);
+}
+
 // Jacobian entries enter as C, except for double-float C where the float
-// entries multiply directly (a cheaper mixed product).
+// entries multiply directly (the fused overload above).
 template <class C, class E>
 __device__ __forceinline__ void cov_transport(C* m, const Step<E>& st) {
   using J = typename std::conditional<is_df64<C>::value, E, C>::type;
-  cov_transport<C, J>(m, (J)st.j_ys, (J)st.j_yq, (J)st.j_zs, (J)st.j_zt, (J)st.j_zq, (J)st.j_sq);
+  cov_transport(m, (J)st.j_ys, (J)st.j_yq, (J)st.j_zs, (J)st.j_zt, (J)st.j_zq, (J)st.j_sq);
 }
 
 // chi2 of residual (r0, r1) against S = C[yz] + diag(vy, vz)
