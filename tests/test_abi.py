@@ -66,3 +66,10 @@ def test_invalid_arguments(lib):
     assert lib.tpct_set_tuning(h, 0, 33, 0) == B.TPCT_E_INVALID
     lib.tpct_destroy(h)
     assert lib.tpct_status_str(B.TPCT_E_CAPACITY) == b"output capacity exceeded"
+
+
+def test_static_scratch_fits_one_sector(lib):
+    # tpct_track_static carries a 20 MiB scratch array sized for one sector
+    # instance of 65536 clusters at 152 rows; the workspace plan must fit it
+    import paper_2502_09138_gb300 as G
+    assert G.Tracker(device="cpu").workspace_bytes(65536, 1) <= 20 << 20
