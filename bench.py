@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--tuning-cache", default=None, help="autotuner cache file (default: a fresh temp file)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--variants", default="mixed_df", help="comma-separated extra precisions timed in the same run")
     ap.add_argument("--frames", type=int, default=40, help="time frames of the serving leg")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-load", type=float, default=0.7, help="arrival rate / measured capacity")
@@ -167,7 +168,7 @@ def cpu_baseline(ev, gpu_out, gpu_dbg, budget_s=20.0):
         rep["param_max_rel_err"] = max(r["param_max_rel_err"])
     return {"value": sub.n / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(idx)} of {ev.n_instances} sector instances ({sub.n} clusters), "
-                      f"single-threaded FP64, {dt:.1f} s"}, rep
+                      f"single-threaded FP64, {dt:.1f} s"}, rep, idx
 
 
 def serving_leg(args, ev, G, capacity_cps):
@@ -227,6 +228,40 @@ def serving_leg(args, ev, G, capacity_cps):
         srv.close()
         del srv
     return out
+
+
+def _oracle_chunk(payload):
+    import oracle
+    import synth
+    y, z, row, offs, sig = payload
+    ev = synth.Event(x=None, y=y, z=z, charge=None, row=row, sector_offsets=offs, sectors=None, mc=None,
+                     sigma=synth.events.SigmaModel(*sig))
+    t0 = time.perf_counter()
+    oracle.track_event(ev)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_parallel(ev, idx, workers):
+    """The same oracle, unchanged, over the same sample split into independent
+    sector instances, on a spawn process pool of all host cores."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    chunks = np.array_split(np.asarray(idx), workers * 4)
+    payloads = []
+    for ch in chunks:
+        if len(ch) == 0:
+            continue
+        sub = ev.select_instances(ch)
+        payloads.append((sub.y, sub.z, sub.row, sub.sector_offsets,
+                         (ev.sigma.at_readout, ev.sigma.at_cathode, ev.sigma.z_max)))
+    n = sum(int(p[3][-1]) for p in payloads)
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_chunk, payloads[:workers]))          # start-up and warm-up
+        t0 = time.perf_counter()
+        list(ex.map(_oracle_chunk, payloads))
+        dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "clusters/s", "cores": workers, "kind": "oracle",
+            "sample": f"the same {len(idx)} sector instances ({n} clusters) on {workers} processes, {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -289,9 +324,9 @@ def main():
             torch.distributed.barrier()
 
     tuning = None
+    import tempfile
+    cache = args.tuning_cache or os.path.join(tempfile.gettempdir(), f"tpct_tuning_{os.getpid()}.cache")
     if not args.no_autotune:
-        import tempfile
-        cache = args.tuning_cache or os.path.join(tempfile.gettempdir(), f"tpct_tuning_{os.getpid()}.cache")
         tuning = trk.autotune(dc, out, cache_path=cache)
     # warm-up (also builds the graph)
     for _ in range(args.warmup):
@@ -438,13 +473,49 @@ def main():
         line["e2e"] = {"value": ev.n * world / (ems * 1e-3), "unit": "clusters/s", "ms_per_step": ems,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    variants = {}
+    for vp in [v for v in args.variants.split(",") if v and v != args.precision]:
+        vt = G.Tracker(precision=vp, bz=ev.bz, cuts=cuts, device=dev)
+        vt.reserve(ev.n, ev.n_instances)
+        vtun = None if args.no_autotune else vt.autotune(dc, out, cache_path=cache)
+        for _ in range(args.warmup):
+            vt.track(dc, out, batched=True)
+        torch.cuda.synchronize()
+        vev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+        for row_ in vev:
+            for e in row_:
+                e.record(stream)
+        vt.set_stage_events(vev[0])
+        vt.track(dc, out, batched=True)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for k in range(args.steps):
+            vt.set_stage_events(vev[k])
+            vt.track(dc, out, batched=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        vms = c0.elapsed_time(c1) / args.steps
+        st_v = vt.device_status()
+        variants[vp] = {"value": ev.n / (vms * 1e-3), "unit": "clusters/s", "ms_per_step": vms,
+                        "device_status": st_v, "tuning": vtun,
+                        "stage_ms": {name: statistics.mean(vev[k][i].elapsed_time(vev[k][i + 1])
+                                                           for k in range(args.steps))
+                                     for i, name in enumerate(STAGES)}}
+        vt.set_stage_events(None)
+        del vt
+    if variants:
+        line["variants"] = variants
+
     if not args.no_serving and args.workload == "batch":
         line["serving"] = serving_leg(args, ev, G, value / world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, par = cpu_baseline(ev, gout, gdbg)
+        cb, par, idx = cpu_baseline(ev, gout, gdbg)
         line["cpu_baseline"] = cb
         line["parity_on_sample"] = par
+        line["cpu_baseline_parallel"] = cpu_baseline_parallel(ev, idx, os.cpu_count() or 1)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
