@@ -144,11 +144,22 @@ __device__ __forceinline__ float sigma_of<float>(const Params& P, float z) {
   return P.sig_readout_f + P.sig_slope_f * d;
 }
 
+// Cluster variance sigma(z)^2 in float: the tracklet filter takes the
+// measurement model in float and converts it once (the FP64 covariance
+// arithmetic itself is unchanged; 1e-7 relative on a variance moves chi2 by
+// 1e-7 relative).  The refit keeps sigma in its own precision.
+__device__ __forceinline__ float cluster_var(const Params& P, float z);
+
 // Double-float callers take sigma in float: it enters only as the cluster
 // variance, where 1e-7 relative is far below every tolerance.
 template <>
 __device__ __forceinline__ df64 sigma_of<df64>(const Params& P, df64 z) {
   return df64(sigma_of<float>(P, to_float(z)));
+}
+
+__device__ __forceinline__ float cluster_var(const Params& P, float z) {
+  const float sg = sigma_of<float>(P, z);
+  return sg * sg;
 }
 
 // Row-table access in the precision of the caller.

@@ -96,12 +96,13 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
           const int r0 = ir0 % R;
           row0 = ir0 - r0;
           const int h1 = P.upc[p0];
-          const S dx = (S)(P.rx[r0 + 1] - P.rx[r0]);
-          const S dy = (S)P.sy[h1] - (S)P.sy[p0], dz = (S)P.sz[h1] - (S)P.sz[p0];
-          const S len = sqrt(dx * dx + dy * dy);
-          p[0] = (S)P.sy[p0]; p[1] = (S)P.sz[p0]; p[2] = dy / len; p[3] = dz / len; p[4] = (S)0;
-          const C sg = sigma_of<C>(P, (C)P.sz[p0]);
-          cov_diag<C>(m, sg * sg, sg * sg, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
+          // direction of the first link in float (like all transport arithmetic)
+          const float dx = P.rdxf[r0 + 1];
+          const float dy = P.sy[h1] - P.sy[p0], dz = P.sz[h1] - P.sz[p0];
+          const float il = rsqrtf(dx * dx + dy * dy);
+          p[0] = (S)P.sy[p0]; p[1] = (S)P.sz[p0]; p[2] = (S)(dy * il); p[3] = (S)(dz * il); p[4] = (S)0;
+          const C v0 = (C)cluster_var(P, P.sz[p0]);
+          cov_diag<C>(m, v0, v0, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
           hits = P.tl_hits + t;
           hits[0] = p0;
           n_up = 1;
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
     const uint32_t active = __ballot_sync(0xffffffffu, t >= 0);
     if (active == 0u) break;
     if (t < 0) continue;
+    __syncwarp(active);
 
     // ---- one row of the current pass.  Every lane with a tracklet runs the
     // same straight-line sequence (transport, candidate, test/update); the
@@ -148,10 +150,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
     __syncwarp(active);
     bool ok = false;
     if (cand >= 0) {
-      const C sg = sigma_of<C>(P, (C)P.sz[cand]);
       const C ry = (C)((S)P.sy[cand] - p[0]), rz = (C)((S)P.sz[cand] - p[1]);
       ++n_test;
-      if (kf_test_update<C, S>(p, m, ry, rz, sg * sg, chi2_max)) { ++n_upd; ok = true; }
+      if (kf_test_update<C, S>(p, m, ry, rz, (C)cluster_var(P, P.sz[cand]), chi2_max)) { ++n_upd; ok = true; }
     }
     __syncwarp(active);
     if (inside) {
@@ -187,8 +188,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
       up = false;
 #pragma unroll
       for (int i = 0; i < 5; ++i) { p[i] = top[i]; in_p[i] = top[i]; }
-      const C sg = sigma_of<C>(P, (C)P.sz[top_hit]);
-      cov_diag<C>(m, sg * sg, sg * sg, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
+      const C v0 = (C)cluster_var(P, P.sz[top_hit]);
+      cov_diag<C>(m, v0, v0, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
       j_up = n_up - 2;
       n_f = 1;
       hits[(int64_t)(R - 1) * ts] = top_hit;
