@@ -128,6 +128,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(ms, clusters, world, device=None):
+    """Whole-job numbers of a weak-scaling run: the slowest rank's time per
+    step and the clusters of all ranks (every rank tracks its own batch)."""
+    if world <= 1:
+        return float(ms), int(clusters)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([int(clusters)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -370,11 +384,7 @@ def main():
     stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
                 for i, name in enumerate(STAGES)}
     trk.set_stage_events(None)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    n_total = ev.n * world
+    ms, n_total = aggregate_ranks(ms, ev.n, world, dev)
     value = n_total / (ms * 1e-3)
     n_tracks = int(gout["n_tracks"])
 

@@ -1,0 +1,85 @@
+"""Edge cases and the full-size batch, CUDA path against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.check import compare
+from gpu_util import run_gpu, slice_instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2502_09138_gb300.build as b
+    b.build()
+
+
+def _subset(ev, keep):
+    keep = np.asarray(keep)
+    return synth.Event(ev.x[keep], ev.y[keep], ev.z[keep], ev.charge[keep], ev.row[keep],
+                       np.array([0, keep.shape[0]], np.int64), ev.sectors[:1], ev.mc[keep], sigma=ev.sigma,
+                       bz=ev.bz, sectors_per_event=1)
+
+
+def test_full_batch_sampled_parity():
+    # the 128-collision batch in the launch configuration of the benchmark
+    ev = synth.generate_config(3, workers=8)
+    gtr, gdbg, st, _ = run_gpu(ev, "mixed", batched=True, cap=(ev.n // 20 + 1024, ev.n))
+    assert st == 0
+    rng = np.random.default_rng(11)
+    sizes = np.diff(ev.sector_offsets)
+    cand = np.nonzero(sizes > 0)[0]
+    idx = np.sort(rng.choice(cand, 40, replace=False))
+    sub = ev.select_instances(idx)
+    rep = compare(sub, oracle.track_event(sub), *slice_instances(ev, gtr, gdbg, idx)[::-1])
+    assert rep["pass"], rep
+
+
+def test_exact_ties_break_by_id(event0):
+    # duplicated clusters give exactly equal D and search distances in any
+    # precision; both sides must take the smaller id, with no excusal
+    rng = np.random.default_rng(3)
+    dup = np.sort(rng.choice(event0.n, 400, replace=False))
+    keep = np.concatenate([np.arange(event0.n), dup])
+    ev = _subset(event0, keep)
+    ores = oracle.track_event(ev)
+    gtr, gdbg, st, _ = run_gpu(ev, "mixed")
+    assert st == 0
+    assert (ores.nf_margin == 0).sum() > 0          # the ties are there
+    for k in ("up", "down", "upc", "downc"):
+        assert np.array_equal(getattr(ores, k), gdbg[k]), k
+    assert np.array_equal(ores.tr_ids, gtr["cluster_ids"])
+
+
+def test_one_row_only(event0):
+    keep = np.nonzero(event0.row == 70)[0]
+    ev = _subset(event0, keep)
+    gtr, gdbg, st, _ = run_gpu(ev, "mixed")
+    assert st == 0 and gtr["n_tracks"] == 0
+    assert np.all(gdbg["up"] == -1) and np.all(gdbg["down"] == -1)
+
+
+def test_clusters_outside_acceptance(event0):
+    # far-away clusters land in the border bins; nothing may change elsewhere
+    ev = _subset(event0, np.arange(event0.n))
+    n_extra = 300
+    rng = np.random.default_rng(9)
+    rows = rng.integers(0, 152, n_extra).astype(np.uint8)
+    g = synth.default_geometry()
+    ev.x = np.concatenate([ev.x, g.row_x[rows].astype(np.float32)])
+    ev.y = np.concatenate([ev.y, rng.uniform(-400, 400, n_extra).astype(np.float32)])
+    ev.z = np.concatenate([ev.z, rng.uniform(-900, 900, n_extra).astype(np.float32)])
+    ev.row = np.concatenate([ev.row, rows])
+    ev.charge = np.concatenate([ev.charge, np.ones(n_extra, np.uint16)])
+    ev.mc = np.concatenate([ev.mc, -np.ones(n_extra, np.int32)])
+    ev.sector_offsets = np.array([0, ev.y.shape[0]], np.int64)
+    ores = oracle.track_event(ev)
+    gtr, gdbg, st, _ = run_gpu(ev, "mixed")
+    assert st == 0
+    rep = compare(ev, ores, gdbg, gtr)
+    assert rep["pass"] and rep["nf_mismatch"] == 0, rep
