@@ -28,7 +28,8 @@ __global__ void k_weights(const __grid_constant__ Params P) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tl; t += gridDim.x * blockDim.x) {
     const int nh = P.tl_nhits[t];
     const uint32_t w = tracklet_weight(P, t, nh);
-    for (int j = R - nh; j < R; ++j) atomicMax(&P.W[P.tl_hits[(int64_t)j * P.tcap + t]], w);
+    // slots from R-1 down: the lanes of a warp read the same slot (coalesced)
+    for (int j = R - 1; j >= R - nh; --j) atomicMax(&P.W[P.tl_hits[(int64_t)j * P.tcap + t]], w);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int T = P.row_tl_base[P.n_inst * R];
@@ -47,7 +48,7 @@ __global__ void k_own(const __grid_constant__ Params P) {
       const int nh = P.tl_nhits[t];
       const uint32_t w = tracklet_weight(P, t, nh);
       int own = 0;
-      for (int j = R - nh; j < R; ++j) own += P.W[P.tl_hits[(int64_t)j * P.tcap + t]] == w;
+      for (int j = R - 1; j >= R - nh; --j) own += P.W[P.tl_hits[(int64_t)j * P.tcap + t]] == w;
       const bool acc = own >= P.n_min && (double)(nh - own) <= P.f_shared * (double)nh;
       if (acc) sel = (1ull << 32) | (uint64_t)own;
     }
@@ -81,13 +82,15 @@ __global__ void k_emit(const __grid_constant__ Params P) {
     O.ndf[k] = 2 * own - 5;
     P.trk_tl[k] = t;
     if (off + own > O.capacity_ids) continue;   // ids overflow: sizes reported, refit skips it
-    int m = 0;
-    for (int j = R - nh; j < R; ++j) {
+    // owned clusters row-ascending: walk the slots from the top row down and
+    // fill the track's id range from its end
+    int m = own;
+    for (int j = R - 1; j >= R - nh; --j) {
       const int p = P.tl_hits[(int64_t)j * P.tcap + t];
       if (P.W[p] == w) {
+        --m;
         O.cluster_ids[off + m] = P.sid[p];
         P.trk_pos[off + m] = p;
-        ++m;
       }
     }
   }
