@@ -238,7 +238,9 @@ __device__ __forceinline__ bool kf_test_update(S* p, C* m, C r0, C r1, C v, C ch
 // K r are formed in float (1e-7 relative on a cut decision or on an
 // increment much smaller than the state); the gain and the covariance, whose
 // update cancels, stay double-float.
-__device__ __forceinline__ bool kf_test_update(df64* p, df64* m, df64 r0, df64 r1, df64 v, df64 chi2_max) {
+template <>
+__device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df64 r0, df64 r1, df64 v,
+                                                         df64 chi2_max) {
   const df64 s00 = m[0] + v, s01 = m[1], s11 = m[2] + v;
   const float f00 = to_float(s00), f01 = to_float(s01), f11 = to_float(s11);
   const float fr0 = to_float(r0), fr1 = to_float(r1);
