@@ -142,6 +142,24 @@ def aggregate_ranks(ms, clusters, world, device=None):
     return float(t.item()), int(c.item())
 
 
+def tracklet_traffic(helix_steps):
+    """DRAM bytes per launch of k_tracklets<1> from the committed ncu capture,
+    scaled by helix steps; None if the kernel's sources changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_tracklets_traffic.json")) as f:
+            doc = json.load(f)
+        h = hashlib.sha256()
+        for src in doc["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != doc["sources_sha256"]:
+            return None
+        return doc["dram_bytes_per_helix_step"] * helix_steps
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -401,7 +419,8 @@ def main():
         fp64_probe = 2.0 * 8 * 2048 * blocks * 256 / (pm * 1e-3) / 1e12
         ach = fp64_flops / (stage_ms["tracklets"] * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": "k_tracklets (FP64 covariance arithmetic)", "achieved": ach,
-                    "peak": fp64_probe, "unit": "TFLOP/s", "frac": ach / fp64_probe, "traffic": None,
+                    "peak": fp64_probe, "unit": "TFLOP/s", "frac": ach / fp64_probe,
+                    "traffic": tracklet_traffic(steps) if args.precision == "mixed" else None,
                     "peak_source": "FP64 FMA probe in this run (152 SMs x 2 FMA/clk nominal)",
                     "algorithmic_flops_per_launch": fp64_flops}
     else:
