@@ -84,6 +84,9 @@ def lib():
         L.orc_propagate.restype = ctypes.c_int
         L.orc_propagate.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_rotate.restype = ctypes.c_int
+        L.orc_rotate.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_kf_update.restype = ctypes.c_double
         L.orc_kf_update.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double]
@@ -209,6 +212,16 @@ def propagate(bz, s_max, x0, x1, p, want_jacobian=True):
     F = np.zeros(25) if want_jacobian else None
     rc = L.orc_propagate(bz, s_max, x0, x1, _ptr(p), _ptr(F))
     return rc, p, (F.reshape(5, 5) if F is not None else None)
+
+
+def rotate(bz, s_max, dalpha, x0, p, want_jacobian=True):
+    L = lib()
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    p1 = np.zeros(5)
+    x1 = ctypes.c_double()
+    F = np.zeros(25) if want_jacobian else None
+    rc = L.orc_rotate(bz, s_max, dalpha, x0, _ptr(p), ctypes.byref(x1), _ptr(p1), _ptr(F))
+    return rc, x1.value, p1, (F.reshape(5, 5) if F is not None else None)
 
 
 def kf_update(p, C, my, mz, vy, vz):

@@ -173,6 +173,40 @@ int orc_propagate(double bz, double s_max, double x0, double x1, double p[5], do
   return propagate_m(bz, s_max, x0, x1, p, F, NULL);
 }
 
+/* Rotation of the local frame by dalpha.  A point (x, y) becomes
+ * (x cos d + y sin d, -x sin d + y cos d) and the direction angle phi becomes
+ * phi - d.  Perturbing y at fixed x moves the point off the new plane x' =
+ * const; sliding back along the track by dl = -sin(d) dy / cos(phi') gives
+ * dy' = dy cos(phi)/cos(phi'), dz' = dz - t sin(d) dy / cos(phi'), and turns
+ * the direction by rho dl, dsin(phi') = -rho sin(d) dy.  A change of sin(phi)
+ * at a fixed point changes phi' equally: dsin(phi') = cos(phi')/cos(phi) ds. */
+int orc_rotate(double bz, double s_max, double dalpha, double x0, const double p0[5], double* x1,
+               double p1[5], double F[25]) {
+  double ca = cos(dalpha), sa = sin(dalpha);
+  double s = p0[2];
+  if (fabs(s) >= 1.0) return 1;
+  double c = sqrt(1.0 - s * s);
+  double s1 = s * ca - c * sa;          /* sin(phi - d) */
+  double c1 = c * ca + s * sa;          /* cos(phi - d) */
+  if (!(c1 > 0.0) || fabs(s1) >= s_max) return 1;
+  *x1 = x0 * ca + p0[0] * sa;
+  p1[0] = -x0 * sa + p0[0] * ca;
+  p1[1] = p0[1];
+  p1[2] = s1;
+  p1[3] = p0[3];
+  p1[4] = p0[4];
+  if (F) {
+    double rho = -KB_PER_TESLA * bz * p0[4];
+    for (int i = 0; i < 25; ++i) F[i] = 0.0;
+    for (int i = 0; i < 5; ++i) F[i * 5 + i] = 1.0;
+    F[0 * 5 + 0] = c / c1;
+    F[1 * 5 + 0] = -p0[3] * sa / c1;
+    F[2 * 5 + 0] = -rho * sa;
+    F[2 * 5 + 2] = c1 / c;
+  }
+  return 0;
+}
+
 /* C <- F C F^T */
 static void transport_cov(const double F[25], double C[25]) {
   double T[25], R[25];

@@ -89,6 +89,14 @@ const void* orc_array(const orc_result* r, int which);
  * F (row-major 5x5, may be NULL) receives d p1 / d p0.  Returns 0 on success,
  * 1 if |sin phi| reaches s_max. */
 int orc_propagate(double bz, double s_max, double x0, double x1, double p[5], double F[25]);
+/* Rotate a state at local x of one sector frame into a frame turned by dalpha
+ * (radians, new alpha minus old): position and direction exactly; the state is
+ * then at *x1 of the new frame.  F (may be NULL) receives the derivative of the
+ * new state at that plane, for perturbations that keep the track on it.
+ * Returns 0, or 1 if |sin phi| in the new frame reaches s_max or the new
+ * direction points inward. */
+int orc_rotate(double bz, double s_max, double dalpha, double x0, const double p0[5], double* x1,
+               double p1[5], double F[25]);
 /* One Kalman update with measurement (my, mz), variances (vy, vz); C is a full
  * row-major 5x5 matrix.  Returns chi2 of the residual. */
 double orc_kf_update(double p[5], double C[25], double my, double mz, double vy, double vz);
