@@ -84,6 +84,15 @@ def lib():
         L.orc_propagate.restype = ctypes.c_int
         L.orc_propagate.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_merge.restype = ctypes.c_void_p
+        L.orc_merge.argtypes = [ctypes.POINTER(_Geom), ctypes.POINTER(_Cuts), ctypes.POINTER(_MergeCuts),
+                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p]
+        L.orm_free.argtypes = [ctypes.c_void_p]
+        L.orm_count.restype = ctypes.c_int64
+        L.orm_count.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orm_array.restype = ctypes.c_void_p
+        L.orm_array.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_rotate.restype = ctypes.c_int
         L.orc_rotate.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -123,6 +132,61 @@ class Cuts:
         for k, v in over.items():
             setattr(c, k, v)
         return c
+
+
+class _MergeCuts(ctypes.Structure):
+    _fields_ = [("chi2_max", ctypes.c_double), ("max_dtanl", ctypes.c_double), ("max_gap", ctypes.c_double),
+                ("alpha0", ctypes.c_double), ("dalpha", ctypes.c_double)]
+
+
+@dataclass
+class MergeCuts:
+    """Cross-sector merging constants (stated readings)."""
+    chi2_max: float = 50.0
+    max_dtanl: float = 0.1
+    max_gap: float = 40.0
+    alpha0: float = 0.17453292519943295    # 10 degrees
+    dalpha: float = 0.3490658503988659     # 20 degrees
+
+
+(ORM_LINK_OUT, ORM_LINK_IN, ORM_MARGIN, ORM_CH_HEAD, ORM_CH_NSEG, ORM_CH_NCL, ORM_CH_OFFSET, ORM_CH_NDF,
+ ORM_CH_STATUS, ORM_CH_INST, ORM_CH_XREF, ORM_CH_CHI2, ORM_CH_MARGIN, ORM_CH_PARAM, ORM_CH_COV, ORM_CH_SEGS,
+ ORM_CH_IDS, ORM_PAIRS) = range(18)
+_ORM_DT = {ORM_MARGIN: np.float64, ORM_CH_XREF: np.float64, ORM_CH_CHI2: np.float64, ORM_CH_MARGIN: np.float64,
+           ORM_CH_PARAM: np.float64, ORM_CH_COV: np.float64, ORM_PAIRS: np.float64}
+
+
+class MergeResult:
+    """Cross-sector merging output as numpy arrays."""
+
+    def __init__(self, handle):
+        L = lib()
+        names = {ORM_LINK_OUT: "link_out", ORM_LINK_IN: "link_in", ORM_MARGIN: "margin", ORM_CH_HEAD: "ch_head",
+                 ORM_CH_NSEG: "ch_nseg", ORM_CH_NCL: "ch_ncl", ORM_CH_OFFSET: "ch_offset", ORM_CH_NDF: "ch_ndf",
+                 ORM_CH_STATUS: "ch_status", ORM_CH_INST: "ch_inst", ORM_CH_XREF: "ch_x_ref",
+                 ORM_CH_CHI2: "ch_chi2", ORM_CH_MARGIN: "ch_margin", ORM_CH_PARAM: "ch_param",
+                 ORM_CH_COV: "ch_cov", ORM_CH_SEGS: "ch_segs", ORM_CH_IDS: "ch_ids", ORM_PAIRS: "pairs"}
+        for w, name in names.items():
+            n = L.orm_count(handle, w)
+            dt = _ORM_DT.get(w, np.int32)
+            p = L.orm_array(handle, w)
+            if n <= 0 or not p:
+                arr = np.zeros(0, dt)
+            else:
+                buf = (ctypes.c_char * (n * np.dtype(dt).itemsize)).from_address(p)
+                arr = np.frombuffer(buf, dtype=dt).copy()
+            setattr(self, name, arr)
+        self.ch_param = self.ch_param.reshape(-1, 5)
+        self.ch_cov = self.ch_cov.reshape(-1, 15)
+        self.pairs = self.pairs.reshape(-1, 3)
+
+    @property
+    def n_chains(self):
+        return int(self.ch_head.shape[0])
+
+    def chain_ids(self, k):
+        o = int(self.ch_offset[k])
+        return self.ch_ids[o:o + int(self.ch_ncl[k])]
 
 
 def _ptr(a):
@@ -193,6 +257,58 @@ def track(geometry, cuts, sector_offsets, y, z, row=None, x=None, brute_force_nf
         return Result(h, int(rx.shape[0]))
     finally:
         L.orc_free(h)
+
+
+def track_merge(geometry, cuts, mcuts, sector_offsets, y, z, row, inst_sector, inst_event):
+    """Sector tracking followed by cross-sector merging; returns (Result, MergeResult)."""
+    L = lib()
+    rx = np.ascontiguousarray(geometry.row_x, dtype=np.float64)
+    g = _Geom(int(rx.shape[0]), rx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+              float(geometry.tan_half_sector), float(geometry.z_max))
+    c = _Cuts(**asdict(cuts))
+    mc = _MergeCuts(**asdict(mcuts))
+    offs = np.ascontiguousarray(sector_offsets, dtype=np.int64)
+    y64 = np.ascontiguousarray(y, dtype=np.float64)
+    z64 = np.ascontiguousarray(z, dtype=np.float64)
+    r32 = np.ascontiguousarray(row, dtype=np.int32)
+    sec = np.ascontiguousarray(inst_sector, dtype=np.int32)
+    evi = np.ascontiguousarray(inst_event, dtype=np.int32)
+    h = L.orc_track(ctypes.byref(g), ctypes.byref(c), offs.shape[0] - 1, _ptr(offs), None, _ptr(y64), _ptr(z64),
+                    _ptr(r32), 0)
+    if not h:
+        raise RuntimeError("oracle failed (invalid arguments or out of memory)")
+    try:
+        res = Result(h, int(rx.shape[0]))
+        hm = L.orc_merge(ctypes.byref(g), ctypes.byref(c), ctypes.byref(mc), h, offs.shape[0] - 1, _ptr(sec),
+                         _ptr(evi), _ptr(y64), _ptr(z64), _ptr(r32))
+        if not hm:
+            raise RuntimeError("oracle merge failed")
+        try:
+            mres = MergeResult(hm)
+        finally:
+            L.orm_free(hm)
+    finally:
+        L.orc_free(h)
+    return res, mres
+
+
+def event_instances(ev):
+    """Sector number and collision index of every instance of an Event."""
+    ni = ev.n_instances
+    sec = np.asarray(ev.sectors, dtype=np.int32)
+    evi = (np.arange(ni) // max(1, ev.sectors_per_event)).astype(np.int32)
+    return sec, evi
+
+
+def track_merge_event(ev, cuts=None, mcuts=None, geometry=None, exact=False):
+    from synth import default_geometry
+    geometry = geometry or default_geometry()
+    cuts = cuts or Cuts.for_event(ev)
+    mcuts = mcuts or MergeCuts()
+    sec, evi = event_instances(ev)
+    y = ev.y64 if exact else ev.y
+    z = ev.z64 if exact else ev.z
+    return track_merge(geometry, cuts, mcuts, ev.sector_offsets, y, z, ev.row, sec, evi)
 
 
 def track_event(ev, cuts=None, geometry=None, exact=False, **kw) -> Result:

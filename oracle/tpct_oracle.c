@@ -443,6 +443,15 @@ static void init_cov(const inst_ctx* t, double C[25], double zc) {
 }
 
 /* Refit prior: diffuse in every parameter, centred on the previous estimate. */
+static void init_cov_refit_c(const orc_cuts* c, double C[25]) {
+  for (int i = 0; i < 25; ++i) C[i] = 0.0;
+  C[0] = c->c_yz_refit;
+  C[6] = c->c_yz_refit;
+  C[12] = c->c_s;
+  C[18] = c->c_t;
+  C[24] = c->c_qpt_refit;
+}
+
 static void init_cov_refit(const inst_ctx* t, double C[25]) {
   for (int i = 0; i < 25; ++i) C[i] = 0.0;
   C[0] = t->c->c_yz_refit;
@@ -754,4 +763,370 @@ orc_result* orc_track(const orc_geometry* g, const orc_cuts* c, int64_t n_inst,
   }
   free(rows);
   return res;
+}
+
+
+/* ============================================================ cross-sector merging
+ * Reading: a particle that crosses a sector boundary leaves one track in each
+ * sector.  For tracks a, b in adjacent sectors (same side, same collision) the
+ * inner one I has the smaller radius of its reference point (ties: smaller
+ * track index).  The pair is tested if |tanl_I - tanl_O| <= max_dtanl and I's
+ * outermost and O's innermost owned clusters are within max_gap in the
+ * transverse plane.  I's refit state is transported to its outermost
+ * cluster, rotated into O's frame and transported to O's reference x; chi2 =
+ * dp^T (C_I + C_O)^-1 dp with dp the parameter difference; accepted iff chi2
+ * <= chi2_max.  Each track keeps its best outer and its best inner partner
+ * (smallest chi2, ties to the smaller track index); mutual best pairs are
+ * linked.  Linked tracks form chains, inner to outer, refitted together:
+ * the sector refit (reference trajectory, diffuse prior, 3 passes) with the
+ * reference rotated exactly and deviation and covariance rotated by the
+ * Jacobian wherever consecutive clusters lie in different sectors. */
+
+struct orc_merge_result {
+  int64_t k;
+  vec a[ORM_N_ARRAYS];
+};
+
+static const size_t orm_elem[ORM_N_ARRAYS] = {
+  [ORM_LINK_OUT] = 4, [ORM_LINK_IN] = 4, [ORM_MARGIN] = 8, [ORM_CH_HEAD] = 4, [ORM_CH_NSEG] = 4,
+  [ORM_CH_NCL] = 4, [ORM_CH_OFFSET] = 4, [ORM_CH_NDF] = 4, [ORM_CH_STATUS] = 4, [ORM_CH_INST] = 4,
+  [ORM_CH_XREF] = 8, [ORM_CH_CHI2] = 8, [ORM_CH_MARGIN] = 8, [ORM_CH_PARAM] = 8, [ORM_CH_COV] = 8,
+  [ORM_CH_SEGS] = 4, [ORM_CH_IDS] = 4, [ORM_PAIRS] = 8,
+};
+
+int64_t orm_count(const orc_merge_result* r, int w) {
+  if (!r || w < 0 || w >= ORM_N_ARRAYS) return -1;
+  return r->a[w].n;
+}
+const void* orm_array(const orc_merge_result* r, int w) {
+  if (!r || w < 0 || w >= ORM_N_ARRAYS) return NULL;
+  return r->a[w].p;
+}
+void orm_free(orc_merge_result* r) {
+  if (!r) return;
+  for (int i = 0; i < ORM_N_ARRAYS; ++i) vec_free(&r->a[i]);
+  free(r);
+}
+
+typedef struct {
+  int32_t inst, sector, n, status;
+  const int32_t* ids;
+  double alpha, x_ref, r_ref, x_out;
+  double p[5], C[25];
+  double in_x, in_y, out_x, out_y;   /* transverse positions of the innermost / outermost clusters */
+} mtrack;
+
+static double wrap_angle(double a) {
+  while (a > M_PI) a -= 2.0 * M_PI;
+  while (a <= -M_PI) a += 2.0 * M_PI;
+  return a;
+}
+
+/* Solve S x = b (5x5, plain Gaussian elimination with partial pivoting); 1 if singular */
+static int solve5(const double S_in[25], const double b_in[5], double x[5]) {
+  double A[5][6];
+  for (int i = 0; i < 5; ++i) {
+    for (int j = 0; j < 5; ++j) A[i][j] = S_in[i * 5 + j];
+    A[i][5] = b_in[i];
+  }
+  for (int col = 0; col < 5; ++col) {
+    int piv = col;
+    for (int i = col + 1; i < 5; ++i)
+      if (fabs(A[i][col]) > fabs(A[piv][col])) piv = i;
+    if (A[piv][col] == 0.0) return 1;
+    if (piv != col)
+      for (int j = 0; j < 6; ++j) { double t = A[col][j]; A[col][j] = A[piv][j]; A[piv][j] = t; }
+    for (int i = col + 1; i < 5; ++i) {
+      double f = A[i][col] / A[col][col];
+      for (int j = col; j < 6; ++j) A[i][j] -= f * A[col][j];
+    }
+  }
+  for (int i = 4; i >= 0; --i) {
+    double sum = A[i][5];
+    for (int j = i + 1; j < 5; ++j) sum -= A[i][j] * x[j];
+    x[i] = sum / A[i][i];
+  }
+  return 0;
+}
+
+/* chi2 of the pair (I inner, O outer); 1 if a transport or rotation fails */
+static int pair_chi2(const orc_cuts* c, const mtrack* I, const mtrack* O, double* chi2) {
+  double p[5], C[25], F[25], x1;
+  memcpy(p, I->p, sizeof(p));
+  memcpy(C, I->C, sizeof(C));
+  if (propagate_m(c->bz, c->s_max, I->x_ref, I->x_out, p, F, NULL)) return 1;
+  transport_cov(F, C);
+  double pr[5];
+  if (orc_rotate(c->bz, c->s_max, wrap_angle(O->alpha - I->alpha), I->x_out, p, &x1, pr, F)) return 1;
+  transport_cov(F, C);
+  if (propagate_m(c->bz, c->s_max, x1, O->x_ref, pr, F, NULL)) return 1;
+  transport_cov(F, C);
+  double S[25], dp[5], sol[5];
+  for (int i = 0; i < 25; ++i) S[i] = C[i] + O->C[i];
+  for (int i = 0; i < 5; ++i) dp[i] = pr[i] - O->p[i];
+  if (solve5(S, dp, sol)) return 1;
+  double q = 0.0;
+  for (int i = 0; i < 5; ++i) q += dp[i] * sol[i];
+  *chi2 = q;
+  return 0;
+}
+
+typedef struct { int32_t id; int seg; } mcl;
+
+/* Global refit of one chain (segments inner to outer). */
+static int chain_refit(const orc_geometry* g, const orc_cuts* c, const mtrack* T, const int32_t* segs, int m,
+                       const double* y, const double* z, const int32_t* row, const mcl* L, int n,
+                       double p_out[5], double cov_out[15], double* chi2_out, double* x_out, double* margin) {
+  const double* X = g->row_x;
+  double est[5], ref[5], d[5], C[25], F[25], chi2 = 0.0, x_cur, x1;
+  /* pass 0: reference from the outermost segment's own fit, carried within
+   * its frame to its outermost cluster */
+  const mtrack* So = &T[segs[m - 1]];
+  double ref_out[5];
+  memcpy(ref_out, So->p, sizeof(ref_out));
+  if (propagate_m(c->bz, c->s_max, So->x_ref, So->x_out, ref_out, NULL, margin)) return 1;
+  const double x_outer = So->x_out;
+  memcpy(est, T[segs[0]].p, sizeof(est));
+  x_cur = T[segs[0]].x_ref;
+  for (int pass = 0; pass < c->n_refit; ++pass) {
+    /* later passes: the estimate carried outward through the chain; if that
+     * carry fails, the previous pass's outer reference is kept */
+    if (pass > 0) {
+      double carry[5];
+      memcpy(carry, est, sizeof(carry));
+      double xf = x_cur;
+      int ok = 1;
+      for (int j = 0; j < m && ok; ++j) {
+        const mtrack* S = &T[segs[j]];
+        if (propagate_m(c->bz, c->s_max, xf, S->x_out, carry, NULL, margin)) { ok = 0; break; }
+        xf = S->x_out;
+        if (j < m - 1) {
+          double pr[5];
+          if (orc_rotate(c->bz, c->s_max, wrap_angle(T[segs[j + 1]].alpha - S->alpha), xf, carry, &x1, pr,
+                         NULL)) { ok = 0; break; }
+          memcpy(carry, pr, sizeof(carry));
+          xf = x1;
+        }
+      }
+      if (ok) memcpy(ref_out, carry, sizeof(ref_out));
+    }
+    memcpy(ref, ref_out, sizeof(ref));
+    double xf = x_outer;
+    for (int q = 0; q < 5; ++q) d[q] = 0.0;
+    init_cov_refit_c(c, C);
+    chi2 = 0.0;
+    double x_prev = xf;
+    for (int k = n - 1; k >= 0; --k) {
+      int32_t i = L[k].id;
+      double xk = X[row[i]];
+      if (k < n - 1) {
+        if (L[k].seg != L[k + 1].seg) {
+          double pr[5], R[25];
+          if (orc_rotate(c->bz, c->s_max, wrap_angle(T[segs[L[k].seg]].alpha - T[segs[L[k + 1].seg]].alpha),
+                         x_prev, ref, &x1, pr, R))
+            return 1;
+          memcpy(ref, pr, sizeof(ref));
+          double dn[5];
+          for (int a = 0; a < 5; ++a) {
+            dn[a] = 0.0;
+            for (int b = 0; b < 5; ++b) dn[a] += R[a * 5 + b] * d[b];
+          }
+          memcpy(d, dn, sizeof(d));
+          transport_cov(R, C);
+          x_prev = x1;
+        }
+        if (propagate_m(c->bz, c->s_max, x_prev, xk, ref, F, margin)) return 1;
+        double dn[5];
+        for (int a = 0; a < 5; ++a) {
+          dn[a] = 0.0;
+          for (int b = 0; b < 5; ++b) dn[a] += F[a * 5 + b] * d[b];
+        }
+        memcpy(d, dn, sizeof(d));
+        transport_cov(F, C);
+      }
+      double s = sigma_at(g, c, z[i]);
+      chi2 += orc_kf_update(d, C, y[i] - ref[0], z[i] - ref[1], s * s, s * s);
+      x_prev = xk;
+    }
+    for (int q = 0; q < 5; ++q) est[q] = ref[q] + d[q];
+    x_cur = X[row[L[0].id]];
+  }
+  memcpy(p_out, est, sizeof(est));
+  int mm = 0;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j) cov_out[mm++] = C[i * 5 + j];
+  *chi2_out = chi2;
+  *x_out = x_cur;
+  return 0;
+}
+
+#define MPUSH(res, w, val) do { __typeof__(val) v_ = (val); if (vec_push(&(res)->a[w], &v_)) goto oom; } while (0)
+
+orc_merge_result* orc_merge(const orc_geometry* g, const orc_cuts* c, const orc_merge_cuts* mc,
+                            const orc_result* tr, int64_t n_inst, const int32_t* inst_sector,
+                            const int32_t* inst_event, const double* y, const double* z, const int32_t* row) {
+  if (!g || !c || !mc || !tr || !inst_sector || !inst_event || !y || !z || !row || n_inst < 0) return NULL;
+  const int64_t K = tr->a[ORC_TR_INST].n;
+  const int32_t* tinst = (const int32_t*)tr->a[ORC_TR_INST].p;
+  const int32_t* tncl = (const int32_t*)tr->a[ORC_TR_NCL].p;
+  const int32_t* toff = (const int32_t*)tr->a[ORC_TR_OFFSET].p;
+  const int32_t* tst = (const int32_t*)tr->a[ORC_TR_STATUS].p;
+  const int32_t* tids = (const int32_t*)tr->a[ORC_TR_IDS].p;
+  const double* txr = (const double*)tr->a[ORC_TR_XREF].p;
+  const double* tpar = (const double*)tr->a[ORC_TR_PARAM].p;
+  const double* tcov = (const double*)tr->a[ORC_TR_COV].p;
+  orc_merge_result* res = (orc_merge_result*)calloc(1, sizeof(orc_merge_result));
+  if (!res) return NULL;
+  for (int i = 0; i < ORM_N_ARRAYS; ++i) vec_init(&res->a[i], orm_elem[i]);
+  res->k = K;
+  mtrack* T = (mtrack*)calloc((size_t)(K > 0 ? K : 1), sizeof(mtrack));
+  int64_t* first = (int64_t*)calloc((size_t)(n_inst + 1), sizeof(int64_t));
+  int32_t* best_out = (int32_t*)malloc(sizeof(int32_t) * (size_t)(K > 0 ? K : 1));
+  int32_t* best_in = (int32_t*)malloc(sizeof(int32_t) * (size_t)(K > 0 ? K : 1));
+  double* chi_out = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+  double* chi_in = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+  double* chi2_out2 = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+  double* chi2_in2 = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+  double* marg = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+  int32_t* inst_of = NULL;
+  mcl* L = NULL;
+  if (!T || !first || !best_out || !best_in || !chi_out || !chi_in || !chi2_out2 || !chi2_in2 || !marg) goto oom;
+  /* per track */
+  for (int64_t k = 0; k < K; ++k) {
+    mtrack* t = &T[k];
+    t->inst = tinst[k];
+    t->sector = inst_sector[t->inst];
+    t->alpha = mc->alpha0 + (double)(t->sector % 18) * mc->dalpha;
+    t->n = tncl[k];
+    t->status = tst[k];
+    t->ids = tids + toff[k];
+    t->x_ref = txr[k];
+    memcpy(t->p, tpar + 5 * k, sizeof(t->p));
+    int mm = 0;
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j <= i; ++j) { t->C[i * 5 + j] = t->C[j * 5 + i] = tcov[15 * k + mm]; ++mm; }
+    t->r_ref = sqrt(t->x_ref * t->x_ref + t->p[0] * t->p[0]);
+    int32_t a = t->ids[0], b = t->ids[t->n - 1];
+    double ca = cos(t->alpha), sa = sin(t->alpha);
+    double xa = g->row_x[row[a]], xb = g->row_x[row[b]];
+    t->in_x = xa * ca - y[a] * sa; t->in_y = xa * sa + y[a] * ca;
+    t->out_x = xb * ca - y[b] * sa; t->out_y = xb * sa + y[b] * ca;
+    t->x_out = xb;
+    best_out[k] = best_in[k] = -1;
+    chi_out[k] = chi_in[k] = chi2_out2[k] = chi2_in2[k] = INFINITY;
+    marg[k] = INFINITY;
+    first[t->inst + 1]++;
+  }
+  for (int64_t i = 0; i < n_inst; ++i) first[i + 1] += first[i];
+  /* instance of (collision, sector) */
+  int32_t n_ev = 0;
+  for (int64_t i = 0; i < n_inst; ++i) if (inst_event[i] + 1 > n_ev) n_ev = inst_event[i] + 1;
+  inst_of = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_ev > 0 ? n_ev : 1) * 36);
+  if (!inst_of) goto oom;
+  for (int64_t i = 0; i < (int64_t)n_ev * 36; ++i) inst_of[i] = -1;
+  for (int64_t i = 0; i < n_inst; ++i)
+    if (inst_sector[i] >= 0 && inst_sector[i] < 36) inst_of[(int64_t)inst_event[i] * 36 + inst_sector[i]] = (int32_t)i;
+  /* pairs over every boundary k | k+1 of each side */
+  for (int32_t e = 0; e < n_ev; ++e)
+    for (int side = 0; side < 2; ++side)
+      for (int kk = 0; kk < 18; ++kk) {
+        int32_t ia = inst_of[(int64_t)e * 36 + side * 18 + kk];
+        int32_t ib = inst_of[(int64_t)e * 36 + side * 18 + (kk + 1) % 18];
+        if (ia < 0 || ib < 0) continue;
+        for (int64_t a = first[ia]; a < first[ia + 1]; ++a)
+          for (int64_t b = first[ib]; b < first[ib + 1]; ++b) {
+            if (T[a].status || T[b].status) continue;
+            int64_t I = a, O = b;
+            if (T[b].r_ref < T[a].r_ref || (T[b].r_ref == T[a].r_ref && b < a)) { I = b; O = a; }
+            double dt = fabs(T[I].p[3] - T[O].p[3]);
+            double gx = T[I].out_x - T[O].in_x, gy = T[I].out_y - T[O].in_y;
+            double gap = sqrt(gx * gx + gy * gy);
+            double m = dmin(rel_margin(dt, mc->max_dtanl), rel_margin(gap, mc->max_gap));
+            if (dt <= mc->max_dtanl * EXT && gap <= mc->max_gap * EXT) {
+              marg[I] = dmin(marg[I], m);
+              marg[O] = dmin(marg[O], m);
+            }
+            if (!(dt <= mc->max_dtanl && gap <= mc->max_gap)) continue;
+            double chi2;
+            if (pair_chi2(c, &T[I], &T[O], &chi2)) continue;
+            double pr[3] = {(double)I, (double)O, chi2};
+            for (int q = 0; q < 3; ++q) MPUSH(res, ORM_PAIRS, pr[q]);
+            double mc2 = rel_margin(chi2, mc->chi2_max);
+            marg[I] = dmin(marg[I], mc2);
+            marg[O] = dmin(marg[O], mc2);
+            if (!(chi2 <= mc->chi2_max)) continue;
+            /* best outer partner of I, best inner partner of O (ties to the smaller index) */
+            if (chi2 < chi_out[I] || (chi2 == chi_out[I] && O < best_out[I])) {
+              chi2_out2[I] = chi_out[I]; chi_out[I] = chi2; best_out[I] = (int32_t)O;
+            } else if (chi2 < chi2_out2[I]) {
+              chi2_out2[I] = chi2;
+            }
+            if (chi2 < chi_in[O] || (chi2 == chi_in[O] && I < best_in[O])) {
+              chi2_in2[O] = chi_in[O]; chi_in[O] = chi2; best_in[O] = (int32_t)I;
+            } else if (chi2 < chi2_in2[O]) {
+              chi2_in2[O] = chi2;
+            }
+          }
+      }
+  /* links: mutual best */
+  for (int64_t k = 0; k < K; ++k) {
+    if (chi2_out2[k] < INFINITY) marg[k] = dmin(marg[k], (chi2_out2[k] - chi_out[k]) / chi2_out2[k]);
+    if (chi2_in2[k] < INFINITY) marg[k] = dmin(marg[k], (chi2_in2[k] - chi_in[k]) / chi2_in2[k]);
+  }
+  for (int64_t k = 0; k < K; ++k) {
+    int32_t o = best_out[k];
+    int32_t lo = (o >= 0 && best_in[o] == k) ? o : -1;
+    MPUSH(res, ORM_LINK_OUT, lo);
+  }
+  for (int64_t k = 0; k < K; ++k) {
+    int32_t i = best_in[k];
+    int32_t li = (i >= 0 && best_out[i] == k) ? i : -1;
+    MPUSH(res, ORM_LINK_IN, li);
+    MPUSH(res, ORM_MARGIN, marg[k]);
+  }
+  /* chains and their global refit, in order of the head track */
+  const int32_t* lout = (const int32_t*)res->a[ORM_LINK_OUT].p;
+  const int32_t* lin = (const int32_t*)res->a[ORM_LINK_IN].p;
+  int32_t segs[64];
+  for (int64_t k = 0; k < K; ++k) {
+    if (lin[k] >= 0 || lout[k] < 0) continue;
+    int m = 0, n = 0;
+    for (int64_t s2 = k; s2 >= 0 && m < 64; s2 = lout[s2]) { segs[m++] = (int32_t)s2; n += T[s2].n; }
+    free(L);
+    L = (mcl*)malloc(sizeof(mcl) * (size_t)n);
+    if (!L) goto oom;
+    int q = 0;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < T[segs[j]].n; ++i) { L[q].id = T[segs[j]].ids[i]; L[q].seg = j; ++q; }
+    double pout[5], cov[15], chi2 = 0.0, xout = 0.0, margin = INFINITY;
+    int status = chain_refit(g, c, T, segs, m, y, z, row, L, n, pout, cov, &chi2, &xout, &margin);
+    if (status) {
+      memcpy(pout, T[k].p, sizeof(pout));
+      for (int i = 0; i < 15; ++i) cov[i] = 0.0;
+      xout = T[k].x_ref;
+      chi2 = 0.0;
+    }
+    MPUSH(res, ORM_CH_HEAD, (int32_t)k);
+    MPUSH(res, ORM_CH_NSEG, (int32_t)m);
+    MPUSH(res, ORM_CH_NCL, (int32_t)n);
+    MPUSH(res, ORM_CH_OFFSET, (int32_t)res->a[ORM_CH_IDS].n);
+    MPUSH(res, ORM_CH_NDF, (int32_t)(2 * n - 5));
+    MPUSH(res, ORM_CH_STATUS, (int32_t)status);
+    MPUSH(res, ORM_CH_INST, T[k].inst);
+    MPUSH(res, ORM_CH_XREF, xout);
+    MPUSH(res, ORM_CH_CHI2, chi2);
+    MPUSH(res, ORM_CH_MARGIN, margin);
+    for (int i = 0; i < 5; ++i) MPUSH(res, ORM_CH_PARAM, pout[i]);
+    for (int i = 0; i < 15; ++i) MPUSH(res, ORM_CH_COV, cov[i]);
+    for (int j = 0; j < m; ++j) MPUSH(res, ORM_CH_SEGS, segs[j]);
+    for (int i = 0; i < n; ++i) MPUSH(res, ORM_CH_IDS, L[i].id);
+  }
+  free(T); free(first); free(best_out); free(best_in); free(chi_out); free(chi_in);
+  free(chi2_out2); free(chi2_in2); free(marg); free(inst_of); free(L);
+  return res;
+oom:
+  free(T); free(first); free(best_out); free(best_in); free(chi_out); free(chi_in);
+  free(chi2_out2); free(chi2_in2); free(marg); free(inst_of); free(L);
+  orm_free(res);
+  return NULL;
 }

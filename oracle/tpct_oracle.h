@@ -84,6 +84,39 @@ enum {
 int64_t orc_count(const orc_result* r, int which);
 const void* orc_array(const orc_result* r, int which);
 
+/* ---------------------------------------------------------------- cross-sector merging */
+typedef struct {
+  double chi2_max;         /* accept a pair iff chi2 <= chi2_max */
+  double max_dtanl;        /* consider a pair only if |tanl_a - tanl_b| <= max_dtanl ... */
+  double max_gap;          /* ... and the facing end clusters are <= max_gap apart (transverse, cm) */
+  double alpha0, dalpha;   /* sector k is centred at alpha0 + (k mod 18) dalpha [rad] */
+} orc_merge_cuts;
+
+typedef struct orc_merge_result orc_merge_result;
+
+/* Merge the sector tracks of `tracks` (from orc_track on the same clusters)
+ * across adjacent sectors of the same side and collision.  inst_sector,
+ * inst_event: sector number and collision of every instance.  row: pad row of
+ * every cluster.  Returns NULL on allocation failure or bad arguments. */
+orc_merge_result* orc_merge(const orc_geometry* g, const orc_cuts* c, const orc_merge_cuts* mc,
+                            const orc_result* tracks, int64_t n_inst, const int32_t* inst_sector,
+                            const int32_t* inst_event, const double* y, const double* z, const int32_t* row);
+void orm_free(orc_merge_result* r);
+enum {
+  ORM_LINK_OUT = 0, ORM_LINK_IN,                 /* int32 [K] partner track or -1 */
+  ORM_MARGIN,                                    /* double [K] smallest decision margin of the track */
+  ORM_CH_HEAD, ORM_CH_NSEG, ORM_CH_NCL, ORM_CH_OFFSET, ORM_CH_NDF, ORM_CH_STATUS, ORM_CH_INST, /* int32 [M] */
+  ORM_CH_XREF, ORM_CH_CHI2, ORM_CH_MARGIN,       /* double [M] */
+  ORM_CH_PARAM,                                  /* double [M*5] */
+  ORM_CH_COV,                                    /* double [M*15] */
+  ORM_CH_SEGS,                                   /* int32 [sum nseg] track indices, inner to outer */
+  ORM_CH_IDS,                                    /* int32 [sum ncl] cluster ids, inner segment first */
+  ORM_PAIRS,                                     /* double [P*3]: inner track, outer track, chi2 of tested pairs */
+  ORM_N_ARRAYS
+};
+int64_t orm_count(const orc_merge_result* r, int which);
+const void* orm_array(const orc_merge_result* r, int which);
+
 /* Stand-alone pieces, exposed for the oracle's own tests. */
 /* Exact helix transport of p = (y, z, sin phi, tan lambda, q/pT) from x0 to x1;
  * F (row-major 5x5, may be NULL) receives d p1 / d p0.  Returns 0 on success,
