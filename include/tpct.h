@@ -241,6 +241,68 @@ const char* tpct_status_str(tpct_status s);
 /* Text of the CUDA error behind the context's last TPCT_E_CUDA (host-owned, static). */
 const char* tpct_last_cuda_error(const tpct_ctx* ctx);
 
+/* ---------------------------------------------------------------- cross-sector merging */
+/* A particle crossing a sector boundary leaves one track in each sector;
+ * merging joins them and refits each chain across the sector frames (the
+ * tracking step of "TPC Processing (Tracking)", Tables 1-3, spans the whole
+ * TPC).  Reading: for tracks a, b in adjacent sectors of the same side and
+ * collision, the one whose reference point has the smaller radius is inner;
+ * a pair is tested iff |tanl_a - tanl_b| <= max_dtanl and the inner track's
+ * outermost and the outer track's innermost clusters are at most max_gap
+ * apart in the transverse plane; chi2 compares the inner track, transported
+ * to its outermost cluster, rotated into the outer frame and transported to
+ * the outer reference x, with the outer track; chi2 <= chi2_max is accepted;
+ * mutual best partners (smallest chi2, ties to the smaller index) are linked;
+ * chains are refitted in FP64 (reference-trajectory Kalman filter, 3 passes,
+ * frame rotation at each sector change). */
+typedef struct {
+  double chi2_max;            /* (50) */
+  double max_dtanl;           /* (0.1) */
+  double max_gap;             /* [cm] (40) */
+  double alpha0, dalpha;      /* sector k centred at alpha0 + (k mod 18) dalpha [rad] (10, 20 deg) */
+} tpct_merge_cuts;
+void tpct_default_merge_cuts(tpct_merge_cuts* cuts);
+
+/* Merged chains (device, caller-owned), ordered by head (innermost) track.
+ * Parameters are at the innermost cluster in the head track's sector frame. */
+typedef struct {
+  int32_t capacity_chains, capacity_ids, capacity_segs;
+  int32_t* n_chains;          /* [1] (also written on overflow) */
+  int32_t* n_ids;             /* [1] */
+  int32_t* n_segs;            /* [1] */
+  int32_t* head;              /* [M] innermost track */
+  int32_t* n_seg;             /* [M] tracks in the chain */
+  int32_t* seg_offset;        /* [M] first entry in segs */
+  int32_t* segs;              /* [capacity_segs] track indices, inner to outer */
+  int32_t* instance;          /* [M] sector instance of the head */
+  int32_t* n_cl;              /* [M] */
+  int32_t* offset;            /* [M] first entry in cluster_ids */
+  int32_t* ndf;               /* [M] */
+  int32_t* status;            /* [M] 0 = refit converged, 1 = transport or rotation failed */
+  double* x_ref;              /* [M] */
+  double* param;              /* [M*5] */
+  double* cov;                /* [M*15] */
+  double* chi2;               /* [M] */
+  int32_t* cluster_ids;       /* [capacity_ids] inner track first, rows ascending in each track */
+  int32_t* link_out;          /* [capacity of the input tracks] outer partner of every track or -1 (may be NULL) */
+  int32_t* link_in;           /* [capacity of the input tracks] inner partner or -1 (may be NULL) */
+} tpct_chains_out;
+
+/* Device workspace of tpct_merge for up to max_tracks input tracks. */
+size_t tpct_merge_workspace_bytes(int32_t max_tracks, int32_t n_instances, int32_t n_events);
+
+/* Merge the output of tpct_track / tpct_track_batch (`tracks`, on the same
+ * `clusters`; tracks ordered by instance).  inst_sector, inst_event: device
+ * [n_instances] sector number (0..35) and collision (0..n_events-1) of every
+ * instance.  Asynchronous on `stream`; an overflow of `out` shows as
+ * *n_chains > capacity_chains (or ids, segs): those counters are always
+ * written, the rows that do not fit are not.  TPCT_E_NOMEM if the workspace
+ * is smaller than tpct_merge_workspace_bytes(tracks->capacity_tracks, ...). */
+tpct_status tpct_merge(tpct_ctx* ctx, const tpct_clusters* clusters, const int32_t* inst_sector,
+                       const int32_t* inst_event, int32_t n_events, const tpct_tracks_out* tracks,
+                       const tpct_merge_cuts* cuts, void* workspace, size_t workspace_bytes,
+                       tpct_chains_out* out, tpct_stream stream);
+
 /* ---------------------------------------------------------------- serving */
 /* A serving runtime: time frames (batches of sector instances) submitted from
  * host memory are tracked concurrently in up to n_slots streams.  A frame is

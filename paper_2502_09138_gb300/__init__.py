@@ -96,6 +96,60 @@ class Tracks:
                     chi2=g(self.chi2, nt_), cluster_ids=g(self.cluster_ids, ni_))
 
 
+def default_merge_cuts(**over) -> B.MergeCuts:
+    c = B.MergeCuts()
+    B.load().tpct_default_merge_cuts(ctypes.byref(c))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+class Chains:
+    """Output buffers of tpct_merge (device tensors)."""
+
+    def __init__(self, cap_chains, cap_ids, cap_segs, cap_tracks, device):
+        i32 = dict(dtype=torch.int32, device=device)
+        f64 = dict(dtype=torch.float64, device=device)
+        self.cap = (int(cap_chains), int(cap_ids), int(cap_segs))
+        self.counts = torch.zeros(3, **i32)
+        c = max(1, cap_chains)
+        self.head = torch.empty(c, **i32)
+        self.n_seg = torch.empty(c, **i32)
+        self.seg_offset = torch.empty(c, **i32)
+        self.segs = torch.empty(max(1, cap_segs), **i32)
+        self.instance = torch.empty(c, **i32)
+        self.n_cl = torch.empty(c, **i32)
+        self.offset = torch.empty(c, **i32)
+        self.ndf = torch.empty(c, **i32)
+        self.status = torch.empty(c, **i32)
+        self.x_ref = torch.empty(c, **f64)
+        self.param = torch.empty(c, 5, **f64)
+        self.cov = torch.empty(c, 15, **f64)
+        self.chi2 = torch.empty(c, **f64)
+        self.cluster_ids = torch.empty(max(1, cap_ids), **i32)
+        self.link_out = torch.full((max(1, cap_tracks),), -1, **i32)
+        self.link_in = torch.full((max(1, cap_tracks),), -1, **i32)
+
+    def as_struct(self) -> B.ChainsOut:
+        p = self.counts.data_ptr()
+        return B.ChainsOut(self.cap[0], self.cap[1], self.cap[2], ctypes.c_void_p(p), ctypes.c_void_p(p + 4),
+                           ctypes.c_void_p(p + 8), _ptr(self.head), _ptr(self.n_seg), _ptr(self.seg_offset),
+                           _ptr(self.segs), _ptr(self.instance), _ptr(self.n_cl), _ptr(self.offset), _ptr(self.ndf),
+                           _ptr(self.status), _ptr(self.x_ref), _ptr(self.param), _ptr(self.cov), _ptr(self.chi2),
+                           _ptr(self.cluster_ids), _ptr(self.link_out), _ptr(self.link_in))
+
+    def to_host(self, n_tracks):
+        nc, ni, ns = (int(v) for v in self.counts.cpu())
+        a, b, c = min(nc, self.cap[0]), min(ni, self.cap[1]), min(ns, self.cap[2])
+        g = lambda t, k: t[:k].cpu().numpy()
+        return dict(n_chains=nc, n_ids=ni, n_segs=ns, head=g(self.head, a), n_seg=g(self.n_seg, a),
+                    seg_offset=g(self.seg_offset, a), segs=g(self.segs, c), instance=g(self.instance, a),
+                    n_cl=g(self.n_cl, a), offset=g(self.offset, a), ndf=g(self.ndf, a), status=g(self.status, a),
+                    x_ref=g(self.x_ref, a), param=g(self.param, a), cov=g(self.cov, a), chi2=g(self.chi2, a),
+                    cluster_ids=g(self.cluster_ids, b), link_out=g(self.link_out, n_tracks),
+                    link_in=g(self.link_in, n_tracks))
+
+
 class Debug:
     """Intermediate arrays for parity checks (device tensors)."""
 
@@ -226,6 +280,27 @@ class Tracker:
         fn = B.load().tpct_track_batch if batched else B.load().tpct_track
         B.check(fn(self._h, ctypes.byref(cs), n, ctypes.byref(os_), ctypes.c_void_p(s.cuda_stream)),
                 "tpct_track_batch" if batched else "tpct_track", self._h)
+        return out
+
+    def merge(self, clusters: "DeviceClusters", tracks: "Tracks", inst_sector, inst_event, n_events,
+              cuts=None, out: "Chains" = None, stream=None):
+        """Cross-sector merging of the output of track() on the same clusters."""
+        cuts = cuts or default_merge_cuts()
+        cap = tracks.capacity_tracks
+        nb = int(B.load().tpct_merge_workspace_bytes(cap, clusters.n_instances, int(n_events)))
+        if getattr(self, "_mws", None) is None or self._mws.numel() < nb + 256:
+            self._mws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        base = (self._mws.data_ptr() + 255) // 256 * 256
+        if out is None:
+            out = Chains(cap // 2 + 16, clusters.n, cap + 16, cap, self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        sec = torch.as_tensor(np.asarray(inst_sector, np.int32), device=self.device)
+        evi = torch.as_tensor(np.asarray(inst_event, np.int32), device=self.device)
+        self._keep_m = (sec, evi, out, clusters, tracks)
+        cs, ts, os_ = clusters.as_struct(), tracks.as_struct(), out.as_struct()
+        B.check(B.load().tpct_merge(self._h, ctypes.byref(cs), _ptr(sec), _ptr(evi), int(n_events), ctypes.byref(ts),
+                                    ctypes.byref(cuts), ctypes.c_void_p(base), nb, ctypes.byref(os_),
+                                    ctypes.c_void_p(s.cuda_stream)), "tpct_merge", self._h)
         return out
 
     def set_stage_events(self, events):

@@ -49,6 +49,20 @@ class DebugOut(ctypes.Structure):
                 ("counters", c_void_p)]
 
 
+class MergeCuts(ctypes.Structure):
+    _fields_ = [("chi2_max", c_double), ("max_dtanl", c_double), ("max_gap", c_double), ("alpha0", c_double),
+                ("dalpha", c_double)]
+
+
+class ChainsOut(ctypes.Structure):
+    _fields_ = [("capacity_chains", c_int32), ("capacity_ids", c_int32), ("capacity_segs", c_int32),
+                ("n_chains", c_void_p), ("n_ids", c_void_p), ("n_segs", c_void_p), ("head", c_void_p),
+                ("n_seg", c_void_p), ("seg_offset", c_void_p), ("segs", c_void_p), ("instance", c_void_p),
+                ("n_cl", c_void_p), ("offset", c_void_p), ("ndf", c_void_p), ("status", c_void_p),
+                ("x_ref", c_void_p), ("param", c_void_p), ("cov", c_void_p), ("chi2", c_void_p),
+                ("cluster_ids", c_void_p), ("link_out", c_void_p), ("link_in", c_void_p)]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("n_slots", c_int), ("arena", c_void_p), ("arena_bytes", c_size_t)]
 
@@ -101,6 +115,10 @@ EXPORTS = {
     "tpct_status_str": (ctypes.c_char_p, [c_int]),
     "tpct_last_cuda_error": (ctypes.c_char_p, [c_void_p]),
     "tpct_kernel_launches": (c_int64, [c_void_p]),
+    "tpct_default_merge_cuts": (None, [ctypes.POINTER(MergeCuts)]),
+    "tpct_merge_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
+    "tpct_merge": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_void_p, c_void_p, c_int32, ctypes.POINTER(TracksOut),
+                           ctypes.POINTER(MergeCuts), c_void_p, c_size_t, ctypes.POINTER(ChainsOut), c_void_p]),
     "tpct_get_tuning": (c_int, [c_void_p, ctypes.POINTER(Tuning)]),
     "tpct_autotune": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut), c_void_p,
                               ctypes.c_char_p, ctypes.POINTER(Tuning)]),

@@ -463,6 +463,45 @@ const char* tpct_status_str(tpct_status s) {
 
 int64_t tpct_kernel_launches(const tpct_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+void tpct_default_merge_cuts(tpct_merge_cuts* c) {
+  if (!c) return;
+  c->chi2_max = 50.0;
+  c->max_dtanl = 0.1;
+  c->max_gap = 40.0;
+  c->alpha0 = 0.17453292519943295;   // 10 degrees
+  c->dalpha = 0.3490658503988659;    // 20 degrees
+}
+
+size_t tpct_merge_workspace_bytes(int32_t max_tracks, int32_t n_instances, int32_t n_events) {
+  if (max_tracks < 1 || n_instances < 1 || n_events < 1) return 0;
+  return merge_workspace_bytes(max_tracks, n_instances, n_events);
+}
+
+tpct_status tpct_merge(tpct_ctx* ctx, const tpct_clusters* cl, const int32_t* inst_sector, const int32_t* inst_event,
+                       int32_t n_events, const tpct_tracks_out* tracks, const tpct_merge_cuts* cuts, void* ws,
+                       size_t ws_bytes, tpct_chains_out* out, tpct_stream stream) {
+  if (!ctx || !cl || !inst_sector || !inst_event || n_events < 1 || !tracks || !cuts || !ws || !out)
+    return TPCT_E_INVALID;
+  if (((uintptr_t)ws % kAlign) || cl->n_instances < 1 || (!cl->row && !cl->x) || !cl->y || !cl->z)
+    return TPCT_E_INVALID;
+  if (tracks->capacity_tracks < 1 || !tracks->n_tracks || !tracks->instance || !tracks->cluster_ids)
+    return TPCT_E_INVALID;
+  if (!out->n_chains || !out->n_ids || !out->n_segs || out->capacity_chains < 0 || out->capacity_ids < 0 ||
+      out->capacity_segs < 0)
+    return TPCT_E_INVALID;
+  if (out->capacity_chains > 0 && (!out->head || !out->n_seg || !out->seg_offset || !out->instance ||
+                                   !out->n_cl || !out->offset || !out->ndf || !out->status || !out->x_ref ||
+                                   !out->param || !out->cov || !out->chi2))
+    return TPCT_E_INVALID;
+  if ((out->capacity_ids > 0 && !out->cluster_ids) || (out->capacity_segs > 0 && !out->segs)) return TPCT_E_INVALID;
+  const int k = enqueue_merge(ctx->row_x.data(), ctx->n_rows, kKbPerTesla * ctx->bz, ctx->cuts, ctx->z_max, *cuts,
+                              *cl, inst_sector, inst_event, n_events, *tracks, ws, ws_bytes, *out,
+                              (cudaStream_t)stream);
+  if (k < 0) return TPCT_E_NOMEM;
+  ctx->launches += k;
+  return fail_cuda(ctx, cudaGetLastError());
+}
+
 tpct_status tpct_get_tuning(const tpct_ctx* ctx, tpct_tuning* t) {
   if (!ctx || !t) return TPCT_E_INVALID;
   t->clusters_per_bin = ctx->clusters_per_bin;

@@ -1,0 +1,542 @@
+// Cross-sector merging of sector tracks and the refit of merged chains.
+//
+// A particle crossing a sector boundary leaves one track in each sector
+// ("TPC Processing (Tracking)", Tables 1-3 of the paper, counts the whole
+// tracking; merging joins what sector tracking splits).  For tracks a, b in
+// adjacent sectors of the same side and collision, the inner one I has the
+// smaller radius of its reference point (ties: smaller index).  A pair is
+// tested iff |tanl_I - tanl_O| <= max_dtanl and I's outermost and O's
+// innermost owned clusters are at most max_gap apart in the transverse plane;
+// then I's refit state is transported to its outermost cluster, rotated into
+// O's frame and transported to O's reference x, and chi2 = dp^T (C_I + C_O)^-1 dp.
+// Accepted pairs (chi2 <= chi2_max) compete: every track keeps its best outer
+// and best inner partner (smallest chi2, ties to the smaller index) and
+// mutual best pairs are linked.  Linked tracks form chains, refitted together
+// in FP64 with the reference rotated at every change of sector.
+#include "track_math.cuh"
+
+namespace tpct {
+namespace {
+
+constexpr int kBlock = 256;
+
+struct MParams {
+  const double* rx;
+  int n_rows, n_inst, n_events, n_cap_tracks;
+  int32_t cap_pairs;
+  double kb, s_max, chi2_max, max_dtanl, max_gap, alpha0, dalpha;
+  double c_s, c_t, c_yz_refit, c_qpt_refit, sig_readout, sig_slope, z_max;
+  int n_refit;
+  // inputs
+  const float *x, *y, *z;
+  const uint8_t* row;
+  const int32_t *inst_sector, *inst_event;
+  tpct_tracks_out trk;
+  // workspace
+  uint32_t* status;
+  int32_t* inst_of;           // [n_events * 36]
+  int32_t *first, *last;      // [n_inst] track range of each instance
+  double *alpha, *rref, *xout, *inx, *iny, *outx, *outy;   // [cap tracks]
+  uint64_t *best_out_chi, *best_in_chi;                      // [cap tracks] order-preserving chi2 bits
+  int32_t *best_out, *best_in;                               // [cap tracks]
+  int32_t* n_pairs;                                          // [1]
+  int32_t* pair_i;                                           // [cap_pairs] inner, outer
+  int32_t* pair_o;
+  double* pair_chi;
+  int32_t *head_flag, *head_idx, *nseg, *segoff, *ncl, *cloff;   // [cap tracks + 1] per head
+  uint64_t* scan_tmp;
+  tpct_chains_out out;
+};
+
+__device__ __forceinline__ int nearest_row_m(const MParams& M, float xc) {
+  const double x = (double)xc;
+  int lo = 0, hi = M.n_rows - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (M.rx[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  if (lo > 0 && fabs(x - M.rx[lo - 1]) <= fabs(x - M.rx[lo])) lo = lo - 1;
+  return lo;
+}
+__device__ __forceinline__ int row_of(const MParams& M, int id) {
+  return M.row ? (int)M.row[id] : nearest_row_m(M, M.x[id]);
+}
+__device__ __forceinline__ int track_count(const MParams& M) {
+  return min(*M.trk.n_tracks, M.trk.capacity_tracks);
+}
+__device__ __forceinline__ double wrap_pi(double a) {
+  const double tp = 6.283185307179586;
+  while (a > 3.141592653589793) a -= tp;
+  while (a <= -3.141592653589793) a += tp;
+  return a;
+}
+
+// Rotation of the sector frame by d (new alpha - old alpha).  Position and
+// direction rotate exactly; a perturbation of y at fixed x slides back onto
+// the new plane along the track (dl = -sin d dy / cos phi'), which scales y by
+// cos phi / cos phi', moves z by -t sin d / cos phi' and turns the direction
+// by rho dl; a change of sin phi at a fixed point changes sin phi' by
+// cos phi' / cos phi.
+struct Rot {
+  double jyy, jzy, jsy, jss;
+};
+__device__ __forceinline__ bool rotate_state(double d, double kb, double smax, double x0, double* p, double* x1,
+                                             Rot* J) {
+  double sd, cd;
+  sincos(d, &sd, &cd);
+  const double s = p[2];
+  if (!(fabs(s) < 1.0)) return false;
+  const double c = sqrt(1.0 - s * s);
+  const double s1 = s * cd - c * sd, c1 = c * cd + s * sd;
+  if (!(c1 > 0.0) || !(fabs(s1) < smax)) return false;
+  *x1 = x0 * cd + p[0] * sd;
+  const double y1 = -x0 * sd + p[0] * cd;
+  if (J) {
+    const double rho = -kb * p[4];
+    J->jyy = c / c1;
+    J->jzy = -p[3] * sd / c1;
+    J->jsy = -rho * sd;
+    J->jss = c1 / c;
+  }
+  p[0] = y1;
+  p[2] = s1;
+  return true;
+}
+
+// C <- J C J^T for the rotation Jacobian (rows y, z, s change).
+__device__ __forceinline__ void cov_rotate(double* m, const Rot& J) {
+  // full symmetric 5x5 from the packed lower triangle
+  double C[5][5];
+  int idx = 0;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j, ++idx) C[i][j] = C[j][i] = m[idx];
+  double A[5][5];   // J C
+  for (int j = 0; j < 5; ++j) {
+    A[0][j] = J.jyy * C[0][j];
+    A[1][j] = J.jzy * C[0][j] + C[1][j];
+    A[2][j] = J.jsy * C[0][j] + J.jss * C[2][j];
+    A[3][j] = C[3][j];
+    A[4][j] = C[4][j];
+  }
+  double B[5][5];   // (J C) J^T
+  for (int i = 0; i < 5; ++i) {
+    B[i][0] = A[i][0] * J.jyy;
+    B[i][1] = A[i][0] * J.jzy + A[i][1];
+    B[i][2] = A[i][0] * J.jsy + A[i][2] * J.jss;
+    B[i][3] = A[i][3];
+    B[i][4] = A[i][4];
+  }
+  idx = 0;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] = B[i][j];
+}
+
+// chi2 = dp^T S^-1 dp for symmetric positive S (packed), by Cholesky.
+__device__ __forceinline__ bool chi2_packed(const double* S, const double* dp, double* chi2) {
+  double L[15];
+  int idx = 0;
+  for (int i = 0; i < 5; ++i) {
+    for (int j = 0; j <= i; ++j, ++idx) {
+      double sum = S[idx];
+      for (int k = 0; k < j; ++k) sum -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+      if (i == j) {
+        if (!(sum > 0.0)) return false;
+        L[idx] = sqrt(sum);
+      } else {
+        L[idx] = sum / L[j * (j + 1) / 2 + j];
+      }
+    }
+  }
+  double w[5];
+  double q = 0.0;
+  for (int i = 0; i < 5; ++i) {
+    double sum = dp[i];
+    for (int k = 0; k < i; ++k) sum -= L[i * (i + 1) / 2 + k] * w[k];
+    w[i] = sum / L[i * (i + 1) / 2 + i];
+    q += w[i] * w[i];
+  }
+  *chi2 = q;
+  return true;
+}
+
+__device__ __forceinline__ void load_track(const MParams& M, int k, double* p, double* C) {
+  for (int i = 0; i < 5; ++i) p[i] = M.trk.param[(int64_t)k * 5 + i];
+  for (int i = 0; i < 15; ++i) C[i] = M.trk.cov[(int64_t)k * 15 + i];
+}
+
+__device__ __forceinline__ bool transport(const MParams& M, double x0, double x1, double* p, double* C) {
+  Step<double> st;
+  if (!helix_step<double>(p[2], p[3], p[4], x1 - x0, M.kb, M.s_max, st)) return false;
+  p[0] += st.dy; p[1] += st.dz; p[2] += st.ds;
+  if (C) cov_transport<double, double>(C, st);
+  return true;
+}
+
+// ------------------------------------------------------------------ kernels
+struct RowTab {
+  double x[kMaxRows];
+};
+__global__ void k_m_rows(double* rx, int n, const RowTab tab) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rx[i] = tab.x[i];
+}
+
+__global__ void k_m_init(const __grid_constant__ MParams M) {
+  const int nt = M.n_cap_tracks;
+  const int ni = M.n_events * 36;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(max(nt, ni), M.n_inst) + 1;
+       i += gridDim.x * blockDim.x) {
+    if (i < ni) M.inst_of[i] = -1;
+    if (i < M.n_inst) { M.first[i] = 0; M.last[i] = 0; }
+    if (i < nt) {
+      M.best_out_chi[i] = ~0ull; M.best_in_chi[i] = ~0ull;
+      M.best_out[i] = 0x7fffffff; M.best_in[i] = 0x7fffffff;
+      M.head_flag[i] = 0; M.nseg[i] = 0; M.ncl[i] = 0;
+    }
+    if (i == 0) *M.n_pairs = 0;
+  }
+}
+
+__global__ void k_m_prep(const __grid_constant__ MParams M) {
+  const int n = track_count(M);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M.n_inst; i += gridDim.x * blockDim.x) {
+    const int s = M.inst_sector[i], e = M.inst_event[i];
+    if (s >= 0 && s < 36 && e >= 0 && e < M.n_events) M.inst_of[e * 36 + s] = i;
+  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int inst = M.trk.instance[k];
+    if (k == 0 || M.trk.instance[k - 1] != inst) M.first[inst] = k;
+    if (k == n - 1 || M.trk.instance[k + 1] != inst) M.last[inst] = k + 1;
+    const double al = M.alpha0 + (double)(M.inst_sector[inst] % 18) * M.dalpha;
+    M.alpha[k] = al;
+    const double xr = M.trk.x_ref[k], yr = M.trk.param[(int64_t)k * 5];
+    M.rref[k] = sqrt(xr * xr + yr * yr);
+    const int off = M.trk.offset[k], ncl = M.trk.n_cl[k];
+    const int a = M.trk.cluster_ids[off], b = M.trk.cluster_ids[off + ncl - 1];
+    double sa, ca;
+    sincos(al, &sa, &ca);
+    const double xa = M.rx[row_of(M, a)], xb = M.rx[row_of(M, b)];
+    const double ya = (double)M.y[a], yb = (double)M.y[b];
+    M.inx[k] = xa * ca - ya * sa; M.iny[k] = xa * sa + ya * ca;
+    M.outx[k] = xb * ca - yb * sa; M.outy[k] = xb * sa + yb * ca;
+    M.xout[k] = xb;
+  }
+}
+
+// One block per boundary (collision, side, sector k | k+1).
+__global__ void k_m_pairs(const __grid_constant__ MParams M) {
+  const int b = blockIdx.x;
+  const int e = b / 36, side = (b / 18) % 2, kk = b % 18;
+  if (e >= M.n_events) return;
+  const int ia = M.inst_of[e * 36 + side * 18 + kk];
+  const int ib = M.inst_of[e * 36 + side * 18 + (kk + 1) % 18];
+  if (ia < 0 || ib < 0) return;
+  const int a0 = M.first[ia], na = M.last[ia] - a0;
+  const int b0 = M.first[ib], nb = M.last[ib] - b0;
+  if (na <= 0 || nb <= 0) return;
+  for (int64_t q = threadIdx.x; q < (int64_t)na * nb; q += blockDim.x) {
+    const int a = a0 + (int)(q / nb), bb = b0 + (int)(q % nb);
+    if (M.trk.status[a] || M.trk.status[bb]) continue;
+    int I = a, O = bb;
+    if (M.rref[bb] < M.rref[a] || (M.rref[bb] == M.rref[a] && bb < a)) { I = bb; O = a; }
+    const double dt = fabs(M.trk.param[(int64_t)I * 5 + 3] - M.trk.param[(int64_t)O * 5 + 3]);
+    const double gx = M.outx[I] - M.inx[O], gy = M.outy[I] - M.iny[O];
+    if (!(dt <= M.max_dtanl && sqrt(gx * gx + gy * gy) <= M.max_gap)) continue;
+    double p[5], C[15];
+    load_track(M, I, p, C);
+    if (!transport(M, M.trk.x_ref[I], M.xout[I], p, C)) continue;
+    double x1;
+    Rot J;
+    if (!rotate_state(wrap_pi(M.alpha[O] - M.alpha[I]), M.kb, M.s_max, M.xout[I], p, &x1, &J)) continue;
+    cov_rotate(C, J);
+    if (!transport(M, x1, M.trk.x_ref[O], p, C)) continue;
+    double dp[5], S[15];
+    for (int i = 0; i < 5; ++i) dp[i] = p[i] - M.trk.param[(int64_t)O * 5 + i];
+    for (int i = 0; i < 15; ++i) S[i] = C[i] + M.trk.cov[(int64_t)O * 15 + i];
+    double chi2;
+    if (!chi2_packed(S, dp, &chi2) || !(chi2 <= M.chi2_max)) continue;
+    const int slot = atomicAdd(M.n_pairs, 1);
+    if (slot >= M.cap_pairs) { atomicOr(M.status, kDevCapacity); continue; }
+    M.pair_i[slot] = I; M.pair_o[slot] = O; M.pair_chi[slot] = chi2;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(chi2);   // chi2 >= 0: bits order like values
+    atomicMin((unsigned long long*)&M.best_out_chi[I], bits);
+    atomicMin((unsigned long long*)&M.best_in_chi[O], bits);
+  }
+}
+
+__global__ void k_m_best(const __grid_constant__ MParams M) {
+  const int np = min(*M.n_pairs, M.cap_pairs);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
+    const int I = M.pair_i[q], O = M.pair_o[q];
+    const uint64_t bits = (uint64_t)__double_as_longlong(M.pair_chi[q]);
+    if (bits == M.best_out_chi[I]) atomicMin(&M.best_out[I], O);
+    if (bits == M.best_in_chi[O]) atomicMin(&M.best_in[O], I);
+  }
+}
+
+// links, chain heads (no inner link, an outer link), segments and clusters per chain
+__global__ void k_m_links(const __grid_constant__ MParams M) {
+  const int n = track_count(M);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int o = M.best_out[k], i = M.best_in[k];
+    const int lo = (o != 0x7fffffff && M.best_in[o] == k) ? o : -1;
+    const int li = (i != 0x7fffffff && M.best_out[i] == k) ? i : -1;
+    if (M.out.link_out) M.out.link_out[k] = lo;
+    if (M.out.link_in) M.out.link_in[k] = li;
+  }
+}
+
+__device__ __forceinline__ int link_out_of(const MParams& M, int k) {
+  const int o = M.best_out[k];
+  return (o != 0x7fffffff && M.best_in[o] == k) ? o : -1;
+}
+__device__ __forceinline__ int link_in_of(const MParams& M, int k) {
+  const int i = M.best_in[k];
+  return (i != 0x7fffffff && M.best_out[i] == k) ? i : -1;
+}
+
+__global__ void k_m_heads(const __grid_constant__ MParams M) {
+  const int n = track_count(M);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M.n_cap_tracks; k += gridDim.x * blockDim.x) {
+    int flag = 0, segs = 0, cls = 0;
+    if (k < n && link_in_of(M, k) < 0 && link_out_of(M, k) >= 0) {
+      flag = 1;
+      for (int s = k; s >= 0 && segs < 64; s = link_out_of(M, s)) { ++segs; cls += M.trk.n_cl[s]; }
+    }
+    M.head_flag[k] = flag;
+    M.nseg[k] = segs;
+    M.ncl[k] = cls;
+  }
+}
+
+__global__ void k_m_emit(const __grid_constant__ MParams M) {
+  const int n = track_count(M);
+  const tpct_chains_out& O = M.out;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int nc = M.head_idx[M.n_cap_tracks], ni = M.cloff[M.n_cap_tracks], ns = M.segoff[M.n_cap_tracks];
+    *O.n_chains = nc;
+    *O.n_ids = ni;
+    *O.n_segs = ns;
+    if (nc > O.capacity_chains || ni > O.capacity_ids || ns > O.capacity_segs) atomicOr(M.status, kDevCapacity);
+  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    if (!M.head_flag[k]) continue;
+    const int c = M.head_idx[k], off = M.cloff[k], so = M.segoff[k];
+    if (c >= O.capacity_chains) continue;
+    O.head[c] = k;
+    O.n_seg[c] = M.nseg[k];
+    O.seg_offset[c] = so;
+    O.n_cl[c] = M.ncl[k];
+    O.offset[c] = off;
+    O.ndf[c] = 2 * M.ncl[k] - 5;
+    O.instance[c] = M.trk.instance[k];
+    if (off + M.ncl[k] > O.capacity_ids || so + M.nseg[k] > O.capacity_segs) continue;
+    int q = off, j = so;
+    for (int s = k; s >= 0 && j < so + M.nseg[k]; s = link_out_of(M, s)) {
+      O.segs[j++] = s;
+      const int to = M.trk.offset[s];
+      for (int i = 0; i < M.trk.n_cl[s]; ++i) O.cluster_ids[q++] = M.trk.cluster_ids[to + i];
+    }
+  }
+}
+
+// Chain refit (FP64): reference-trajectory Kalman filter over all clusters of
+// the chain, outermost to innermost, 3 passes; pass 0 takes its reference
+// from the outermost segment's own fit carried to its outermost cluster;
+// later passes carry the previous estimate outward through the chain (kept
+// from the previous pass if that carry fails).
+__global__ void __launch_bounds__(128) k_m_refit(const __grid_constant__ MParams M) {
+  const tpct_chains_out& O = M.out;
+  const int nc = min(M.head_idx[M.n_cap_tracks], O.capacity_chains);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+    const int m = O.n_seg[c], n = O.n_cl[c], off = O.offset[c], so = O.seg_offset[c];
+    if (off + n > O.capacity_ids || so + m > O.capacity_segs) continue;
+    const int* segs = O.segs + so;
+    const int* ids = O.cluster_ids + off;
+    int status = 0;
+    double est[5], ref[5], ref_out[5], d[5], C[15], chi2 = 0.0;
+    const int so_t = segs[m - 1];
+    for (int i = 0; i < 5; ++i) ref_out[i] = M.trk.param[(int64_t)so_t * 5 + i];
+    const double x_outer = M.xout[so_t];
+    if (!transport(M, M.trk.x_ref[so_t], x_outer, ref_out, nullptr)) status = 1;
+    for (int i = 0; i < 5; ++i) est[i] = M.trk.param[(int64_t)segs[0] * 5 + i];
+    double x_cur = M.trk.x_ref[segs[0]];
+    for (int pass = 0; pass < M.n_refit && !status; ++pass) {
+      if (pass > 0) {
+        double carry[5];
+        for (int i = 0; i < 5; ++i) carry[i] = est[i];
+        double xf = x_cur;
+        bool ok = true;
+        for (int j = 0; j < m && ok; ++j) {
+          ok = transport(M, xf, M.xout[segs[j]], carry, nullptr);
+          xf = M.xout[segs[j]];
+          if (ok && j < m - 1) {
+            double x1;
+            ok = rotate_state(wrap_pi(M.alpha[segs[j + 1]] - M.alpha[segs[j]]), M.kb, M.s_max, xf, carry, &x1, nullptr);
+            xf = x1;
+          }
+        }
+        if (ok)
+          for (int i = 0; i < 5; ++i) ref_out[i] = carry[i];
+      }
+      for (int i = 0; i < 5; ++i) { ref[i] = ref_out[i]; d[i] = 0.0; }
+      cov_diag<double>(C, M.c_yz_refit, M.c_yz_refit, M.c_s, M.c_t, M.c_qpt_refit);
+      chi2 = 0.0;
+      double x_prev = x_outer;
+      int seg = m - 1;
+      int seg_start = n - M.trk.n_cl[segs[m - 1]];   // first cluster index of the current segment
+      for (int k = n - 1; k >= 0 && !status; --k) {
+        const int id = ids[k];
+        const double xk = M.rx[row_of(M, id)];
+        if (k < n - 1) {
+          if (k < seg_start) {   // the cluster lies in the previous (inner) segment: rotate
+            const int from = segs[seg];
+            --seg;
+            seg_start -= M.trk.n_cl[segs[seg]];
+            double x1;
+            Rot J;
+            if (!rotate_state(wrap_pi(M.alpha[segs[seg]] - M.alpha[from]), M.kb, M.s_max, x_prev, ref, &x1, &J)) {
+              status = 1;
+              break;
+            }
+            const double d0 = d[0];
+            d[0] = J.jyy * d0;
+            d[1] = J.jzy * d0 + d[1];
+            d[2] = J.jsy * d0 + J.jss * d[2];
+            cov_rotate(C, J);
+            x_prev = x1;
+          }
+          Step<double> st;
+          if (!helix_step<double>(ref[2], ref[3], ref[4], xk - x_prev, M.kb, M.s_max, st)) { status = 1; break; }
+          ref[0] += st.dy; ref[1] += st.dz; ref[2] += st.ds;
+          d[0] += st.j_ys * d[2] + st.j_yq * d[4];
+          d[1] += st.j_zs * d[2] + st.j_zt * d[3] + st.j_zq * d[4];
+          d[2] += st.j_sq * d[4];
+          cov_transport<double, double>(C, st);
+        }
+        const double zc = (double)M.z[id];
+        double dd = M.z_max - fabs(zc);
+        dd = dd < 0.0 ? 0.0 : (dd > M.z_max ? M.z_max : dd);
+        const double sg = M.sig_readout + M.sig_slope * dd;
+        const double r0 = ((double)M.y[id] - ref[0]) - d[0], r1 = (zc - ref[1]) - d[1];
+        chi2 += kf_chi2_update<double, double>(d, C, r0, r1, sg * sg);
+        x_prev = xk;
+      }
+      if (status) break;
+      for (int i = 0; i < 5; ++i) est[i] = ref[i] + d[i];
+      x_cur = M.rx[row_of(M, ids[0])];
+    }
+    O.status[c] = status;
+    O.chi2[c] = status ? 0.0 : chi2;
+    O.x_ref[c] = status ? M.trk.x_ref[segs[0]] : x_cur;
+    for (int i = 0; i < 5; ++i)
+      O.param[(int64_t)c * 5 + i] = status ? M.trk.param[(int64_t)segs[0] * 5 + i] : est[i];
+    for (int i = 0; i < 15; ++i) O.cov[(int64_t)c * 15 + i] = status ? 0.0 : C[i];
+  }
+}
+
+int blocks_for(int64_t work, int block) {
+  int64_t b = (work + block - 1) / block;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (int)b;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Workspace carve (device pointers; base may be null to measure).
+size_t merge_carve(char* base, int cap_tracks, int n_inst, int n_events, int cap_pairs, MParams* M) {
+  size_t off = 0;
+  auto take = [&](size_t b) -> char* { char* p = base ? base + off : nullptr; off += align256(b ? b : 1); return p; };
+  const size_t nt = (size_t)cap_tracks + 1;
+  MParams q{};
+  q.status = (uint32_t*)take(16);
+  q.rx = (const double*)take(8 * kMaxRows);
+  q.inst_of = (int32_t*)take(4 * (size_t)n_events * 36);
+  q.first = (int32_t*)take(4 * (size_t)n_inst);
+  q.last = (int32_t*)take(4 * (size_t)n_inst);
+  q.alpha = (double*)take(8 * nt);
+  q.rref = (double*)take(8 * nt);
+  q.xout = (double*)take(8 * nt);
+  q.inx = (double*)take(8 * nt);
+  q.iny = (double*)take(8 * nt);
+  q.outx = (double*)take(8 * nt);
+  q.outy = (double*)take(8 * nt);
+  q.best_out_chi = (uint64_t*)take(8 * nt);
+  q.best_in_chi = (uint64_t*)take(8 * nt);
+  q.best_out = (int32_t*)take(4 * nt);
+  q.best_in = (int32_t*)take(4 * nt);
+  q.n_pairs = (int32_t*)take(16);
+  q.pair_i = (int32_t*)take(4 * (size_t)cap_pairs);
+  q.pair_o = (int32_t*)take(4 * (size_t)cap_pairs);
+  q.pair_chi = (double*)take(8 * (size_t)cap_pairs);
+  q.head_flag = (int32_t*)take(4 * nt);
+  q.head_idx = (int32_t*)take(4 * nt);
+  q.nseg = (int32_t*)take(4 * nt);
+  q.segoff = (int32_t*)take(4 * nt);
+  q.ncl = (int32_t*)take(4 * nt);
+  q.cloff = (int32_t*)take(4 * nt);
+  q.scan_tmp = (uint64_t*)take(8 * (size_t)(scan_tmp_elems(nt) + 32));
+  if (M) {
+    M->status = q.status; M->rx = q.rx; M->inst_of = q.inst_of; M->first = q.first; M->last = q.last; M->alpha = q.alpha;
+    M->rref = q.rref; M->xout = q.xout; M->inx = q.inx; M->iny = q.iny; M->outx = q.outx; M->outy = q.outy;
+    M->best_out_chi = q.best_out_chi; M->best_in_chi = q.best_in_chi; M->best_out = q.best_out;
+    M->best_in = q.best_in; M->n_pairs = q.n_pairs; M->pair_i = q.pair_i; M->pair_o = q.pair_o;
+    M->pair_chi = q.pair_chi; M->head_flag = q.head_flag; M->head_idx = q.head_idx; M->nseg = q.nseg;
+    M->segoff = q.segoff; M->ncl = q.ncl; M->cloff = q.cloff; M->scan_tmp = q.scan_tmp;
+  }
+  return off;
+}
+
+}  // namespace
+
+size_t merge_workspace_bytes(int cap_tracks, int n_inst, int n_events) {
+  return merge_carve(nullptr, cap_tracks, n_inst, n_events, 4 * cap_tracks + 1024, nullptr);
+}
+
+// Enqueue the merge; returns the number of kernels launched (or -1 on a bad workspace).
+int enqueue_merge(const double* row_x_host, int n_rows, double kb, const tpct_cuts& cuts, double z_max,
+                  const tpct_merge_cuts& mc, const tpct_clusters& cl, const int32_t* inst_sector,
+                  const int32_t* inst_event, int n_events, const tpct_tracks_out& trk, void* ws, size_t ws_bytes,
+                  const tpct_chains_out& out, cudaStream_t s) {
+  const int cap = trk.capacity_tracks;
+  const int cap_pairs = 4 * cap + 1024;
+  if (merge_carve(nullptr, cap, cl.n_instances, n_events, cap_pairs, nullptr) > ws_bytes) return -1;
+  MParams M{};
+  merge_carve((char*)ws, cap, cl.n_instances, n_events, cap_pairs, &M);
+  RowTab tab;
+  for (int i = 0; i < n_rows; ++i) tab.x[i] = row_x_host[i];
+  M.n_rows = n_rows;
+  M.n_inst = cl.n_instances;
+  M.n_events = n_events;
+  M.n_cap_tracks = cap;
+  M.cap_pairs = cap_pairs;
+  M.kb = kb;
+  M.s_max = cuts.s_max;
+  M.chi2_max = mc.chi2_max; M.max_dtanl = mc.max_dtanl; M.max_gap = mc.max_gap;
+  M.alpha0 = mc.alpha0; M.dalpha = mc.dalpha;
+  M.c_s = cuts.c_s; M.c_t = cuts.c_t; M.c_yz_refit = cuts.c_yz_refit; M.c_qpt_refit = cuts.c_qpt_refit;
+  M.sig_readout = cuts.sig_readout; M.sig_slope = (cuts.sig_cathode - cuts.sig_readout) / z_max; M.z_max = z_max;
+  M.n_refit = cuts.n_refit;
+  M.x = cl.x; M.y = cl.y; M.z = cl.z; M.row = cl.row;
+  M.inst_sector = inst_sector; M.inst_event = inst_event;
+  M.trk = trk;
+  M.out = out;
+  int k = 0;
+  cudaMemsetAsync(M.status, 0, 16, s);
+  k_m_rows<<<1, 256, 0, s>>>(const_cast<double*>(M.rx), n_rows, tab); ++k;
+  const int big = max(max(cap, n_events * 36), cl.n_instances) + 1;
+  k_m_init<<<blocks_for(big, kBlock), kBlock, 0, s>>>(M); ++k;
+  k_m_prep<<<blocks_for(max(cap, cl.n_instances), kBlock), kBlock, 0, s>>>(M); ++k;
+  k_m_pairs<<<max(1, n_events * 36), kBlock, 0, s>>>(M); ++k;
+  k_m_best<<<blocks_for(cap_pairs, kBlock), kBlock, 0, s>>>(M); ++k;
+  k_m_links<<<blocks_for(cap, kBlock), kBlock, 0, s>>>(M); ++k;
+  k_m_heads<<<blocks_for(cap, kBlock), kBlock, 0, s>>>(M); ++k;
+  launch_scan_i32(M.head_flag, M.head_idx, cap, M.scan_tmp, s); k += 3;
+  launch_scan_i32(M.nseg, M.segoff, cap, M.scan_tmp, s); k += 3;
+  launch_scan_i32(M.ncl, M.cloff, cap, M.scan_tmp, s); k += 3;
+  k_m_emit<<<blocks_for(cap, kBlock), kBlock, 0, s>>>(M); ++k;
+  k_m_refit<<<blocks_for(cap, 128), 128, 0, s>>>(M); ++k;
+  return k;
+}
+
+}  // namespace tpct

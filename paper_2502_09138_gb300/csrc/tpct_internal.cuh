@@ -205,5 +205,10 @@ void launch_refit(const Params& P, int mode, int stage, int block, int blocks, c
 void launch_export_links(const Params& P, const tpct_debug_out& d, cudaStream_t s);
 void launch_export_tracklets(const Params& P, const tpct_debug_out& d, cudaStream_t s);
 int kernels_per_track(void);
+size_t merge_workspace_bytes(int cap_tracks, int n_inst, int n_events);
+int enqueue_merge(const double* row_x_host, int n_rows, double kb, const tpct_cuts& cuts, double z_max,
+                  const tpct_merge_cuts& mc, const tpct_clusters& cl, const int32_t* inst_sector,
+                  const int32_t* inst_event, int n_events, const tpct_tracks_out& trk, void* ws, size_t ws_bytes,
+                  const tpct_chains_out& out, cudaStream_t s);
 
 }  // namespace tpct
