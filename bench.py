@@ -34,9 +34,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 STAGES = ["grid", "neighbours", "clean_start", "tracklets", "selection", "refit"]
-# FP64 flops of one helix step (covariance transport), one chi2 test and one
-# Kalman update in the mixed precision (see the flop count in the design notes)
-FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 113, 14, 104
+# FP64 flops of the mixed-precision tracklet filter: a helix step transports
+# the covariance (51 multiply-adds) and adds the float increments to the
+# double state (3 adds); a chi2 test forms the double residuals (2 adds, the
+# chi2 itself is float); an update forms S (2), det (2), the refined 1/det
+# (2 multiply-adds), S^-1 (3), the gain (10 + 10), the covariance (30
+# multiply-adds) and adds the state increments (5)
+FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 2 * 51 + 3, 2, 2 + 3 + 4 + 3 + 30 + 60 + 5
 
 
 def parse():
@@ -53,6 +57,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-merge", action="store_true")
     ap.add_argument("--tuning-cache", default=None, help="autotuner cache file (default: a fresh temp file)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variants", default="mixed_df", help="comma-separated extra precisions timed in the same run")
@@ -201,6 +206,32 @@ def cpu_baseline(ev, gpu_out, gpu_dbg, budget_s=20.0):
     return {"value": sub.n / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(idx)} of {ev.n_instances} sector instances ({sub.n} clusters), "
                       f"single-threaded FP64, {dt:.1f} s"}, rep, idx
+
+
+def merge_leg(args, ev, G, trk, dc, out, stream):
+    """Cross-sector merging of the tracked batch: mean CUDA-event time of
+    tpct_merge over a few calls on the resident tracks."""
+    import torch
+    sec = np.asarray(ev.sectors, dtype=np.int32)
+    evi = (np.arange(ev.n_instances) // ev.sectors_per_event).astype(np.int32)
+    n_events = int(evi.max()) + 1
+    ch = trk.merge(dc, out, sec, evi, n_events)
+    for _ in range(2):
+        trk.merge(dc, out, sec, evi, n_events, out=ch)
+    torch.cuda.synchronize()
+    m0 = torch.cuda.Event(enable_timing=True)
+    m1 = torch.cuda.Event(enable_timing=True)
+    reps = 5
+    m0.record(stream)
+    for _ in range(reps):
+        trk.merge(dc, out, sec, evi, n_events, out=ch)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    mms = m0.elapsed_time(m1) / reps
+    n_tracks = int(out.counts[0].item())
+    n_chains = int(ch.counts[0].item())
+    return {"ms": mms, "tracks_in": n_tracks, "chains": n_chains,
+            "tracks_per_s": n_tracks / (mms * 1e-3), "device_status": trk.device_status()}
 
 
 def serving_leg(args, ev, G, capacity_cps):
@@ -413,7 +444,7 @@ def main():
     fp64_flops = steps * FLOPS_STEP + tests * FLOPS_TEST + updates * FLOPS_UPDATE
     fp64_probe = None
     roofline = None
-    if dom == "tracklets" and args.precision in ("mixed", "fp64"):
+    if dom == "tracklets" and args.precision == "mixed":
         blocks = 152 * 16
         pm = G.probe_fma(True, blocks, 2048)
         fp64_probe = 2.0 * 8 * 2048 * blocks * 256 / (pm * 1e-3) / 1e12
@@ -501,6 +532,11 @@ def main():
         ems = b0.elapsed_time(b1) / reps
         line["e2e"] = {"value": ev.n * world / (ems * 1e-3), "unit": "clusters/s", "ms_per_step": ems,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # cross-sector merging of the batch's sector tracks (a step after the
+    # tracking chain, timed on its own; not part of `value`)
+    if not args.no_merge and ev.sectors_per_event > 1:
+        line["merge"] = merge_leg(args, ev, G, trk, dc, out, stream)
 
     variants = {}
     for vp in [v for v in args.variants.split(",") if v and v != args.precision]:

@@ -212,6 +212,9 @@ tpct_status make_params(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const
   p.sig_readout_f = (float)c.sig_readout;
   p.sig_slope_f = (float)p.sig_slope;
   p.z_max_f = (float)ctx->z_max;
+  p.search_k_f = (float)c.search_k;
+  p.sig_hi_f = (float)(c.sig_readout > c.sig_cathode ? c.sig_readout : c.sig_cathode);
+  p.chi2_max_f = (float)c.chi2_max;
   p.max_miss = c.max_miss; p.n_min = c.n_min; p.n_refit = c.n_refit;
   p.x = cl->x; p.y = cl->y; p.z = cl->z; p.row = cl->row; p.inst_off = cl->sector_offsets;
   p.out = *out;
@@ -257,7 +260,7 @@ int enqueue_track(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
   launch_scan_u64(P.tl_sel, P.tl_sel_scan, P.tcap, P.scan_tmp, s); k += scan_k;
   launch_emit(P, s); ++k;
   mark(5);
-  if (mode == 3 && P.n_refit >= 2) {
+  if ((mode == 1 || mode == 3) && P.n_refit >= 2) {
     // leading passes in double-float, the last pass in double
     launch_refit(P, mode, 1, ctx->refit_block, ctx->rf_blocks, s); ++k;
     launch_refit(P, mode, 2, ctx->refit_block, ctx->rf_blocks, s); ++k;
@@ -639,6 +642,9 @@ extern "C" tpct_status tpct_track_static(tpct_ctx* ctx, const tpct_clusters* cl,
   p.sig_readout_f = (float)c.sig_readout;
   p.sig_slope_f = (float)p.sig_slope;
   p.z_max_f = (float)ctx->z_max;
+  p.search_k_f = (float)c.search_k;
+  p.sig_hi_f = (float)(c.sig_readout > c.sig_cathode ? c.sig_readout : c.sig_cathode);
+  p.chi2_max_f = (float)c.chi2_max;
   p.max_miss = c.max_miss; p.n_min = c.n_min; p.n_refit = c.n_refit;
   p.x = cl->x; p.y = cl->y; p.z = cl->z; p.row = cl->row; p.inst_off = cl->sector_offsets;
   p.out = *out;

@@ -11,8 +11,43 @@
 // use the _rn intrinsics so the compiler neither contracts nor reorders them.
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace tpct {
+
+// ---------------------------------------------------------------- float <-> double on the integer pipes
+// GB300 runs every FP64-pipe instruction, conversions between float and
+// double included, at 2 lanes per SM per clock (1/64 of the FP32 rate).
+// These two conversions rebuild the IEEE-754 bit patterns with a handful of
+// integer instructions instead.  binary32 = sign | 8-bit exponent (bias 127)
+// | 23-bit fraction; binary64 = sign | 11-bit exponent (bias 1023) | 52-bit
+// fraction, so a normal number moves between the two by re-biasing the
+// exponent (896 = 1023 - 127) and shifting the fraction by 29 bits.
+
+// float -> double, exact for zero, normal, infinite and NaN floats; float
+// subnormals (|f| < 2^-126) become zero.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t mag = b & 0x7fffffffu;
+  uint32_t hi = (mag >> 3) + 0x38000000u;                  // exponent + 896 (in bits 30..20)
+  uint32_t lo = b << 29;
+  if (mag >= 0x7f800000u) hi = 0x7ff00000u | ((mag >> 3) & 0xfffffu);   // inf, NaN
+  if (mag < 0x00800000u) { hi = 0u; lo = 0u; }              // zero, subnormal
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
+}
+
+// double -> float, rounded to nearest (ties away from zero) by adding half a
+// float ulp to the bit pattern before truncating it; results below float's
+// normal range come out as zero or a subnormal below 2^-146, results above
+// it saturate to the largest float, infinities and NaNs become NaN.
+__device__ __forceinline__ float narrow(double d) {
+  const uint64_t u = (uint64_t)__double_as_longlong(d) + 0x10000000ull;
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  int32_t e = (int32_t)(hi & 0x7fffffffu) - 0x38000000;    // exponent - 896 (in bits 30..20)
+  e = min(max(e, 0), 0x0fefffff);
+  const float r = __uint_as_float((hi & 0x80000000u) | __funnelshift_l(lo, (uint32_t)e, 3));
+  return (hi & 0x7ff00000u) == 0x7ff00000u ? __uint_as_float(0x7fc00000u) : r;
+}
 
 // the float/double overloads stay visible next to the df64 ones below
 using ::fabs;
@@ -26,8 +61,13 @@ struct df64 {
   __host__ __device__ explicit df64(float a) : hi(a), lo(0.f) {}
   __host__ __device__ explicit df64(int a) : hi((float)a), lo(0.f) {}
   __host__ __device__ explicit df64(double a) {
+#ifdef __CUDA_ARCH__
+    hi = narrow(a);
+    lo = narrow(a - widen(hi));
+#else
     hi = (float)a;
     lo = (float)(a - (double)hi);
+#endif
   }
   __host__ __device__ explicit operator float() const { return hi + lo; }
   __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
@@ -122,11 +162,23 @@ __device__ __forceinline__ df64 sqrt(df64 a) {
 
 // ---------------------------------------------------------------- conversions used by the kernels
 __device__ __forceinline__ float to_float(float a) { return a; }
-__device__ __forceinline__ float to_float(double a) { return (float)a; }
+__device__ __forceinline__ float to_float(double a) { return narrow(a); }
 __device__ __forceinline__ float to_float(df64 a) { return __fadd_rn(a.hi, a.lo); }
-__device__ __forceinline__ double to_double(float a) { return (double)a; }
+__device__ __forceinline__ double to_double(float a) { return widen(a); }
 __device__ __forceinline__ double to_double(double a) { return a; }
-__device__ __forceinline__ double to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double to_double(df64 a) { return widen(a.hi) + widen(a.lo); }
+
+// A float or double value in the type T of a state, covariance or
+// transport variable (float, double or double-float).
+template <class T> struct FromF;
+template <> struct FromF<float> {
+  __device__ static float get(float a) { return a; }
+  __device__ static float get(double a) { return narrow(a); }
+};
+template <> struct FromF<double> {
+  __device__ static double get(float a) { return widen(a); }
+  __device__ static double get(double a) { return a; }
+};
 
 template <class E> struct ToE;
 template <> struct ToE<float> {
@@ -142,16 +194,21 @@ template <> struct ToE<df64> {
   __device__ static df64 get(float a) { return df64(a); }
 };
 template <class E, class T> __device__ __forceinline__ E to_e(T a) { return ToE<E>::get(a); }
+template <> struct FromF<df64> {
+  __device__ static df64 get(float a) { return df64(a); }
+  __device__ static df64 get(double a) { return df64(a); }
+};
+template <class T, class V> __device__ __forceinline__ T conv(V a) { return FromF<T>::get(a); }
 
 // (c - p) converted to E, with c a float cluster coordinate and p a state entry
 __device__ __forceinline__ float diff_f(float c, float p) { return c - p; }
-__device__ __forceinline__ float diff_f(float c, double p) { return (float)((double)c - p); }
+__device__ __forceinline__ float diff_f(float c, double p) { return narrow(widen(c) - p); }
 __device__ __forceinline__ float diff_f(float c, df64 p) { return to_float(df64(c) - p); }
 template <class E, class S> struct DiffTo {
   __device__ static E get(float c, S p) { return (E)diff_f(c, p); }
 };
 template <class S> struct DiffTo<double, S> {
-  __device__ static double get(float c, S p) { return (double)c - to_double(p); }
+  __device__ static double get(float c, S p) { return widen(c) - to_double(p); }
 };
 template <class E, class S> __device__ __forceinline__ E diff_to(float c, S p) { return DiffTo<E, S>::get(c, p); }
 

@@ -183,11 +183,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
       for (int i = 0; i < 5; ++i) { ref[i] = est[i]; d[i] = (S)0; }
     }
     Step<E> st;
-    if (!helix_step<E>(to_e<E>(ref[2]), to_e<E>(ref[3]), to_e<E>(ref[4]), (E)(xj - (start ? x_cur : x_prev)),
+    if (!helix_step<E>(to_e<E>(ref[2]), to_e<E>(ref[3]), to_e<E>(ref[4]), conv<E>(xj - (start ? x_cur : x_prev)),
                        kb, smax, st)) {
       status = 1;
     } else {
-      ref[0] += (S)st.dy; ref[1] += (S)st.dz; ref[2] += (S)st.ds;
+      ref[0] += conv<S>(st.dy); ref[1] += conv<S>(st.dz); ref[2] += conv<S>(st.ds);
       if (start) {
         cov_diag<C>(m, (C)P.c_yz_refit, (C)P.c_yz_refit, (C)P.c_s, (C)P.c_t, (C)P.c_qpt_refit);
         chi2 = (C)0;
@@ -201,8 +201,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
     bool done = status != 0 || pass >= pass_end;
     if (!done) {
       x_prev = xj;
-      const C sg = sigma_of<C>(P, (C)P.sz[pj]);
-      const C r0 = ((C)(S)P.sy[pj] - ref[0]) - d[0], r1 = ((C)(S)P.sz[pj] - ref[1]) - d[1];
+      const C sg = sigma_of<C>(P, conv<C>(P.sz[pj]));
+      const C r0 = (conv<C>(P.sy[pj]) - ref[0]) - d[0], r1 = (conv<C>(P.sz[pj]) - ref[1]) - d[1];
       chi2 += kf_chi2_update<C, S>(d, m, r0, r1, sg * sg);
       if (--j < 0) {
 #pragma unroll
@@ -294,6 +294,8 @@ void launch_refit(const Params& P, int mode, int stage, int block, int blocks, c
   switch (mode * 4 + stage) {
     case 0: k_refit<0, 0><<<blocks, block, 0, s>>>(P); break;
     case 4: k_refit<1, 0><<<blocks, block, 0, s>>>(P); break;
+    case 5: k_refit<1, 1><<<blocks, block, 0, s>>>(P); break;
+    case 6: k_refit<1, 2><<<blocks, block, 0, s>>>(P); break;
     case 8: k_refit<2, 0><<<blocks, block, 0, s>>>(P); break;
     case 12: k_refit<3, 0><<<blocks, block, 0, s>>>(P); break;
     case 13: k_refit<3, 1><<<blocks, block, 0, s>>>(P); break;
@@ -307,7 +309,13 @@ int refit_blocks_per_sm(int mode, int block) {
   cudaError_t e;
   switch (mode) {
     case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<0, 0>, block, 0); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<1, 0>, block, 0); break;
+    case 1: {
+      int nb1 = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<1, 2>, block, 0);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_refit<1, 1>, block, 0);
+      if (nb1 < nb) nb = nb1;
+      break;
+    }
     case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<2, 0>, block, 0); break;
     default: {
       int nb1 = 0;

@@ -45,6 +45,7 @@ struct Params {
   double sig_readout, sig_cathode, c_s, c_t, c_qpt, c_yz_refit, c_qpt_refit;
   double sig_slope;            // (sig_cathode - sig_readout) / z_max
   float sig_readout_f, sig_slope_f, z_max_f;
+  float search_k_f, sig_hi_f, chi2_max_f;   // search_k, max(sig_readout, sig_cathode), chi2_max in float
   int32_t max_miss, n_min, n_refit;
   // input (device, caller-owned)
   const float *x, *y, *z;
@@ -98,20 +99,23 @@ struct Params {
 // ------------------------------------------------------------------ precision
 // S: track state, E: helix-transport / neighbour / search arithmetic,
 // C: covariance, Kalman update; RS/RE/RC: the same for the refit.
-// MODE 0 FP32; 1 mixed (float E, double S/C and an all-double refit);
-// 2 FP64; 3 mixed double-float (float E, double-float S/C in the tracklets;
-// the refit stays all-double: its covariance starts from a diffuse prior and
-// amplifies rounding by ~1e12, beyond what the 48-bit double-float keeps).
+// MODE 0 FP32; 1 mixed (float E, double S/C: float transport increments,
+// double Kalman update); 2 FP64; 3 mixed double-float (float E, double-float
+// S/C in the tracklets).  The last refit pass is all-double in modes 1-3: its
+// covariance starts from a diffuse prior and amplifies rounding by ~1e12,
+// beyond what the 48-bit double-float keeps.
 template <int MODE> struct Prec;
 // PS/PE/PC: the refit passes before the last, which only move the
-// linearisation point (mode 3 runs them in double-float with float transport;
-// the last pass, which gives the estimate and the covariance, in double).
+// linearisation point of a Gauss-Newton iteration (an error e there moves the
+// final estimate by O(e^2)): modes 1 and 3 run them in double-float with float
+// transport; the last pass, which gives the estimate and the covariance, in
+// double.
 template <> struct Prec<0> { using S = float;  using E = float;  using C = float;
                              using RS = float;  using RE = float;  using RC = float;
                              using PS = float;  using PE = float;  using PC = float; };
 template <> struct Prec<1> { using S = double; using E = float;  using C = double;
                              using RS = double; using RE = double; using RC = double;
-                             using PS = double; using PE = double; using PC = double; };
+                             using PS = df64;   using PE = float;  using PC = df64; };
 template <> struct Prec<2> { using S = double; using E = double; using C = double;
                              using RS = double; using RE = double; using RC = double;
                              using PS = double; using PE = double; using PC = double; };

@@ -177,7 +177,8 @@ __device__ __forceinline__ void cov_transport(df64* m, float a, float b, float c
 template <class C, class E>
 __device__ __forceinline__ void cov_transport(C* m, const Step<E>& st) {
   using J = typename std::conditional<is_df64<C>::value, E, C>::type;
-  cov_transport(m, (J)st.j_ys, (J)st.j_yq, (J)st.j_zs, (J)st.j_zt, (J)st.j_zq, (J)st.j_sq);
+  cov_transport(m, conv<J>(st.j_ys), conv<J>(st.j_yq), conv<J>(st.j_zs), conv<J>(st.j_zt), conv<J>(st.j_zq),
+                conv<J>(st.j_sq));
 }
 
 // chi2 of residual (r0, r1) against S = C[yz] + diag(vy, vz)
@@ -256,6 +257,42 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
     k0[i] = c0[i] * i00 + c1[i] * i01;
     k1[i] = c0[i] * i01 + c1[i] * i11;
     p[i] += df64(to_float(k0[i]) * fr0 + to_float(k1[i]) * fr1);
+  }
+  int idx = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] -= k0[i] * c0[j] + k1[i] * c1[j];
+  return true;
+}
+
+// Mixed tracklet filter (double state and covariance, float transport): the
+// chi2 decision in float (1e-6 relative at most, inside the 1e-5 near-cut
+// band), 1/det from the float reciprocal refined by one Newton step in double
+// (relative error ~1e-14), the state increment K r in float (1e-7 of an
+// increment far smaller than the state); the gain and the covariance update,
+// whose subtraction cancels, in double.
+__device__ __forceinline__ bool kf_test_update_mixed(double* p, double* m, double r0, double r1, float v,
+                                                     float chi2_max) {
+  const float f00 = narrow(m[0]) + v, f01 = narrow(m[1]), f11 = narrow(m[2]) + v;
+  const float fr0 = narrow(r0), fr1 = narrow(r1);
+  const float fdet = f00 * f11 - f01 * f01;
+  const float chi2 = (fr0 * (f11 * fr0 - f01 * fr1) + fr1 * (f00 * fr1 - f01 * fr0)) / fdet;
+  if (!(chi2 <= chi2_max)) return false;
+  const double vd = widen(v);
+  const double s00 = m[0] + vd, s01 = m[1], s11 = m[2] + vd;
+  const double det = s00 * s11 - s01 * s01;
+  double idet = widen(1.0f / fdet);
+  idet = fma(idet, fma(-det, idet, 1.0), idet);
+  const double i00 = s11 * idet, i01 = -s01 * idet, i11 = s00 * idet;
+  const double c0[5] = {m[0], m[1], m[3], m[6], m[10]};
+  const double c1[5] = {m[1], m[2], m[4], m[7], m[11]};
+  double k0[5], k1[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    k0[i] = c0[i] * i00 + c1[i] * i01;
+    k1[i] = c0[i] * i01 + c1[i] * i11;
+    p[i] += widen(narrow(k0[i]) * fr0 + narrow(k1[i]) * fr1);
   }
   int idx = 0;
 #pragma unroll

@@ -25,8 +25,9 @@ namespace {
 template <class E, class S>
 __device__ int search_row(const Params& P, int ir, S py, S pz, E cyy, E czz) {
   const RowGrid g = P.grid[ir];
-  const E k = (E)P.search_k, k2 = k * k;
-  const E sig_hi = (E)fmax(P.sig_readout, P.sig_cathode);
+  constexpr bool kF = std::is_same<E, float>::value;
+  const E k = kF ? (E)P.search_k_f : (E)P.search_k, k2 = k * k;
+  const E sig_hi = kF ? (E)P.sig_hi_f : (E)fmax(P.sig_readout, P.sig_cathode);
   const E wy = k * sqrt(cyy + sig_hi * sig_hi), wz = k * sqrt(czz + sig_hi * sig_hi);
   const E ey = to_e<E>(py), ez = to_e<E>(pz);
   const float fy = (float)ey, fz = (float)ez;
@@ -59,6 +60,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
   using S = typename Prec<MODE>::S;
   using E = typename Prec<MODE>::E;
   using C = typename Prec<MODE>::C;
+  // float transport with a double covariance: the mixed filter (float chi2
+  // decision and state increment, double gain and covariance update)
+  constexpr bool kMixed = std::is_same<E, float>::value && std::is_same<C, double>::value;
   const int R = P.n_rows;
   const int n_tl = min(P.row_tl_base[P.n_inst * R], P.tcap);
   const E kb = (E)P.kb, smax = (E)P.s_max;
@@ -100,8 +104,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
           const float dx = P.rdxf[r0 + 1];
           const float dy = P.sy[h1] - P.sy[p0], dz = P.sz[h1] - P.sz[p0];
           const float il = rsqrtf(dx * dx + dy * dy);
-          p[0] = (S)P.sy[p0]; p[1] = (S)P.sz[p0]; p[2] = (S)(dy * il); p[3] = (S)(dz * il); p[4] = (S)0;
-          const C v0 = (C)cluster_var(P, P.sz[p0]);
+          p[0] = conv<S>(P.sy[p0]); p[1] = conv<S>(P.sz[p0]); p[2] = conv<S>(dy * il); p[3] = conv<S>(dz * il);
+          p[4] = conv<S>(0.0f);
+          const C v0 = conv<C>(cluster_var(P, P.sz[p0]));
           cov_diag<C>(m, v0, v0, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
           hits = P.tl_hits + t;
           hits[0] = p0;
@@ -132,10 +137,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
     const bool stepped = helix_step<E>(to_e<E>(p[2]), to_e<E>(p[3]), to_e<E>(p[4]), dx, kb, smax, st);
     if (stepped) {
       ++n_step;
-      p[0] += (S)st.dy; p[1] += (S)st.dz; p[2] += (S)st.ds;
+      p[0] += conv<S>(st.dy); p[1] += conv<S>(st.dz); p[2] += conv<S>(st.ds);
       cov_transport<C, E>(m, st);
     }
-    const bool inside = stepped && !abs_exceeds(p[0], EdgeOf<S>::get(P, r));
+    // the edge and sin(phi) limits are compared in the transport precision
+    const bool inside = stepped && !abs_exceeds(to_e<E>(p[0]), EdgeOf<E>::get(P, r));
     go = inside;
     int cand = -1;
     if (inside) {
@@ -150,9 +156,12 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
     __syncwarp(active);
     bool ok = false;
     if (cand >= 0) {
-      const C ry = (C)((S)P.sy[cand] - p[0]), rz = (C)((S)P.sz[cand] - p[1]);
+      const C ry = (C)(conv<S>(P.sy[cand]) - p[0]), rz = (C)(conv<S>(P.sz[cand]) - p[1]);
       ++n_test;
-      if (kf_test_update<C, S>(p, m, ry, rz, (C)cluster_var(P, P.sz[cand]), chi2_max)) { ++n_upd; ok = true; }
+      bool pass;
+      if constexpr (kMixed) pass = kf_test_update_mixed(p, m, ry, rz, cluster_var(P, P.sz[cand]), P.chi2_max_f);
+      else pass = kf_test_update<C, S>(p, m, ry, rz, conv<C>(cluster_var(P, P.sz[cand])), chi2_max);
+      if (pass) { ++n_upd; ok = true; }
     }
     __syncwarp(active);
     if (inside) {
@@ -172,7 +181,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
 #pragma unroll
             for (int i = 0; i < 5; ++i) in_p[i] = p[i];
           }
-          if (!abs_below(p[2], SmaxOf<S>::get(P))) go = false;
+          if (!abs_below(to_e<E>(p[2]), SmaxOf<E>::get(P))) go = false;
         } else if (++miss > P.max_miss) {
           go = false;
         }
@@ -188,7 +197,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
       up = false;
 #pragma unroll
       for (int i = 0; i < 5; ++i) { p[i] = top[i]; in_p[i] = top[i]; }
-      const C v0 = (C)cluster_var(P, P.sz[top_hit]);
+      const C v0 = conv<C>(cluster_var(P, P.sz[top_hit]));
       cov_diag<C>(m, v0, v0, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
       j_up = n_up - 2;
       n_f = 1;
