@@ -19,13 +19,15 @@ namespace tpct {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kLenBins = 1024;   // chain-length classes of the refit order (longer chains share the top one)
 
 struct MParams {
   const double* rx;
   int n_rows, n_inst, n_events, n_cap_tracks;
-  int32_t cap_pairs;
+  int32_t cap_pairs, cap_cand;
   double kb, s_max, chi2_max, max_dtanl, max_gap, alpha0, dalpha;
   double c_s, c_t, c_yz_refit, c_qpt_refit, sig_readout, sig_slope, z_max;
+  float sig_readout_f, sig_slope_f, z_max_f;
   int n_refit;
   // inputs
   const float *x, *y, *z;
@@ -39,11 +41,17 @@ struct MParams {
   double *alpha, *rref, *xout, *inx, *iny, *outx, *outy;   // [cap tracks]
   uint64_t *best_out_chi, *best_in_chi;                      // [cap tracks] order-preserving chi2 bits
   int32_t *best_out, *best_in;                               // [cap tracks]
+  int32_t* n_cand;                                           // [1]
+  int32_t *cand_i, *cand_o;                                  // [cap_cand] prefiltered pairs (inner, outer)
   int32_t* n_pairs;                                          // [1]
   int32_t* pair_i;                                           // [cap_pairs] inner, outer
   int32_t* pair_o;
   double* pair_chi;
   int32_t *head_flag, *head_idx, *nseg, *segoff, *ncl, *cloff;   // [cap tracks + 1] per head
+  int32_t* len_cursor;                                       // [kLenBins] chains per length, then cursors
+  int32_t* ch_order;                                         // [cap tracks] chains, longest first
+  double *ch_est, *ch_ref, *ch_x;                            // [5 cap], [5 cap], [cap] after the leading passes
+  int32_t* ch_st;                                            // [cap]
   uint64_t* scan_tmp;
   tpct_chains_out out;
 };
@@ -183,7 +191,7 @@ __global__ void k_m_rows(double* rx, int n, const RowTab tab) {
 __global__ void k_m_init(const __grid_constant__ MParams M) {
   const int nt = M.n_cap_tracks;
   const int ni = M.n_events * 36;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(max(nt, ni), M.n_inst) + 1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(max(max(nt, ni), M.n_inst), kLenBins) + 1;
        i += gridDim.x * blockDim.x) {
     if (i < ni) M.inst_of[i] = -1;
     if (i < M.n_inst) { M.first[i] = 0; M.last[i] = 0; }
@@ -192,7 +200,8 @@ __global__ void k_m_init(const __grid_constant__ MParams M) {
       M.best_out[i] = 0x7fffffff; M.best_in[i] = 0x7fffffff;
       M.head_flag[i] = 0; M.nseg[i] = 0; M.ncl[i] = 0;
     }
-    if (i == 0) *M.n_pairs = 0;
+    if (i < kLenBins) M.len_cursor[i] = 0;
+    if (i == 0) { *M.n_pairs = 0; *M.n_cand = 0; }
   }
 }
 
@@ -222,8 +231,11 @@ __global__ void k_m_prep(const __grid_constant__ MParams M) {
   }
 }
 
-// One block per boundary (collision, side, sector k | k+1).
-__global__ void k_m_pairs(const __grid_constant__ MParams M) {
+// Prefilter of all track pairs across one sector boundary, one block per
+// (collision, side, sector k | k+1).  The few pairs that pass are compacted
+// (warp ballot, one atomic per warp) into a candidate list, so that the FP64
+// pair chi2 below runs with full warps instead of a few lanes of each.
+__global__ void k_m_cand(const __grid_constant__ MParams M) {
   const int b = blockIdx.x;
   const int e = b / 36, side = (b / 18) % 2, kk = b % 18;
   if (e >= M.n_events) return;
@@ -233,14 +245,46 @@ __global__ void k_m_pairs(const __grid_constant__ MParams M) {
   const int a0 = M.first[ia], na = M.last[ia] - a0;
   const int b0 = M.first[ib], nb = M.last[ib] - b0;
   if (na <= 0 || nb <= 0) return;
-  for (int64_t q = threadIdx.x; q < (int64_t)na * nb; q += blockDim.x) {
-    const int a = a0 + (int)(q / nb), bb = b0 + (int)(q % nb);
-    if (M.trk.status[a] || M.trk.status[bb]) continue;
-    int I = a, O = bb;
-    if (M.rref[bb] < M.rref[a] || (M.rref[bb] == M.rref[a] && bb < a)) { I = bb; O = a; }
-    const double dt = fabs(M.trk.param[(int64_t)I * 5 + 3] - M.trk.param[(int64_t)O * 5 + 3]);
-    const double gx = M.outx[I] - M.inx[O], gy = M.outy[I] - M.iny[O];
-    if (!(dt <= M.max_dtanl && sqrt(gx * gx + gy * gy) <= M.max_gap)) continue;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = (int64_t)na * nb;
+  // every thread runs the same number of rounds, so whole warps reach the ballot
+  for (int64_t q0 = 0; q0 < total; q0 += blockDim.x) {
+    const int64_t q = q0 + threadIdx.x;
+    bool pass = false;
+    int I = 0, O = 0;
+    if (q < total) {
+      const int a = a0 + (int)(q / nb), bb = b0 + (int)(q % nb);
+      if (!M.trk.status[a] && !M.trk.status[bb]) {
+        I = a; O = bb;
+        if (M.rref[bb] < M.rref[a] || (M.rref[bb] == M.rref[a] && bb < a)) { I = bb; O = a; }
+        const double dt = fabs(M.trk.param[(int64_t)I * 5 + 3] - M.trk.param[(int64_t)O * 5 + 3]);
+        const double gx = M.outx[I] - M.inx[O], gy = M.outy[I] - M.iny[O];
+        pass = dt <= M.max_dtanl && sqrt(gx * gx + gy * gy) <= M.max_gap;
+      }
+    }
+    const uint32_t ball = __ballot_sync(0xffffffffu, pass);
+    if (ball) {
+      const int leader = __ffs(ball) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(M.n_cand, __popc(ball));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (pass) {
+        const int slot = base + __popc(ball & ((1u << lane) - 1u));
+        if (slot < M.cap_cand) { M.cand_i[slot] = I; M.cand_o[slot] = O; }
+        else atomicOr(M.status, kDevCapacity);
+      }
+    }
+  }
+}
+
+// Pair chi2 of every candidate (one thread each): I's refit state transported
+// to its outermost cluster, rotated into O's frame, transported to O's
+// reference x and compared with O's state.  The candidate order does not
+// matter: the best partners come from order-independent atomic minima.
+__global__ void k_m_chi(const __grid_constant__ MParams M) {
+  const int nc = min(*M.n_cand, M.cap_cand);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+    const int I = M.cand_i[q], O = M.cand_o[q];
     double p[5], C[15];
     load_track(M, I, p, C);
     if (!transport(M, M.trk.x_ref[I], M.xout[I], p, C)) continue;
@@ -339,28 +383,115 @@ __global__ void k_m_emit(const __grid_constant__ MParams M) {
   }
 }
 
-// Chain refit (FP64): reference-trajectory Kalman filter over all clusters of
-// the chain, outermost to innermost, 3 passes; pass 0 takes its reference
-// from the outermost segment's own fit carried to its outermost cluster;
-// later passes carry the previous estimate outward through the chain (kept
-// from the previous pass if that carry fails).
-__global__ void __launch_bounds__(128) k_m_refit(const __grid_constant__ MParams M) {
+// Chain lengths, longest first: a counting sort on min(n_cl, kLenBins - 1)
+// so that consecutive threads of the chain refit take chains of similar
+// length and the lanes of a warp finish together.  Each chain's refit is
+// independent, so the order changes no result.
+__global__ void k_m_len_count(const __grid_constant__ MParams M) {
   const tpct_chains_out& O = M.out;
   const int nc = min(M.head_idx[M.n_cap_tracks], O.capacity_chains);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+    atomicAdd(&M.len_cursor[min(O.n_cl[c], kLenBins - 1)], 1);
+}
+
+// one block of kLenBins threads: cursor[L] = number of chains in longer classes
+__global__ void __launch_bounds__(kLenBins) k_m_len_scan(const __grid_constant__ MParams M) {
+  __shared__ int sh[kLenBins];
+  const int L = threadIdx.x;
+  const int cnt = M.len_cursor[L];
+  sh[L] = cnt;
+  __syncthreads();
+  for (int off = 1; off < kLenBins; off <<= 1) {   // inclusive suffix sums
+    const int v = L + off < kLenBins ? sh[L + off] : 0;
+    __syncthreads();
+    sh[L] += v;
+    __syncthreads();
+  }
+  M.len_cursor[L] = sh[L] - cnt;
+}
+
+__global__ void k_m_len_scatter(const __grid_constant__ MParams M) {
+  const tpct_chains_out& O = M.out;
+  const int nc = min(M.head_idx[M.n_cap_tracks], O.capacity_chains);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+    M.ch_order[atomicAdd(&M.len_cursor[min(O.n_cl[c], kLenBins - 1)], 1)] = c;
+}
+
+// Rotation Jacobian entry times a deviation or covariance entry, in the
+// precision of the latter (float entries for double-float).
+__device__ __forceinline__ double mulj(double j, double v) { return j * v; }
+__device__ __forceinline__ df64 mulj(double j, df64 v) { return v * narrow(j); }
+
+// C <- J C J^T for a double-float covariance (packed lower triangle; rows
+// y, z, s of J differ from the identity: y' = jyy y, z' = jzy y + z,
+// s' = jsy y + jss s).
+__device__ __forceinline__ void cov_rotate(df64* m, const Rot& J) {
+  const df64 a10 = mulj(J.jzy, m[0]) + m[1];                    // (J C)_10
+  const df64 a20 = mulj(J.jsy, m[0]) + mulj(J.jss, m[3]);       // (J C)_20
+  const df64 a21 = mulj(J.jsy, m[1]) + mulj(J.jss, m[4]);       // (J C)_21
+  const df64 a22 = mulj(J.jsy, m[3]) + mulj(J.jss, m[5]);       // (J C)_22
+  const df64 a11 = mulj(J.jzy, m[1]) + m[2];                    // (J C)_11
+  const df64 c00 = mulj(J.jyy, mulj(J.jyy, m[0]));
+  const df64 c10 = mulj(J.jyy, a10);
+  const df64 c11 = mulj(J.jzy, a10) + a11;
+  const df64 c20 = mulj(J.jyy, a20);
+  const df64 c21 = mulj(J.jzy, a20) + a21;
+  const df64 c22 = mulj(J.jsy, a20) + mulj(J.jss, a22);
+  const df64 m30 = m[6], m40 = m[10];
+  m[0] = c00; m[1] = c10; m[2] = c11; m[3] = c20; m[4] = c21; m[5] = c22;
+  m[6] = mulj(J.jyy, m30);
+  m[7] = mulj(J.jzy, m30) + m[7];
+  m[8] = mulj(J.jsy, m30) + mulj(J.jss, m[8]);
+  m[10] = mulj(J.jyy, m40);
+  m[11] = mulj(J.jzy, m40) + m[11];
+  m[12] = mulj(J.jsy, m40) + mulj(J.jss, m[12]);
+}
+
+// Chain refit: reference-trajectory Kalman filter over all clusters of the
+// chain, outermost to innermost, n_refit passes; pass 0 takes its reference
+// from the outermost segment's own fit carried to its outermost cluster;
+// later passes carry the previous estimate outward through the chain (kept
+// from the previous pass if that carry fails).  As in the sector refit, the
+// passes before the last only move the linearisation point (an error e there
+// moves the result by O(e^2)): STAGE 1 runs them in double-float with float
+// transport and stores the estimate; STAGE 2 runs the last pass, which gives
+// the parameters, covariance and chi2, in double.  One thread per chain, in
+// the longest-first order.
+template <int STAGE>
+__global__ void __launch_bounds__(128) k_m_refit(const __grid_constant__ MParams M) {
+  using S = typename std::conditional<STAGE == 1, df64, double>::type;
+  using E = typename std::conditional<STAGE == 1, float, double>::type;
+  using C = S;
+  const tpct_chains_out& O = M.out;
+  const int nc = min(M.head_idx[M.n_cap_tracks], O.capacity_chains);
+  const int pass_begin = STAGE == 1 ? 0 : max(M.n_refit - 1, 0);
+  const int pass_end = STAGE == 1 ? M.n_refit - 1 : M.n_refit;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+    const int c = M.ch_order[q];
     const int m = O.n_seg[c], n = O.n_cl[c], off = O.offset[c], so = O.seg_offset[c];
     if (off + n > O.capacity_ids || so + m > O.capacity_segs) continue;
     const int* segs = O.segs + so;
     const int* ids = O.cluster_ids + off;
     int status = 0;
-    double est[5], ref[5], ref_out[5], d[5], C[15], chi2 = 0.0;
+    double est[5], ref_out[5], x_cur;
     const int so_t = segs[m - 1];
-    for (int i = 0; i < 5; ++i) ref_out[i] = M.trk.param[(int64_t)so_t * 5 + i];
     const double x_outer = M.xout[so_t];
-    if (!transport(M, M.trk.x_ref[so_t], x_outer, ref_out, nullptr)) status = 1;
-    for (int i = 0; i < 5; ++i) est[i] = M.trk.param[(int64_t)segs[0] * 5 + i];
-    double x_cur = M.trk.x_ref[segs[0]];
-    for (int pass = 0; pass < M.n_refit && !status; ++pass) {
+    if (pass_begin == 0) {
+      for (int i = 0; i < 5; ++i) ref_out[i] = M.trk.param[(int64_t)so_t * 5 + i];
+      if (!transport(M, M.trk.x_ref[so_t], x_outer, ref_out, nullptr)) status = 1;
+      for (int i = 0; i < 5; ++i) est[i] = M.trk.param[(int64_t)segs[0] * 5 + i];
+      x_cur = M.trk.x_ref[segs[0]];
+    } else {
+      for (int i = 0; i < 5; ++i) {
+        est[i] = M.ch_est[(int64_t)i * M.n_cap_tracks + c];
+        ref_out[i] = M.ch_ref[(int64_t)i * M.n_cap_tracks + c];
+      }
+      x_cur = M.ch_x[c];
+      status = M.ch_st[c];
+    }
+    S ref[5], d[5];
+    C Cm[15], chi2 = conv<C>(0.0);
+    for (int pass = pass_begin; pass < pass_end && !status; ++pass) {
       if (pass > 0) {
         double carry[5];
         for (int i = 0; i < 5; ++i) carry[i] = est[i];
@@ -378,9 +509,10 @@ __global__ void __launch_bounds__(128) k_m_refit(const __grid_constant__ MParams
         if (ok)
           for (int i = 0; i < 5; ++i) ref_out[i] = carry[i];
       }
-      for (int i = 0; i < 5; ++i) { ref[i] = ref_out[i]; d[i] = 0.0; }
-      cov_diag<double>(C, M.c_yz_refit, M.c_yz_refit, M.c_s, M.c_t, M.c_qpt_refit);
-      chi2 = 0.0;
+      for (int i = 0; i < 5; ++i) { ref[i] = conv<S>(ref_out[i]); d[i] = conv<S>(0.0); }
+      cov_diag<C>(Cm, conv<C>(M.c_yz_refit), conv<C>(M.c_yz_refit), conv<C>(M.c_s), conv<C>(M.c_t),
+                  conv<C>(M.c_qpt_refit));
+      chi2 = conv<C>(0.0);
       double x_prev = x_outer;
       int seg = m - 1;
       int seg_start = n - M.trk.n_cl[segs[m - 1]];   // first cluster index of the current segment
@@ -392,45 +524,69 @@ __global__ void __launch_bounds__(128) k_m_refit(const __grid_constant__ MParams
             const int from = segs[seg];
             --seg;
             seg_start -= M.trk.n_cl[segs[seg]];
-            double x1;
+            double x1, rd[5];
             Rot J;
-            if (!rotate_state(wrap_pi(M.alpha[segs[seg]] - M.alpha[from]), M.kb, M.s_max, x_prev, ref, &x1, &J)) {
+            for (int i = 0; i < 5; ++i) rd[i] = to_double(ref[i]);
+            if (!rotate_state(wrap_pi(M.alpha[segs[seg]] - M.alpha[from]), M.kb, M.s_max, x_prev, rd, &x1, &J)) {
               status = 1;
               break;
             }
-            const double d0 = d[0];
-            d[0] = J.jyy * d0;
-            d[1] = J.jzy * d0 + d[1];
-            d[2] = J.jsy * d0 + J.jss * d[2];
-            cov_rotate(C, J);
+            for (int i = 0; i < 5; ++i) ref[i] = conv<S>(rd[i]);
+            const S d0 = d[0];
+            d[0] = mulj(J.jyy, d0);
+            d[1] = mulj(J.jzy, d0) + d[1];
+            d[2] = mulj(J.jsy, d0) + mulj(J.jss, d[2]);
+            cov_rotate(Cm, J);
             x_prev = x1;
           }
-          Step<double> st;
-          if (!helix_step<double>(ref[2], ref[3], ref[4], xk - x_prev, M.kb, M.s_max, st)) { status = 1; break; }
-          ref[0] += st.dy; ref[1] += st.dz; ref[2] += st.ds;
+          Step<E> st;
+          if (!helix_step<E>(to_e<E>(ref[2]), to_e<E>(ref[3]), to_e<E>(ref[4]), conv<E>(xk - x_prev), (E)M.kb,
+                             (E)M.s_max, st)) {
+            status = 1;
+            break;
+          }
+          ref[0] += conv<S>(st.dy); ref[1] += conv<S>(st.dz); ref[2] += conv<S>(st.ds);
           d[0] += st.j_ys * d[2] + st.j_yq * d[4];
           d[1] += st.j_zs * d[2] + st.j_zt * d[3] + st.j_zq * d[4];
           d[2] += st.j_sq * d[4];
-          cov_transport<double, double>(C, st);
+          cov_transport<C, E>(Cm, st);
         }
-        const double zc = (double)M.z[id];
-        double dd = M.z_max - fabs(zc);
-        dd = dd < 0.0 ? 0.0 : (dd > M.z_max ? M.z_max : dd);
-        const double sg = M.sig_readout + M.sig_slope * dd;
-        const double r0 = ((double)M.y[id] - ref[0]) - d[0], r1 = (zc - ref[1]) - d[1];
-        chi2 += kf_chi2_update<double, double>(d, C, r0, r1, sg * sg);
+        C var;
+        if constexpr (STAGE == 1) {
+          float dd = M.z_max_f - fabsf(M.z[id]);
+          dd = fminf(fmaxf(dd, 0.0f), M.z_max_f);
+          const float sg = M.sig_readout_f + M.sig_slope_f * dd;
+          var = conv<C>(sg * sg);
+        } else {
+          const double zc = widen(M.z[id]);
+          double dd = M.z_max - fabs(zc);
+          dd = dd < 0.0 ? 0.0 : (dd > M.z_max ? M.z_max : dd);
+          const double sg = M.sig_readout + M.sig_slope * dd;
+          var = sg * sg;
+        }
+        const C r0 = (conv<C>(M.y[id]) - ref[0]) - d[0], r1 = (conv<C>(M.z[id]) - ref[1]) - d[1];
+        chi2 += kf_chi2_update<C, S>(d, Cm, r0, r1, var);
         x_prev = xk;
       }
       if (status) break;
-      for (int i = 0; i < 5; ++i) est[i] = ref[i] + d[i];
+      for (int i = 0; i < 5; ++i) est[i] = to_double(ref[i] + d[i]);
       x_cur = M.rx[row_of(M, ids[0])];
     }
+    if (STAGE == 1) {
+      for (int i = 0; i < 5; ++i) {
+        M.ch_est[(int64_t)i * M.n_cap_tracks + c] = est[i];
+        M.ch_ref[(int64_t)i * M.n_cap_tracks + c] = ref_out[i];
+      }
+      M.ch_x[c] = x_cur;
+      M.ch_st[c] = status;
+      continue;
+    }
     O.status[c] = status;
-    O.chi2[c] = status ? 0.0 : chi2;
+    O.chi2[c] = status ? 0.0 : to_double(chi2);
     O.x_ref[c] = status ? M.trk.x_ref[segs[0]] : x_cur;
     for (int i = 0; i < 5; ++i)
       O.param[(int64_t)c * 5 + i] = status ? M.trk.param[(int64_t)segs[0] * 5 + i] : est[i];
-    for (int i = 0; i < 15; ++i) O.cov[(int64_t)c * 15 + i] = status ? 0.0 : C[i];
+    for (int i = 0; i < 15; ++i) O.cov[(int64_t)c * 15 + i] = status ? 0.0 : to_double(Cm[i]);
   }
 }
 
@@ -444,7 +600,8 @@ int blocks_for(int64_t work, int block) {
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Workspace carve (device pointers; base may be null to measure).
-size_t merge_carve(char* base, int cap_tracks, int n_inst, int n_events, int cap_pairs, MParams* M) {
+size_t merge_carve(char* base, int cap_tracks, int n_inst, int n_events, int cap_pairs, int cap_cand,
+                   MParams* M) {
   size_t off = 0;
   auto take = [&](size_t b) -> char* { char* p = base ? base + off : nullptr; off += align256(b ? b : 1); return p; };
   const size_t nt = (size_t)cap_tracks + 1;
@@ -465,6 +622,9 @@ size_t merge_carve(char* base, int cap_tracks, int n_inst, int n_events, int cap
   q.best_in_chi = (uint64_t*)take(8 * nt);
   q.best_out = (int32_t*)take(4 * nt);
   q.best_in = (int32_t*)take(4 * nt);
+  q.n_cand = (int32_t*)take(16);
+  q.cand_i = (int32_t*)take(4 * (size_t)cap_cand);
+  q.cand_o = (int32_t*)take(4 * (size_t)cap_cand);
   q.n_pairs = (int32_t*)take(16);
   q.pair_i = (int32_t*)take(4 * (size_t)cap_pairs);
   q.pair_o = (int32_t*)take(4 * (size_t)cap_pairs);
@@ -475,6 +635,12 @@ size_t merge_carve(char* base, int cap_tracks, int n_inst, int n_events, int cap
   q.segoff = (int32_t*)take(4 * nt);
   q.ncl = (int32_t*)take(4 * nt);
   q.cloff = (int32_t*)take(4 * nt);
+  q.len_cursor = (int32_t*)take(4 * (size_t)kLenBins);
+  q.ch_order = (int32_t*)take(4 * nt);
+  q.ch_est = (double*)take(8 * 5 * nt);
+  q.ch_ref = (double*)take(8 * 5 * nt);
+  q.ch_x = (double*)take(8 * nt);
+  q.ch_st = (int32_t*)take(4 * nt);
   q.scan_tmp = (uint64_t*)take(8 * (size_t)(scan_tmp_elems(nt) + 32));
   if (M) {
     M->status = q.status; M->rx = q.rx; M->inst_of = q.inst_of; M->first = q.first; M->last = q.last; M->alpha = q.alpha;
@@ -483,6 +649,8 @@ size_t merge_carve(char* base, int cap_tracks, int n_inst, int n_events, int cap
     M->best_in = q.best_in; M->n_pairs = q.n_pairs; M->pair_i = q.pair_i; M->pair_o = q.pair_o;
     M->pair_chi = q.pair_chi; M->head_flag = q.head_flag; M->head_idx = q.head_idx; M->nseg = q.nseg;
     M->segoff = q.segoff; M->ncl = q.ncl; M->cloff = q.cloff; M->scan_tmp = q.scan_tmp;
+    M->n_cand = q.n_cand; M->cand_i = q.cand_i; M->cand_o = q.cand_o; M->len_cursor = q.len_cursor;
+    M->ch_order = q.ch_order; M->ch_est = q.ch_est; M->ch_ref = q.ch_ref; M->ch_x = q.ch_x; M->ch_st = q.ch_st;
   }
   return off;
 }
@@ -490,7 +658,7 @@ size_t merge_carve(char* base, int cap_tracks, int n_inst, int n_events, int cap
 }  // namespace
 
 size_t merge_workspace_bytes(int cap_tracks, int n_inst, int n_events) {
-  return merge_carve(nullptr, cap_tracks, n_inst, n_events, 4 * cap_tracks + 1024, nullptr);
+  return merge_carve(nullptr, cap_tracks, n_inst, n_events, 4 * cap_tracks + 1024, 16 * cap_tracks + 4096, nullptr);
 }
 
 // Enqueue the merge; returns the number of kernels launched (or -1 on a bad workspace).
@@ -500,9 +668,10 @@ int enqueue_merge(const double* row_x_host, int n_rows, double kb, const tpct_cu
                   const tpct_chains_out& out, cudaStream_t s) {
   const int cap = trk.capacity_tracks;
   const int cap_pairs = 4 * cap + 1024;
-  if (merge_carve(nullptr, cap, cl.n_instances, n_events, cap_pairs, nullptr) > ws_bytes) return -1;
+  const int cap_cand = 16 * cap + 4096;
+  if (merge_carve(nullptr, cap, cl.n_instances, n_events, cap_pairs, cap_cand, nullptr) > ws_bytes) return -1;
   MParams M{};
-  merge_carve((char*)ws, cap, cl.n_instances, n_events, cap_pairs, &M);
+  merge_carve((char*)ws, cap, cl.n_instances, n_events, cap_pairs, cap_cand, &M);
   RowTab tab;
   for (int i = 0; i < n_rows; ++i) tab.x[i] = row_x_host[i];
   M.n_rows = n_rows;
@@ -510,6 +679,7 @@ int enqueue_merge(const double* row_x_host, int n_rows, double kb, const tpct_cu
   M.n_events = n_events;
   M.n_cap_tracks = cap;
   M.cap_pairs = cap_pairs;
+  M.cap_cand = cap_cand;
   M.kb = kb;
   M.s_max = cuts.s_max;
   M.chi2_max = mc.chi2_max; M.max_dtanl = mc.max_dtanl; M.max_gap = mc.max_gap;
@@ -517,6 +687,7 @@ int enqueue_merge(const double* row_x_host, int n_rows, double kb, const tpct_cu
   M.c_s = cuts.c_s; M.c_t = cuts.c_t; M.c_yz_refit = cuts.c_yz_refit; M.c_qpt_refit = cuts.c_qpt_refit;
   M.sig_readout = cuts.sig_readout; M.sig_slope = (cuts.sig_cathode - cuts.sig_readout) / z_max; M.z_max = z_max;
   M.n_refit = cuts.n_refit;
+  M.sig_readout_f = (float)M.sig_readout; M.sig_slope_f = (float)M.sig_slope; M.z_max_f = (float)z_max;
   M.x = cl.x; M.y = cl.y; M.z = cl.z; M.row = cl.row;
   M.inst_sector = inst_sector; M.inst_event = inst_event;
   M.trk = trk;
@@ -527,7 +698,8 @@ int enqueue_merge(const double* row_x_host, int n_rows, double kb, const tpct_cu
   const int big = max(max(cap, n_events * 36), cl.n_instances) + 1;
   k_m_init<<<blocks_for(big, kBlock), kBlock, 0, s>>>(M); ++k;
   k_m_prep<<<blocks_for(max(cap, cl.n_instances), kBlock), kBlock, 0, s>>>(M); ++k;
-  k_m_pairs<<<max(1, n_events * 36), kBlock, 0, s>>>(M); ++k;
+  k_m_cand<<<max(1, n_events * 36), kBlock, 0, s>>>(M); ++k;
+  k_m_chi<<<blocks_for(cap_cand, kBlock), kBlock, 0, s>>>(M); ++k;
   k_m_best<<<blocks_for(cap_pairs, kBlock), kBlock, 0, s>>>(M); ++k;
   k_m_links<<<blocks_for(cap, kBlock), kBlock, 0, s>>>(M); ++k;
   k_m_heads<<<blocks_for(cap, kBlock), kBlock, 0, s>>>(M); ++k;
@@ -535,7 +707,11 @@ int enqueue_merge(const double* row_x_host, int n_rows, double kb, const tpct_cu
   launch_scan_i32(M.nseg, M.segoff, cap, M.scan_tmp, s); k += 3;
   launch_scan_i32(M.ncl, M.cloff, cap, M.scan_tmp, s); k += 3;
   k_m_emit<<<blocks_for(cap, kBlock), kBlock, 0, s>>>(M); ++k;
-  k_m_refit<<<blocks_for(cap, 128), 128, 0, s>>>(M); ++k;
+  k_m_len_count<<<blocks_for(cap, kBlock), kBlock, 0, s>>>(M); ++k;
+  k_m_len_scan<<<1, kLenBins, 0, s>>>(M); ++k;
+  k_m_len_scatter<<<blocks_for(cap, kBlock), kBlock, 0, s>>>(M); ++k;
+  if (cuts.n_refit >= 2) { k_m_refit<1><<<blocks_for(cap, 128), 128, 0, s>>>(M); ++k; }
+  k_m_refit<2><<<blocks_for(cap, 128), 128, 0, s>>>(M); ++k;
   return k;
 }
 
