@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-merge", action="store_true")
+    ap.add_argument("--no-clusters", action="store_true")
     ap.add_argument("--tuning-cache", default=None, help="autotuner cache file (default: a fresh temp file)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variants", default="mixed_df", help="comma-separated extra precisions timed in the same run")
@@ -232,6 +233,47 @@ def merge_leg(args, ev, G, trk, dc, out, stream):
     n_chains = int(ch.counts[0].item())
     return {"ms": mms, "tracks_in": n_tracks, "chains": n_chains,
             "tracks_per_s": n_tracks / (mms * 1e-3), "device_status": trk.device_status()}
+
+
+def cluster_leg(args, G, dev, stream, copies=4, reps=10):
+    """Cluster finding (the step upstream of track finding) on the digits of
+    the central Pb-Pb-like event, replicated `copies` times as independent
+    collisions so that the input (~430 MB) exceeds L2; mean CUDA-event time of
+    tpct_find_clusters over `reps` calls after 3 warm-ups."""
+    import torch
+    import synth.digits as D
+    dg = D.generate_digits(1, workers=min(16, os.cpu_count() or 1))
+    n_rk = dg.row_offsets.shape[0] - 1
+    offs = np.concatenate([dg.row_offsets[:-1] + c * dg.n for c in range(copies)] + [[copies * dg.n]])
+    rep = D.Digits(pad=np.tile(dg.pad, copies), time=np.tile(dg.time, copies), adc=np.tile(dg.adc, copies),
+                   row_offsets=offs.astype(np.int64), sectors=np.tile(dg.sectors, copies), readout=dg.readout,
+                   n_pad=dg.n_pad, truth={})
+    trk = G.Tracker(precision="mixed", device=dev)
+    dd = G.DeviceDigits.from_digits(rep, device=dev)
+    out = trk.find_clusters(dd)
+    for _ in range(2):
+        trk.find_clusters(dd, out=out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        trk.find_clusters(dd, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    h = out.counts.cpu().numpy()
+    n_cl = int(h[0])
+    # algorithmic bytes: pad, time, adc (6 B) per digit, one row offset (8 B)
+    # per row, the 36 B of each cluster written
+    bytes_alg = 6.0 * rep.n + 8.0 * (copies * n_rk + 1) + 36.0 * n_cl
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    ach = bytes_alg / (ms * 1e-3) / 1e9
+    return {"workload": f"central Pb-Pb-like event digits x{copies} ({rep.n} digits, {copies * n_rk} pad rows)",
+            "ms": ms, "digits_per_s": rep.n / (ms * 1e-3), "clusters": n_cl, "clusters_per_s": n_cl / (ms * 1e-3),
+            "status": int(h[1]),
+            "roofline": {"bound": "hbm", "kernel": "k_clusterer", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "algorithmic_bytes_per_launch": bytes_alg}}
 
 
 def serving_leg(args, ev, G, capacity_cps):
@@ -537,6 +579,8 @@ def main():
     # tracking chain, timed on its own; not part of `value`)
     if not args.no_merge and ev.sectors_per_event > 1:
         line["merge"] = merge_leg(args, ev, G, trk, dc, out, stream)
+    if not args.no_clusters:
+        line["cluster_finding"] = cluster_leg(args, G, dev, stream)
 
     variants = {}
     for vp in [v for v in args.variants.split(",") if v and v != args.precision]:

@@ -303,6 +303,74 @@ tpct_status tpct_merge(tpct_ctx* ctx, const tpct_clusters* clusters, const int32
                        const tpct_merge_cuts* cuts, void* workspace, size_t workspace_bytes,
                        tpct_chains_out* out, tpct_stream stream);
 
+/* ---------------------------------------------------------------- cluster finding */
+/* TPC cluster finding, the step upstream of track finding: zero-suppressed
+ * digits -> clusters.  The paper names clustering inside "TPC Processing
+ * (Tracking, Clustering, Compression)" (Table 1, 99.37 % of synchronous
+ * reconstruction) without describing it.  Readings: row r has
+ * n_pad = 2 ceil(x_r tan_half / pitch - 1e-9) pads (pitch: pad_pitch_inner
+ * below n_inner_rows, else pad_pitch_outer) and n_time time bins; a digit of
+ * charge q at (pad p, time t) is a PEAK iff q >= q_peak_min, q > each of its 8
+ * neighbours that comes before it in (time, pad) order and q >= the others
+ * (cells without a digit hold 0); a peak is DROPPED iff a higher peak (equal:
+ * the earlier one) lies at Chebyshev distance 2 and the cell one step from
+ * the peak towards it holds >= q - valley_delta (no valley between them); a
+ * kept peak's CLUSTER sums its 3x3 cells plus every cell of the distance-2
+ * ring whose inner neighbour towards the peak holds at least its charge:
+ * pad / time = peak + charge-weighted mean offset, sigma_pad / sigma_time =
+ * the charge-weighted standard deviation, q_tot = the sum, q_max = the peak
+ * charge, y = (pad + 0.5 - n_pad/2) * pitch, z = +-(z_max - (time + 0.5) *
+ * time_bin) on side A / C (instance sector < 18 / >= 18), x = the row
+ * radius of the context's geometry. */
+typedef struct {
+  double pad_pitch_inner;      /* [cm] (0.4) */
+  double pad_pitch_outer;      /* [cm] (0.6) */
+  int32_t n_inner_rows;        /* rows with the inner pitch (63) */
+  double time_bin;             /* drift length per time bin [cm] (0.5) */
+  int32_t n_time;              /* time bins per row (500); n_pad x n_time must fit in shared memory */
+  int32_t q_peak_min;          /* (7) */
+  int32_t valley_delta;        /* (2) */
+} tpct_cf_params;
+void tpct_default_cf_params(tpct_cf_params* p);
+
+/* Digits (device, caller-owned, read-only): SoA, grouped by (instance, row),
+ * any order inside a row, each (pad, time) cell at most once per row. */
+typedef struct {
+  const uint16_t *pad, *time, *adc;
+  const int64_t* row_offsets;  /* [n_instances * n_rows + 1] */
+  const int32_t* inst_sector;  /* [n_instances] sector number 0..35 of each instance */
+  int32_t n_instances;
+} tpct_digits;
+
+/* Clusters (device, caller-owned): SoA in (instance, row) order, inside a
+ * row in the input order of the peak digits; x, y, z are the tracker's
+ * cluster input (tpct_clusters) for these instances. */
+typedef struct {
+  int32_t capacity;
+  int32_t* n_clusters;         /* [1] always written (may exceed capacity) */
+  uint32_t* status;            /* [1] TPCT_CF_* bits, zeroed by each call */
+  float *x, *y, *z, *pad, *time, *sigma_pad, *sigma_time;
+  uint32_t* q_tot;
+  uint16_t* q_max;
+  uint8_t *row, *flags;        /* flags: 1 = peak on the first/last pad, 2 = on the first/last time bin */
+  int64_t* inst_offsets;       /* [n_instances + 1] first cluster of each instance (may be NULL) */
+} tpct_cf_out;
+#define TPCT_CF_BAD_DIGIT 1u      /* a digit outside its row's pads or time bins (skipped) */
+#define TPCT_CF_TIMEOUT 2u        /* a bounded wait for a preceding row gave up (offsets invalid) */
+#define TPCT_CF_ROW_OVERFLOW 4u   /* a row had more than 8192 clusters (the rest not written) */
+#define TPCT_CF_CAPACITY 8u       /* more clusters than capacity (the rest not written) */
+
+/* Device workspace of tpct_find_clusters for n_instances instances. */
+size_t tpct_cf_workspace_bytes(int32_t n_instances, int32_t n_rows);
+
+/* Find the clusters of all rows of all instances; asynchronous on `stream`.
+ * TPCT_E_INVALID for bad arguments or readout parameters whose largest row
+ * map does not fit in one block's shared memory; TPCT_E_NOMEM if the
+ * workspace (256-byte aligned) is smaller than tpct_cf_workspace_bytes.
+ * Device conditions are reported in *out->status. */
+tpct_status tpct_find_clusters(tpct_ctx* ctx, const tpct_digits* digits, const tpct_cf_params* params,
+                               void* workspace, size_t workspace_bytes, tpct_cf_out* out, tpct_stream stream);
+
 /* ---------------------------------------------------------------- serving */
 /* A serving runtime: time frames (batches of sector instances) submitted from
  * host memory are tracked concurrently in up to n_slots streams.  A frame is

@@ -15,6 +15,10 @@ Parity status of each oracle function (what pins it, in tests/test_oracle_*):
   whole tracker     generator truth (efficiency, fake rate, chi2/ndf, pulls);
                     the absolute efficiency level is parity unpinned (the paper
                     prints no tracking-efficiency number)
+  cluster finding   hand-computed fixture (tests/golden/cf_hand_fixture.json);
+                    generator truth of isolated crossings (efficiency,
+                    centroid residuals, charge); translation and input-order
+                    invariance
 """
 import ctypes
 import os
@@ -24,6 +28,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tpct_oracle.c")
+_SRC_CF = os.path.join(_HERE, "cluster_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libtpct_oracle.so")
 _lib = None
 
@@ -43,10 +48,10 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "tpct_oracle.h"))):
+            os.path.getmtime(_SRC), os.path.getmtime(_SRC_CF), os.path.getmtime(os.path.join(_HERE, "tpct_oracle.h"))):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+                               "-fno-fast-math", "-o", tmp, _SRC, _SRC_CF, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -346,3 +351,89 @@ def kf_update(p, C, my, mz, vy, vz):
     C = np.ascontiguousarray(C, dtype=np.float64).copy()
     chi2 = L.orc_kf_update(_ptr(p), _ptr(C), my, mz, vy, vz)
     return chi2, p, C
+
+
+# ---------------------------------------------------------------- cluster finding
+class _CfParams(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int), ("row_x", ctypes.POINTER(ctypes.c_double)),
+                ("tan_half", ctypes.c_double), ("z_max", ctypes.c_double),
+                ("pad_pitch_inner", ctypes.c_double), ("pad_pitch_outer", ctypes.c_double),
+                ("n_inner_rows", ctypes.c_int), ("time_bin", ctypes.c_double), ("n_time", ctypes.c_int),
+                ("q_peak_min", ctypes.c_int), ("valley_delta", ctypes.c_int)]
+
+
+@dataclass
+class CfParams:
+    """Readings of cluster finding (see cluster_oracle.c): readout geometry,
+    peak threshold and valley depth."""
+    pad_pitch_inner: float = 0.4
+    pad_pitch_outer: float = 0.6
+    n_inner_rows: int = 63
+    time_bin: float = 0.5
+    n_time: int = 500
+    q_peak_min: int = 7
+    valley_delta: int = 2
+
+
+(OCF_X, OCF_Y, OCF_Z, OCF_PAD, OCF_TIME, OCF_SPAD, OCF_STIME, OCF_QTOT, OCF_QMAX, OCF_ROW, OCF_FLAGS,
+ OCF_INST, OCF_PEAK) = range(13)
+_CF_FIELDS = [("x", OCF_X, np.float64), ("y", OCF_Y, np.float64), ("z", OCF_Z, np.float64),
+              ("pad", OCF_PAD, np.float64), ("time", OCF_TIME, np.float64), ("sigma_pad", OCF_SPAD, np.float64),
+              ("sigma_time", OCF_STIME, np.float64), ("q_tot", OCF_QTOT, np.uint32),
+              ("q_max", OCF_QMAX, np.uint16), ("row", OCF_ROW, np.uint8), ("flags", OCF_FLAGS, np.uint8),
+              ("instance", OCF_INST, np.int32), ("peak", OCF_PEAK, np.int64)]
+
+
+class ClusterResult:
+    """Clusters of the oracle (numpy arrays, one entry per cluster)."""
+
+    def __init__(self, fields):
+        self.__dict__.update(fields)
+
+    @property
+    def n(self):
+        return int(self.instance.shape[0])
+
+
+def find_clusters(digits, params: CfParams = None, geometry=None) -> ClusterResult:
+    """Cluster finding on a synth.digits.Digits (or an object with the same
+    fields: pad, time, adc, row_offsets, sectors)."""
+    from synth import default_geometry
+    L = lib()
+    if not getattr(L, "_cf_ready", False):
+        L.orc_find_clusters.restype = ctypes.c_void_p
+        L.orc_find_clusters.argtypes = [ctypes.POINTER(_CfParams), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_int)]
+        L.orc_cf_count.restype = ctypes.c_int64
+        L.orc_cf_count.argtypes = [ctypes.c_void_p]
+        L.orc_cf_array.restype = ctypes.c_void_p
+        L.orc_cf_array.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_cf_free.argtypes = [ctypes.c_void_p]
+        L._cf_ready = True
+    g = geometry or default_geometry()
+    prm = params or CfParams()
+    row_x = np.ascontiguousarray(g.row_x, dtype=np.float64)
+    cp = _CfParams(g.n_rows, row_x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), g.tan_half_sector, g.z_max,
+                   prm.pad_pitch_inner, prm.pad_pitch_outer, prm.n_inner_rows, prm.time_bin, prm.n_time,
+                   prm.q_peak_min, prm.valley_delta)
+    pad = np.ascontiguousarray(digits.pad, dtype=np.uint16)
+    tim = np.ascontiguousarray(digits.time, dtype=np.uint16)
+    adc = np.ascontiguousarray(digits.adc, dtype=np.uint16)
+    offs = np.ascontiguousarray(digits.row_offsets, dtype=np.int64)
+    sec = np.ascontiguousarray(digits.sectors, dtype=np.int32)
+    err = ctypes.c_int(0)
+    h = L.orc_find_clusters(ctypes.byref(cp), int(sec.shape[0]), _ptr(sec), _ptr(offs), _ptr(pad), _ptr(tim),
+                            _ptr(adc), ctypes.byref(err))
+    if not h:
+        raise ValueError(f"oracle cluster finding failed (code {err.value})")
+    try:
+        n = int(L.orc_cf_count(h))
+        out = {}
+        for name, w, dt in _CF_FIELDS:
+            p = L.orc_cf_array(h, w)
+            out[name] = (np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(np.ctypeslib.as_ctypes_type(dt))),
+                                                shape=(n,)).copy() if n and p else np.zeros(0, dt))
+    finally:
+        L.orc_cf_free(h)
+    return ClusterResult(out)

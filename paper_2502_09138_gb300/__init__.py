@@ -150,6 +150,76 @@ class Chains:
                     link_in=g(self.link_in, n_tracks))
 
 
+def default_cf_params(**over) -> B.CfParams:
+    p = B.CfParams()
+    B.load().tpct_default_cf_params(ctypes.byref(p))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+class DeviceDigits:
+    """Digits on the device (SoA uint16 pad, time, adc; int64 row offsets per
+    (instance, row); int32 sector of each instance)."""
+
+    def __init__(self, pad, time, adc, row_offsets, inst_sector):
+        self.pad, self.time, self.adc = pad, time, adc
+        self.row_offsets, self.inst_sector = row_offsets, inst_sector
+
+    @property
+    def n(self):
+        return int(self.adc.shape[0])
+
+    @property
+    def n_instances(self):
+        return int(self.inst_sector.shape[0])
+
+    @classmethod
+    def from_digits(cls, dg, device="cuda"):
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).to(device)
+        # uint16 arrays travel as int16 bit patterns (torch has no uint16 arithmetic)
+        u16 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint16).view(np.int16)).to(device)
+        return cls(u16(dg.pad), u16(dg.time), u16(dg.adc), t(dg.row_offsets, np.int64), t(dg.sectors, np.int32))
+
+    def as_struct(self) -> B.Digits:
+        return B.Digits(_ptr(self.pad), _ptr(self.time), _ptr(self.adc), _ptr(self.row_offsets),
+                        _ptr(self.inst_sector), self.n_instances)
+
+
+class ClusterOut:
+    """Cluster-finding output buffers (device)."""
+    FIELDS = (("x", torch.float32), ("y", torch.float32), ("z", torch.float32), ("pad", torch.float32),
+              ("time", torch.float32), ("sigma_pad", torch.float32), ("sigma_time", torch.float32),
+              ("q_tot", torch.int32), ("q_max", torch.int16), ("row", torch.uint8), ("flags", torch.uint8))
+
+    def __init__(self, capacity, n_instances, device):
+        self.capacity = int(capacity)
+        self.counts = torch.zeros(2, dtype=torch.int32, device=device)   # n_clusters, status
+        c = max(1, self.capacity)
+        for name, dt in self.FIELDS:
+            setattr(self, name, torch.empty(c, dtype=dt, device=device))
+        self.inst_offsets = torch.zeros(n_instances + 1, dtype=torch.int64, device=device)
+
+    def as_struct(self) -> B.CfOut:
+        base = self.counts.data_ptr()
+        return B.CfOut(self.capacity, ctypes.c_void_p(base), ctypes.c_void_p(base + 4),
+                       *[_ptr(getattr(self, n)) for n, _ in self.FIELDS], _ptr(self.inst_offsets))
+
+    def to_host(self):
+        counts = self.counts.cpu().numpy()
+        n = int(min(counts[0], self.capacity))
+        out = {"n_clusters": int(counts[0]), "status": int(counts[1]) & 0xffffffff,
+               "inst_offsets": self.inst_offsets.cpu().numpy()}
+        for name, _ in self.FIELDS:
+            a = getattr(self, name)[:n].cpu().numpy()
+            if name == "q_tot":
+                a = a.view(np.uint32)
+            elif name == "q_max":
+                a = a.view(np.uint16)
+            out[name] = a
+        return out
+
+
 class Debug:
     """Intermediate arrays for parity checks (device tensors)."""
 
@@ -301,6 +371,26 @@ class Tracker:
         B.check(B.load().tpct_merge(self._h, ctypes.byref(cs), _ptr(sec), _ptr(evi), int(n_events), ctypes.byref(ts),
                                     ctypes.byref(cuts), ctypes.c_void_p(base), nb, ctypes.byref(os_),
                                     ctypes.c_void_p(s.cuda_stream)), "tpct_merge", self._h)
+        return out
+
+    def find_clusters(self, digits: "DeviceDigits", params=None, out: "ClusterOut" = None, capacity=None,
+                      stream=None):
+        """Cluster finding on device digits (rows of this tracker's geometry)."""
+        params = params or default_cf_params()
+        lib = B.load()
+        nb = int(lib.tpct_cf_workspace_bytes(digits.n_instances, self.n_rows))
+        if getattr(self, "_cfws", None) is None or self._cfws.numel() < nb + 256:
+            self._cfws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        base = (self._cfws.data_ptr() + 255) // 256 * 256
+        if out is None:
+            out = ClusterOut(capacity if capacity is not None else digits.n // 4 + 1024, digits.n_instances,
+                             self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._keep_cf = (digits, out)
+        ds, os_ = digits.as_struct(), out.as_struct()
+        B.check(lib.tpct_find_clusters(self._h, ctypes.byref(ds), ctypes.byref(params), ctypes.c_void_p(base), nb,
+                                       ctypes.byref(os_), ctypes.c_void_p(s.cuda_stream)),
+                "tpct_find_clusters", self._h)
         return out
 
     def set_stage_events(self, events):

@@ -63,6 +63,26 @@ class ChainsOut(ctypes.Structure):
                 ("cluster_ids", c_void_p), ("link_out", c_void_p), ("link_in", c_void_p)]
 
 
+class CfParams(ctypes.Structure):
+    _fields_ = [("pad_pitch_inner", c_double), ("pad_pitch_outer", c_double), ("n_inner_rows", c_int32),
+                ("time_bin", c_double), ("n_time", c_int32), ("q_peak_min", c_int32), ("valley_delta", c_int32)]
+
+
+class Digits(ctypes.Structure):
+    _fields_ = [("pad", c_void_p), ("time", c_void_p), ("adc", c_void_p), ("row_offsets", c_void_p),
+                ("inst_sector", c_void_p), ("n_instances", c_int32)]
+
+
+class CfOut(ctypes.Structure):
+    _fields_ = [("capacity", c_int32), ("n_clusters", c_void_p), ("status", c_void_p), ("x", c_void_p),
+                ("y", c_void_p), ("z", c_void_p), ("pad", c_void_p), ("time", c_void_p), ("sigma_pad", c_void_p),
+                ("sigma_time", c_void_p), ("q_tot", c_void_p), ("q_max", c_void_p), ("row", c_void_p),
+                ("flags", c_void_p), ("inst_offsets", c_void_p)]
+
+
+TPCT_CF_BAD_DIGIT, TPCT_CF_TIMEOUT, TPCT_CF_ROW_OVERFLOW, TPCT_CF_CAPACITY = 1, 2, 4, 8
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("n_slots", c_int), ("arena", c_void_p), ("arena_bytes", c_size_t)]
 
@@ -120,6 +140,10 @@ EXPORTS = {
     "tpct_merge": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_void_p, c_void_p, c_int32, ctypes.POINTER(TracksOut),
                            ctypes.POINTER(MergeCuts), c_void_p, c_size_t, ctypes.POINTER(ChainsOut), c_void_p]),
     "tpct_get_tuning": (c_int, [c_void_p, ctypes.POINTER(Tuning)]),
+    "tpct_default_cf_params": (None, [ctypes.POINTER(CfParams)]),
+    "tpct_cf_workspace_bytes": (c_size_t, [c_int32, c_int32]),
+    "tpct_find_clusters": (c_int, [c_void_p, ctypes.POINTER(Digits), ctypes.POINTER(CfParams), c_void_p, c_size_t,
+                                   ctypes.POINTER(CfOut), c_void_p]),
     "tpct_autotune": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut), c_void_p,
                               ctypes.c_char_p, ctypes.POINTER(Tuning)]),
     "tpct_server_create": (c_int, [ctypes.POINTER(Geometry), c_double, ctypes.POINTER(Cuts), c_int,

@@ -505,6 +505,37 @@ tpct_status tpct_merge(tpct_ctx* ctx, const tpct_clusters* cl, const int32_t* in
   return fail_cuda(ctx, cudaGetLastError());
 }
 
+void tpct_default_cf_params(tpct_cf_params* p) {
+  if (!p) return;
+  p->pad_pitch_inner = 0.4; p->pad_pitch_outer = 0.6; p->n_inner_rows = 63;
+  p->time_bin = 0.5; p->n_time = 500; p->q_peak_min = 7; p->valley_delta = 2;
+}
+
+size_t tpct_cf_workspace_bytes(int32_t n_instances, int32_t n_rows) {
+  if (n_instances < 0 || n_rows < 1) return 0;
+  return cf_workspace_bytes(n_instances, n_rows);
+}
+
+tpct_status tpct_find_clusters(tpct_ctx* ctx, const tpct_digits* dg, const tpct_cf_params* prm, void* ws,
+                               size_t ws_bytes, tpct_cf_out* out, tpct_stream stream) {
+  if (!ctx || !dg || !prm || !ws || !out || dg->n_instances < 0 || ((uintptr_t)ws % kAlign)) return TPCT_E_INVALID;
+  if (dg->n_instances > 0 && (!dg->pad || !dg->time || !dg->adc || !dg->row_offsets || !dg->inst_sector))
+    return TPCT_E_INVALID;
+  if (!out->n_clusters || !out->status || out->capacity < 0) return TPCT_E_INVALID;
+  if (out->capacity > 0 && (!out->x || !out->y || !out->z || !out->pad || !out->time || !out->sigma_pad ||
+                            !out->sigma_time || !out->q_tot || !out->q_max || !out->row || !out->flags))
+    return TPCT_E_INVALID;
+  if (prm->q_peak_min < 1 || prm->valley_delta < 0 || prm->n_inner_rows < 0) return TPCT_E_INVALID;
+  cudaError_t err = cudaSuccess;
+  const int k = enqueue_clusters(ctx->row_x.data(), ctx->n_rows, ctx->tan_half, ctx->z_max, *prm, *dg, ws,
+                                 ws_bytes, *out, (cudaStream_t)stream, &err);
+  if (k == -1 || k == -3) return TPCT_E_INVALID;
+  if (k == -2) return TPCT_E_NOMEM;
+  if (k < 0) return fail_cuda(ctx, err);
+  ctx->launches += k;
+  return TPCT_OK;
+}
+
 tpct_status tpct_get_tuning(const tpct_ctx* ctx, tpct_tuning* t) {
   if (!ctx || !t) return TPCT_E_INVALID;
   t->clusters_per_bin = ctx->clusters_per_bin;

@@ -1,0 +1,324 @@
+// TPC cluster finding: zero-suppressed digits (pad, time bin, ADC) of each
+// pad row -> clusters (charge-weighted centroid and width, total and peak
+// charge, local position).  The paper names clustering as part of "TPC
+// Processing (Tracking, Clustering, Compression)" (Table 1); the steps are
+// the stated readings:
+//   peak      q >= q_peak_min, q > every 3x3 neighbour that comes before it in
+//             (time, pad) order and q >= every later one;
+//   valley    a peak is dropped if a higher peak (ties: the earlier one) lies
+//             at Chebyshev distance 2 and the cell between them holds at least
+//             q - valley_delta;
+//   cluster   the 3x3 cells around a kept peak plus each outer-ring cell whose
+//             inner neighbour towards the peak holds at least its charge.
+// Clusters of a row come in the input order of their peak digits; rows in
+// (instance, row) order.
+//
+// GB300 mapping: a persistent kernel with one 1024-thread CTA per SM.  A CTA
+// takes whole pad rows from a device work counter and keeps the row's charge
+// map (n_pad x n_time u16, 140 KB for the outermost row) and a peak bitmap in
+// shared memory: digits are scattered in once from HBM (coalesced), every
+// neighbourhood test then reads shared memory only, and the map is cleared by
+// re-scattering zeros at the same cells.  Output positions come from a
+// single-pass decoupled look-back over the rows (each row publishes its
+// cluster count, then its inclusive prefix), so clusters are written once,
+// densely and in order.  Waits in the look-back are bounded; a timeout sets a
+// status bit.
+#include "tpct_internal.cuh"
+
+namespace tpct {
+namespace {
+
+constexpr int kCfThreads = 1024;
+constexpr int kCfMaxPeaks = 8192;          // kept peaks per row held in shared memory
+constexpr int kCfMaxSpins = 1 << 22;       // look-back polls before giving up
+constexpr uint64_t kLbAgg = 1ull << 62, kLbInc = 2ull << 62, kLbMask = (1ull << 62) - 1;
+
+struct CfDev {
+  const uint16_t *pad, *time, *adc;
+  const int64_t* row_offsets;
+  const int32_t* inst_sector;
+  int32_t n_inst, n_rows, n_time, np_max;
+  int32_t q_peak_min, valley_delta;
+  float z_max, time_bin;
+  uint32_t map_words, bit_words;            // shared-memory layout (32-bit words)
+  uint64_t* lookback;                       // [n_inst * n_rows]
+  uint32_t* work;                           // [1]
+  int16_t n_pad[kMaxRows];
+  float pitch[kMaxRows], row_x[kMaxRows];
+  tpct_cf_out out;
+};
+
+__device__ __forceinline__ int qat(const uint16_t* map, int np, int nt, int p, int t) {
+  return (p < 0 || p >= np || t < 0 || t >= nt) ? 0 : (int)map[p * nt + t];
+}
+__device__ __forceinline__ bool before(int p1, int t1, int p0, int t0) { return t1 < t0 || (t1 == t0 && p1 < p0); }
+__device__ __forceinline__ int half_step(int d) { return d == 2 ? 1 : (d == -2 ? -1 : 0); }
+__device__ __forceinline__ bool bit_at(const uint32_t* bits, int cell) { return (bits[cell >> 5] >> (cell & 31)) & 1u; }
+
+__device__ bool peak_test(const uint16_t* map, int np, int nt, int p, int t, int qmin) {
+  const int q = qat(map, np, nt, p, t);
+  if (q < qmin) return false;
+#pragma unroll
+  for (int dt = -1; dt <= 1; ++dt)
+#pragma unroll
+    for (int dp = -1; dp <= 1; ++dp) {
+      if (dp == 0 && dt == 0) continue;
+      const int qn = qat(map, np, nt, p + dp, t + dt);
+      if (dt < 0 || (dt == 0 && dp < 0) ? !(q > qn) : !(q >= qn)) return false;
+    }
+  return true;
+}
+
+__device__ bool suppressed(const uint16_t* map, const uint32_t* bits, int np, int nt, int p, int t, int delta) {
+  const int q = qat(map, np, nt, p, t);
+#pragma unroll
+  for (int dt = -2; dt <= 2; ++dt)
+#pragma unroll
+    for (int dp = -2; dp <= 2; ++dp) {
+      if (dp > -2 && dp < 2 && dt > -2 && dt < 2) continue;   // the Chebyshev-2 ring only
+      const int p2 = p + dp, t2 = t + dt;
+      if (p2 < 0 || p2 >= np || t2 < 0 || t2 >= nt || !bit_at(bits, p2 * nt + t2)) continue;
+      const int q2 = map[p2 * nt + t2];
+      if (!(q2 > q || (q2 == q && before(p2, t2, p, t)))) continue;
+      if (qat(map, np, nt, p + half_step(dp), t + half_step(dt)) >= q - delta) return true;
+    }
+  return false;
+}
+
+__device__ __forceinline__ uint64_t ld_volatile(const uint64_t* a) {
+  return *reinterpret_cast<const volatile unsigned long long*>(a);
+}
+
+__global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_constant__ CfDev P) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint16_t* map = reinterpret_cast<uint16_t*>(smem);
+  uint32_t* bits = smem + P.map_words;
+  int32_t* peaks = reinterpret_cast<int32_t*>(bits + P.bit_words);
+  __shared__ int s_row;
+  __shared__ int s_warp[kCfThreads / 32];
+  __shared__ long long s_base;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nt = P.n_time;
+  const int n_rows_total = P.n_inst * P.n_rows;
+  const tpct_cf_out& O = P.out;
+
+  for (uint32_t i = tid; i < P.map_words + P.bit_words; i += kCfThreads) smem[i] = 0u;
+  __syncthreads();
+
+  while (true) {
+    if (tid == 0) s_row = (int)atomicAdd(P.work, 1u);
+    __syncthreads();
+    const int row = s_row;
+    if (row >= n_rows_total) break;
+    const int r = row % P.n_rows, inst = row / P.n_rows;
+    const int64_t b = P.row_offsets[row], e = P.row_offsets[row + 1];
+    const int np = P.n_pad[r];
+
+    // the row's charge map
+    for (int64_t i = b + tid; i < e; i += kCfThreads) {
+      const int p = P.pad[i], t = P.time[i];
+      if (p < np && t < nt) map[p * nt + t] = P.adc[i];
+      else atomicOr(O.status, TPCT_CF_BAD_DIGIT);
+    }
+    __syncthreads();
+    // peaks
+    for (int64_t i = b + tid; i < e; i += kCfThreads) {
+      const int p = P.pad[i], t = P.time[i];
+      if (p < np && t < nt && peak_test(map, np, nt, p, t, P.q_peak_min)) {
+        const int cell = p * nt + t;
+        atomicOr(&bits[cell >> 5], 1u << (cell & 31));
+      }
+    }
+    __syncthreads();
+    // kept peaks, compacted in input order
+    int count = 0;
+    for (int64_t base = b; base < e; base += kCfThreads) {
+      const int64_t i = base + tid;
+      bool keep = false;
+      if (i < e) {
+        const int p = P.pad[i], t = P.time[i];
+        keep = p < np && t < nt && bit_at(bits, p * nt + t) &&
+               !suppressed(map, bits, np, nt, p, t, P.valley_delta);
+      }
+      const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) s_warp[warp] = __popc(ball);
+      __syncthreads();
+      if (warp == 0) {
+        const int v = s_warp[lane];
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += u;
+        }
+        s_warp[lane] = incl - v;                 // exclusive prefix of the warps
+        if (lane == 31) s_base = incl;           // block total (read below, before the next write)
+      }
+      __syncthreads();
+      if (keep) {
+        const int rank = count + s_warp[warp] + __popc(ball & ((1u << lane) - 1u));
+        if (rank < kCfMaxPeaks) peaks[rank] = (int)(i - b);
+      }
+      count += (int)s_base;
+      __syncthreads();
+    }
+    if (count > kCfMaxPeaks && tid == 0) atomicOr(O.status, TPCT_CF_ROW_OVERFLOW);
+
+    // decoupled look-back: publish the count, add the predecessors' counts
+    // until an inclusive prefix is found, publish the inclusive prefix
+    if (tid == 0) {
+      long long prefix = 0;
+      if (row == 0) {
+        __threadfence();
+        atomicExch((unsigned long long*)&P.lookback[0], (unsigned long long)(kLbInc | (uint64_t)count));
+      } else {
+        __threadfence();
+        atomicExch((unsigned long long*)&P.lookback[row], (unsigned long long)(kLbAgg | (uint64_t)count));
+        int j = row - 1, spins = 0;
+        while (j >= 0) {
+          const uint64_t v = ld_volatile(&P.lookback[j]);
+          const uint64_t st = v >> 62;
+          if (st == 0) {
+            if (++spins > kCfMaxSpins) { atomicOr(O.status, TPCT_CF_TIMEOUT); break; }
+            __nanosleep(64);
+            continue;
+          }
+          prefix += (long long)(v & kLbMask);
+          if (st == 2) break;
+          --j;
+        }
+        __threadfence();
+        atomicExch((unsigned long long*)&P.lookback[row],
+                   (unsigned long long)(kLbInc | (uint64_t)(prefix + count)));
+      }
+      s_base = prefix;
+      if (r == 0 && O.inst_offsets) O.inst_offsets[inst] = prefix;
+      if (row == n_rows_total - 1) {
+        *O.n_clusters = (int32_t)min(prefix + count, (long long)0x7fffffff);
+        if (O.inst_offsets) O.inst_offsets[P.n_inst] = prefix + count;
+        if (prefix + count > O.capacity) atomicOr(O.status, TPCT_CF_CAPACITY);
+      }
+    }
+    __syncthreads();
+    const long long base_out = s_base;
+    const int nk = min(count, kCfMaxPeaks);
+    const float pitch = P.pitch[r];
+    const float side = P.inst_sector[inst] >= 18 ? -1.f : 1.f;
+    for (int k = tid; k < nk; k += kCfThreads) {
+      const long long slot = base_out + k;
+      if (slot >= O.capacity) break;
+      const int64_t i = b + peaks[k];
+      const int p = P.pad[i], t = P.time[i];
+      int s0 = 0, sp = 0, st = 0, spp = 0, stt = 0;
+#pragma unroll
+      for (int dt = -2; dt <= 2; ++dt)
+#pragma unroll
+        for (int dp = -2; dp <= 2; ++dp) {
+          const int qc = qat(map, np, nt, p + dp, t + dt);
+          if (qc <= 0) continue;
+          if ((dp == 2 || dp == -2 || dt == 2 || dt == -2) &&
+              !(qc <= qat(map, np, nt, p + half_step(dp), t + half_step(dt))))
+            continue;
+          s0 += qc; sp += qc * dp; st += qc * dt; spp += qc * dp * dp; stt += qc * dt * dt;
+        }
+      const float fs0 = (float)s0;
+      const float mp = __fdiv_rn((float)sp, fs0), mt = __fdiv_rn((float)st, fs0);
+      const float vp = fmaxf(__fdiv_rn((float)spp, fs0) - mp * mp, 0.f);
+      const float vt = fmaxf(__fdiv_rn((float)stt, fs0) - mt * mt, 0.f);
+      const float cp = (float)p + mp, ct = (float)t + mt;
+      O.pad[slot] = cp;
+      O.time[slot] = ct;
+      O.sigma_pad[slot] = sqrtf(vp);
+      O.sigma_time[slot] = sqrtf(vt);
+      O.x[slot] = P.row_x[r];
+      O.y[slot] = (cp + 0.5f - 0.5f * (float)np) * pitch;
+      O.z[slot] = side * (P.z_max - (ct + 0.5f) * P.time_bin);
+      O.q_tot[slot] = (uint32_t)s0;
+      O.q_max[slot] = (uint16_t)map[p * nt + t];
+      O.row[slot] = (uint8_t)r;
+      O.flags[slot] = (uint8_t)((p == 0 || p == np - 1 ? 1 : 0) | (t == 0 || t == nt - 1 ? 2 : 0));
+    }
+    __syncthreads();
+    // clear the row's cells and peak bits
+    for (int64_t i = b + tid; i < e; i += kCfThreads) {
+      const int p = P.pad[i], t = P.time[i];
+      if (p < np && t < nt) {
+        const int cell = p * nt + t;
+        map[cell] = 0;
+        bits[cell >> 5] = 0u;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// Host side ------------------------------------------------------------------
+
+int cf_pads(double row_x, double tan_half, double pitch) {
+  return 2 * (int)std::ceil(row_x * tan_half / pitch - 1e-9);
+}
+
+size_t cf_smem_bytes(int np_max, int n_time) {
+  const size_t map_words = ((size_t)np_max * n_time + 1) / 2;
+  const size_t bit_words = ((size_t)np_max * n_time + 31) / 32;
+  return 4 * (map_words + bit_words) + 4 * (size_t)kCfMaxPeaks;
+}
+
+// Enqueue cluster finding; returns the kernels launched, or -1 (invalid
+// readout), -2 (workspace too small), -3 (shared memory too large), -4 (CUDA).
+int enqueue_clusters(const double* row_x, int n_rows, double tan_half, double z_max, const tpct_cf_params& prm,
+                     const tpct_digits& dg, void* ws, size_t ws_bytes, const tpct_cf_out& out, cudaStream_t s,
+                     cudaError_t* err) {
+  if (n_rows < 1 || n_rows > kMaxRows || prm.n_time < 1 || prm.n_time > 65535 || !(prm.time_bin > 0) ||
+      !(prm.pad_pitch_inner > 0) || !(prm.pad_pitch_outer > 0))
+    return -1;
+  CfDev P{};
+  int np_max = 0;
+  for (int r = 0; r < n_rows; ++r) {
+    const double pitch = r < prm.n_inner_rows ? prm.pad_pitch_inner : prm.pad_pitch_outer;
+    const int np = cf_pads(row_x[r], tan_half, pitch);
+    if (np < 1 || np > 32767) return -1;
+    P.n_pad[r] = (int16_t)np;
+    P.pitch[r] = (float)pitch;
+    P.row_x[r] = (float)row_x[r];
+    np_max = np > np_max ? np : np_max;
+  }
+  const size_t smem = cf_smem_bytes(np_max, prm.n_time);
+  int dev = 0, max_optin = 0, n_sm = 0;
+  if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return -4;
+  if ((*err = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return -4;
+  if ((*err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return -4;
+  if (smem + 2048 > (size_t)max_optin) return -3;
+  const size_t n_rows_total = (size_t)dg.n_instances * n_rows;
+  const size_t need = 8 * n_rows_total + 256;
+  if (ws_bytes < need) return -2;
+  P.pad = dg.pad; P.time = dg.time; P.adc = dg.adc; P.row_offsets = dg.row_offsets; P.inst_sector = dg.inst_sector;
+  P.n_inst = dg.n_instances; P.n_rows = n_rows; P.n_time = prm.n_time; P.np_max = np_max;
+  P.q_peak_min = prm.q_peak_min; P.valley_delta = prm.valley_delta;
+  P.z_max = (float)z_max; P.time_bin = (float)prm.time_bin;
+  P.map_words = (uint32_t)(((size_t)np_max * prm.n_time + 1) / 2);
+  P.bit_words = (uint32_t)(((size_t)np_max * prm.n_time + 31) / 32);
+  P.work = (uint32_t*)ws;
+  P.lookback = (uint64_t*)((char*)ws + 256);
+  P.out = out;
+  if ((*err = cudaFuncSetAttribute(k_clusterer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return -4;
+  int k = 0;
+  cudaMemsetAsync(ws, 0, need, s);
+  cudaMemsetAsync(out.status, 0, sizeof(uint32_t), s);
+  cudaMemsetAsync(out.n_clusters, 0, sizeof(int32_t), s);
+  if (n_rows_total > 0) {
+    const int grid = (int)std::min<size_t>((size_t)n_sm, n_rows_total);
+    k_clusterer<<<grid, kCfThreads, smem, s>>>(P); ++k;
+  }
+  *err = cudaGetLastError();
+  return *err == cudaSuccess ? k : -4;
+}
+
+size_t cf_workspace_bytes(int32_t n_instances, int32_t n_rows) {
+  return 8 * (size_t)n_instances * n_rows + 256;
+}
+
+}  // namespace tpct

@@ -202,6 +202,10 @@ void launch_tracklets(const Params& P, int mode, int block, int blocks, cudaStre
 int tracklet_blocks_per_sm(int mode, int block);
 int refit_blocks_per_sm(int mode, int block);
 void launch_weights(const Params& P, cudaStream_t s);
+int enqueue_clusters(const double* row_x, int n_rows, double tan_half, double z_max, const tpct_cf_params& prm,
+                     const tpct_digits& dg, void* ws, size_t ws_bytes, const tpct_cf_out& out, cudaStream_t s,
+                     cudaError_t* err);
+size_t cf_workspace_bytes(int32_t n_instances, int32_t n_rows);
 void launch_own(const Params& P, cudaStream_t s);
 void launch_emit(const Params& P, cudaStream_t s);
 // stage 0: all refit passes; 1: all but the last (PS/PE/PC types); 2: the last

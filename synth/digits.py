@@ -94,11 +94,68 @@ def _phi(x):
     return 0.5 * (1.0 + erf(x / math.sqrt(2.0)))
 
 
-def digitize(ev, readout: Readout = None, seed: int = None, shuffle: bool = True) -> Digits:
+def _instance_digits(args):
+    """Digit cells (local key (row * 256 + pad) * 512 + time) and ADC values
+    of one sector instance."""
+    i, seed, ro, n_pad_row, row, u, v, su, sv, amp, shuffle = args
+    cells_per_inst = N_ROWS * 256 * 512
+    if row.shape[0] == 0:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    p0 = np.rint(u).astype(np.int64)
+    t0 = np.rint(v).astype(np.int64)
+    offs = np.arange(-WINDOW, WINDOW + 1)
+    pc = p0[:, None] + offs[None, :]                      # [hits, 5]
+    tc = t0[:, None] + offs[None, :]
+    fu = _phi((pc + 0.5 - u[:, None]) / su[:, None]) - _phi((pc - 0.5 - u[:, None]) / su[:, None])
+    fv = _phi((tc + 0.5 - v[:, None]) / sv[:, None]) - _phi((tc - 0.5 - v[:, None]) / sv[:, None])
+    okp = (pc >= 0) & (pc < n_pad_row[row][:, None])
+    okt = (tc >= 0) & (tc < ro.n_time)
+    val = amp[:, None, None] * (fu * okp)[:, :, None] * (fv * okt)[:, None, :]
+    m = okp[:, :, None] & okt[:, None, :]
+    local = ((row[:, None, None] * 256 + np.clip(pc, 0, 255)[:, :, None]) * 512
+             + np.clip(tc, 0, 511)[:, None, :])
+    grid = np.bincount(local[m], weights=val[m], minlength=cells_per_inst)
+    cell = np.nonzero(grid)[0]
+    noise = ro.noise_sigma * rng.normal(seed, S_DIGIT_NOISE, (cell + i * cells_per_inst).astype(np.uint64))
+    adc = np.clip(np.floor(grid[cell] + noise + 0.5), 0, ro.adc_max).astype(np.int64)
+    keep = adc >= ro.threshold
+    cell, adc = cell[keep], adc[keep]
+    # isolated noise digits: round(f * signal digits) per row, dropped on occupied cells
+    cnt = np.bincount(cell // (256 * 512), minlength=N_ROWS)
+    n_noise = np.floor(ro.noise_digit_fraction * cnt + 0.5).astype(np.int64)
+    rws = np.nonzero(n_noise)[0]
+    if rws.shape[0]:
+        reps = n_noise[rws]
+        r_rep = np.repeat(rws, reps)
+        j = np.arange(r_rep.shape[0]) - np.repeat(np.cumsum(reps) - reps, reps)
+        c = ((np.uint64(i * N_ROWS) + r_rep.astype(np.uint64)) << np.uint64(20)) + j.astype(np.uint64)
+        up = rng.uniform(seed, S_NOISE_DIGIT, c * np.uint64(3))
+        ut = rng.uniform(seed, S_NOISE_DIGIT, c * np.uint64(3) + np.uint64(1))
+        ua = rng.uniform(seed, S_NOISE_DIGIT, c * np.uint64(3) + np.uint64(2))
+        ncell = (r_rep * 256 + np.floor(up * n_pad_row[r_rep]).astype(np.int64)) * 512 \
+            + np.floor(ut * ro.n_time).astype(np.int64)
+        nadc = ro.threshold + np.floor(ua * 4).astype(np.int64)
+        occupied = np.zeros(cells_per_inst, bool)
+        occupied[cell] = True
+        ncell, first = np.unique(ncell, return_index=True)
+        nadc = nadc[first]
+        fresh = ~occupied[ncell]
+        cell = np.concatenate([cell, ncell[fresh]])
+        adc = np.concatenate([adc, nadc[fresh]])
+    gkey = cell + i * cells_per_inst
+    # grouped by row, in a seeded random order inside each row
+    tie = rng.bits(seed, S_NOISE_DIGIT + 1, gkey.astype(np.uint64)) if shuffle else gkey.astype(np.uint64)
+    order = np.argsort((cell // (256 * 512)).astype(np.uint64) << np.uint64(48)
+                       | (tie & np.uint64((1 << 48) - 1)), kind="stable")
+    return gkey[order], adc[order]
+
+
+def digitize(ev, readout: Readout = None, seed: int = None, shuffle: bool = True, workers: int = 1) -> Digits:
     """Digits of a synthetic event's crossings (use an event generated with
     smear=False and noise_fraction=0: its clusters are the exact crossings).
     Truth: the crossing positions per instance/row, their continuous pad and
-    time coordinates and their amplitudes."""
+    time coordinates and their amplitudes.  ``workers`` > 1 digitises the
+    sector instances in a spawn process pool (same result)."""
     ro = readout or Readout()
     geom = default_geometry()
     seed = int(ev.meta.get("seed", 0)) if seed is None else int(seed)
@@ -115,71 +172,37 @@ def digitize(ev, readout: Readout = None, seed: int = None, shuffle: bool = True
     su = ro.sigma_pad(d) / pitch
     sv = ro.sigma_time(d) / ro.time_bin
     amp = ro.gain * ev.charge.astype(np.float64)
-    p0 = np.rint(u).astype(np.int64)
-    t0 = np.rint(v).astype(np.int64)
-    offs = np.arange(-WINDOW, WINDOW + 1)
-    pc = p0[:, None] + offs[None, :]                      # [hits, 5]
-    tc = t0[:, None] + offs[None, :]
-    fu = _phi((pc + 0.5 - u[:, None]) / su[:, None]) - _phi((pc - 0.5 - u[:, None]) / su[:, None])
-    fv = _phi((tc + 0.5 - v[:, None]) / sv[:, None]) - _phi((tc - 0.5 - v[:, None]) / sv[:, None])
-    okp = (pc >= 0) & (pc < npad[:, None])
-    okt = (tc >= 0) & (tc < ro.n_time)
-    val = amp[:, None, None] * (fu * okp)[:, :, None] * (fv * okt)[:, None, :]
-    # cell key: ((instance * 152 + row) * 256 + pad) * 512 + time
-    rk = (inst * N_ROWS + row)
-    key = ((rk[:, None, None] * 256 + np.clip(pc, 0, 255)[:, :, None]) * 512
-           + np.clip(tc, 0, 511)[:, None, :])
-    m = (okp[:, :, None] & okt[:, None, :]).ravel()
-    key = key.ravel()[m]
-    val = val.ravel()[m]
-    ukey, inv = np.unique(key, return_inverse=True)
-    sval = np.bincount(inv, weights=val, minlength=ukey.shape[0])
-    noise = ro.noise_sigma * rng.normal(seed, S_DIGIT_NOISE, ukey.astype(np.uint64))
-    adc = np.clip(np.floor(sval + noise + 0.5), 0, ro.adc_max).astype(np.int64)
-    keep = adc >= ro.threshold
-    skey, sadc = ukey[keep], adc[keep]
-
-    # isolated noise digits: round(f * signal digits) per (instance, row)
     n_rk = ev.n_instances * N_ROWS
-    cnt = np.bincount(skey // (256 * 512), minlength=n_rk)
-    n_noise = np.floor(ro.noise_digit_fraction * cnt + 0.5).astype(np.int64)
-    rks = np.nonzero(n_noise)[0]
-    if rks.shape[0]:
-        reps = n_noise[rks]
-        rk_rep = np.repeat(rks, reps)
-        j = np.arange(rk_rep.shape[0]) - np.repeat(np.cumsum(reps) - reps, reps)
-        c = (rk_rep.astype(np.uint64) << np.uint64(20)) + j.astype(np.uint64)
-        up = rng.uniform(seed, S_NOISE_DIGIT, c * np.uint64(3))
-        ut = rng.uniform(seed, S_NOISE_DIGIT, c * np.uint64(3) + np.uint64(1))
-        ua = rng.uniform(seed, S_NOISE_DIGIT, c * np.uint64(3) + np.uint64(2))
-        np_row = n_pad_row[rk_rep % N_ROWS]
-        nkey = (rk_rep * 256 + np.floor(up * np_row).astype(np.int64)) * 512 + np.floor(ut * ro.n_time).astype(np.int64)
-        nadc = ro.threshold + np.floor(ua * 4).astype(np.int64)
-        # a noise digit on an occupied cell (or a repeated one) is dropped
-        fresh = ~np.isin(nkey, skey)
-        nkey, nadc = nkey[fresh], nadc[fresh]
-        nkey, first = np.unique(nkey, return_index=True)
-        nadc = nadc[first]
-        skey = np.concatenate([skey, nkey])
-        sadc = np.concatenate([sadc, nadc])
+    order_h = np.argsort(inst, kind="stable")
+    bounds = np.searchsorted(inst[order_h], np.arange(ev.n_instances + 1))
+    jobs = []
+    for i in range(ev.n_instances):
+        h = order_h[bounds[i]:bounds[i + 1]]
+        jobs.append((i, seed, ro, n_pad_row, row[h], u[h], v[h], su[h], sv[h], amp[h], shuffle))
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_instance_digits, jobs, chunksize=1))
+    else:
+        parts = [_instance_digits(j) for j in jobs]
+    skey = np.concatenate([p[0] for p in parts]) if parts else np.zeros(0, np.int64)
+    sadc = np.concatenate([p[1] for p in parts]) if parts else np.zeros(0, np.int64)
     rk_all = skey // (256 * 512)
     pad = (skey // 512) % 256
     tim = skey % 512
-    tie = rng.bits(seed, S_NOISE_DIGIT + 1, skey.astype(np.uint64)) if shuffle else skey.astype(np.uint64)
-    order = np.lexsort((tie, rk_all))                    # grouped by (instance, row), shuffled inside
-    rk_all = rk_all[order]
     offsets = np.zeros(n_rk + 1, np.int64)
     offsets[1:] = np.cumsum(np.bincount(rk_all, minlength=n_rk))
     truth = dict(inst=inst, row=row, y=y, z=z, u=u, v=v, amp=amp, mc=ev.mc.copy())
-    return Digits(pad=pad[order].astype(np.uint16), time=tim[order].astype(np.uint16),
-                  adc=sadc[order].astype(np.uint16), row_offsets=offsets, sectors=ev.sectors.copy(),
+    return Digits(pad=pad.astype(np.uint16), time=tim.astype(np.uint16),
+                  adc=sadc.astype(np.uint16), row_offsets=offsets, sectors=ev.sectors.copy(),
                   readout=ro, n_pad=n_pad_row, truth=truth)
 
 
-def generate_digits(config_index: int = 1, instance: int = 0, **kw) -> Digits:
+def generate_digits(config_index: int = 1, instance: int = 0, workers: int = 1, **kw) -> Digits:
     """Digits of the exact crossings of a workload's event (the single
     sector or the central Pb-Pb-like event), without cluster noise."""
     from .events import generate_config
     ev = generate_config(config_index, instance=instance, smear=False, noise_fraction=0.0,
                          keep_exact=True, **kw)
-    return digitize(ev)
+    return digitize(ev, workers=workers)
