@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-merge", action="store_true")
     ap.add_argument("--no-clusters", action="store_true")
+    ap.add_argument("--only-clusters", action="store_true",
+                    help="time only the cluster-finding leg (central-event digits x4)")
     ap.add_argument("--tuning-cache", default=None, help="autotuner cache file (default: a fresh temp file)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variants", default="mixed_df", help="comma-separated extra precisions timed in the same run")
@@ -408,6 +410,16 @@ def main():
         run_reference(args)
         return
     rank, world, local = dist_env()
+    if args.only_clusters:
+        # the cluster-finding leg alone (profiling aid): one JSON object
+        import torch
+        import paper_2502_09138_gb300 as G
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        leg = cluster_leg(args, G, dev, torch.cuda.current_stream(dev), reps=max(1, args.steps))
+        if rank == 0:
+            print(json.dumps({"cluster_finding": leg}), flush=True)
+        return
     # generate before any CUDA call (the generator uses a spawn process pool)
     ev = workload(args, rank)
     import torch

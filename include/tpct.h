@@ -327,16 +327,19 @@ typedef struct {
   double pad_pitch_outer;      /* [cm] (0.6) */
   int32_t n_inner_rows;        /* rows with the inner pitch (63) */
   double time_bin;             /* drift length per time bin [cm] (0.5) */
-  int32_t n_time;              /* time bins per row (500); n_pad x n_time must fit in shared memory */
+  int32_t n_time;              /* time bins per row (500); at most 512, every row at most 256 pads, and
+                                  n_pad x n_time of the widest row must fit in one block's shared memory */
   int32_t q_peak_min;          /* (7) */
   int32_t valley_delta;        /* (2) */
 } tpct_cf_params;
 void tpct_default_cf_params(tpct_cf_params* p);
 
 /* Digits (device, caller-owned, read-only): SoA, grouped by (instance, row),
- * any order inside a row, each (pad, time) cell at most once per row. */
+ * any order inside a row, each (pad, time) cell at most once per row, ADC
+ * values below 32768, at most 8192 digits per row (more: TPCT_CF_ROW_OVERFLOW,
+ * the rest ignored). */
 typedef struct {
-  const uint16_t *pad, *time, *adc;
+  const uint16_t *pad, *time, *adc;   /* [row_offsets[last]]; may be NULL when there are no digits */
   const int64_t* row_offsets;  /* [n_instances * n_rows + 1] */
   const int32_t* inst_sector;  /* [n_instances] sector number 0..35 of each instance */
   int32_t n_instances;
@@ -355,9 +358,9 @@ typedef struct {
   uint8_t *row, *flags;        /* flags: 1 = peak on the first/last pad, 2 = on the first/last time bin */
   int64_t* inst_offsets;       /* [n_instances + 1] first cluster of each instance (may be NULL) */
 } tpct_cf_out;
-#define TPCT_CF_BAD_DIGIT 1u      /* a digit outside its row's pads or time bins (skipped) */
+#define TPCT_CF_BAD_DIGIT 1u      /* a digit outside its row's pads or time bins, or ADC >= 32768 (skipped) */
 #define TPCT_CF_TIMEOUT 2u        /* a bounded wait for a preceding row gave up (offsets invalid) */
-#define TPCT_CF_ROW_OVERFLOW 4u   /* a row had more than 8192 clusters (the rest not written) */
+#define TPCT_CF_ROW_OVERFLOW 4u   /* a row had more than 8192 digits or 8192 clusters (the rest dropped) */
 #define TPCT_CF_CAPACITY 8u       /* more clusters than capacity (the rest not written) */
 
 /* Device workspace of tpct_find_clusters for n_instances instances. */

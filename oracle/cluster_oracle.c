@@ -11,7 +11,7 @@
  *   CF0 readout: row r has n_pad(r) = 2 ceil(x_r tan_half / pitch(r) - 1e-9)
  *       pads (pitch: inner rows / outer rows) and n_time time bins; a digit
  *       is one (pad, time) cell of one row with its ADC value; cells are
- *       unique within a row, any order.
+ *       unique within a row, any order; ADC values below 32768.
  *   CF1 peak: a digit of charge q at (p, t) is a peak iff q >= q_peak_min and,
  *       for each of its 8 neighbours n, q > Q(n) when n comes before (p, t)
  *       in (time, pad) order and q >= Q(n) otherwise (Q = 0 off the row's
@@ -162,7 +162,7 @@ orc_cf_result* orc_find_clusters(const orc_cf_params* P, int64_t n_inst, const i
       const double pitch = row_pitch(P, r);
       /* the row's map */
       for (int64_t i = b; i < e; ++i) {
-        if (pad[i] >= np || time[i] >= nt) { *err = 3; goto fail; }
+        if (pad[i] >= np || time[i] >= nt || adc[i] >= 32768) { *err = 3; goto fail; }
         if (map[pad[i] * nt + time[i]] != 0) { *err = 2; goto fail; }
         map[pad[i] * nt + time[i]] = adc[i];
       }

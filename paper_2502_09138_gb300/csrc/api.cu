@@ -519,8 +519,7 @@ size_t tpct_cf_workspace_bytes(int32_t n_instances, int32_t n_rows) {
 tpct_status tpct_find_clusters(tpct_ctx* ctx, const tpct_digits* dg, const tpct_cf_params* prm, void* ws,
                                size_t ws_bytes, tpct_cf_out* out, tpct_stream stream) {
   if (!ctx || !dg || !prm || !ws || !out || dg->n_instances < 0 || ((uintptr_t)ws % kAlign)) return TPCT_E_INVALID;
-  if (dg->n_instances > 0 && (!dg->pad || !dg->time || !dg->adc || !dg->row_offsets || !dg->inst_sector))
-    return TPCT_E_INVALID;
+  if (dg->n_instances > 0 && (!dg->row_offsets || !dg->inst_sector)) return TPCT_E_INVALID;
   if (!out->n_clusters || !out->status || out->capacity < 0) return TPCT_E_INVALID;
   if (out->capacity > 0 && (!out->x || !out->y || !out->z || !out->pad || !out->time || !out->sigma_pad ||
                             !out->sigma_time || !out->q_tot || !out->q_max || !out->row || !out->flags))

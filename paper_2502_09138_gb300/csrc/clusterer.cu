@@ -30,6 +30,7 @@ namespace {
 
 constexpr int kCfThreads = 1024;
 constexpr int kCfMaxPeaks = 8192;          // kept peaks per row held in shared memory
+constexpr int kCfPerThread = 8;            // digits per thread: rows of up to 8192 digits
 constexpr int kCfMaxSpins = 1 << 22;       // look-back polls before giving up
 constexpr uint64_t kLbAgg = 1ull << 62, kLbInc = 2ull << 62, kLbMask = (1ull << 62) - 1;
 
@@ -89,15 +90,24 @@ __device__ __forceinline__ uint64_t ld_volatile(const uint64_t* a) {
   return *reinterpret_cast<const volatile unsigned long long*>(a);
 }
 
+// A digit in one register: pad (8 bits) | time (9 bits) | adc (15 bits).
+constexpr uint32_t kNoDigit = 0xffffffffu;
+__device__ __forceinline__ int w_pad(uint32_t w) { return (int)(w >> 24); }
+__device__ __forceinline__ int w_time(uint32_t w) { return (int)((w >> 15) & 511u); }
+__device__ __forceinline__ int w_adc(uint32_t w) { return (int)(w & 32767u); }
+
 __global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_constant__ CfDev P) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint16_t* map = reinterpret_cast<uint16_t*>(smem);
   uint32_t* bits = smem + P.map_words;
-  int32_t* peaks = reinterpret_cast<int32_t*>(bits + P.bit_words);
+  uint32_t* peaks = bits + P.bit_words;          // kept peaks of the row (packed digits), in input order
   __shared__ int s_row;
-  __shared__ int s_warp[kCfThreads / 32];
+  __shared__ uint32_t s_ball[kCfPerThread][kCfThreads / 32];
+  __shared__ int s_pref[kCfPerThread][kCfThreads / 32];
+  __shared__ int s_count;
   __shared__ long long s_base;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lanes_below = (1u << lane) - 1u;
   const int nt = P.n_time;
   const int n_rows_total = P.n_inst * P.n_rows;
   const tpct_cf_out& O = P.out;
@@ -113,90 +123,132 @@ __global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_consta
     const int r = row % P.n_rows, inst = row / P.n_rows;
     const int64_t b = P.row_offsets[row], e = P.row_offsets[row + 1];
     const int np = P.n_pad[r];
+    if (tid == 0 && e - b > (int64_t)kCfPerThread * kCfThreads) atomicOr(O.status, TPCT_CF_ROW_OVERFLOW);
 
-    // the row's charge map
-    for (int64_t i = b + tid; i < e; i += kCfThreads) {
-      const int p = P.pad[i], t = P.time[i];
-      if (p < np && t < nt) map[p * nt + t] = P.adc[i];
-      else atomicOr(O.status, TPCT_CF_BAD_DIGIT);
+    // the row's digits, k-major (digit b + k * 1024 + tid), loaded once
+    uint32_t w[kCfPerThread];
+#pragma unroll
+    for (int k = 0; k < kCfPerThread; ++k) {
+      const int64_t i = b + (int64_t)k * kCfThreads + tid;
+      w[k] = kNoDigit;
+      if (i < e) {
+        const uint32_t p = P.pad[i], t = P.time[i], q = P.adc[i];
+        if ((int)p < np && (int)t < nt && q < 32768u) w[k] = (p << 24) | (t << 15) | q;
+        else atomicOr(O.status, TPCT_CF_BAD_DIGIT);
+      }
     }
+#pragma unroll
+    for (int k = 0; k < kCfPerThread; ++k)
+      if (w[k] != kNoDigit) map[w_pad(w[k]) * nt + w_time(w[k])] = (uint16_t)w_adc(w[k]);
     __syncthreads();
     // peaks
-    for (int64_t i = b + tid; i < e; i += kCfThreads) {
-      const int p = P.pad[i], t = P.time[i];
-      if (p < np && t < nt && peak_test(map, np, nt, p, t, P.q_peak_min)) {
-        const int cell = p * nt + t;
+#pragma unroll
+    for (int k = 0; k < kCfPerThread; ++k)
+      if (w[k] != kNoDigit && peak_test(map, np, nt, w_pad(w[k]), w_time(w[k]), P.q_peak_min)) {
+        const int cell = w_pad(w[k]) * nt + w_time(w[k]);
         atomicOr(&bits[cell >> 5], 1u << (cell & 31));
       }
+    __syncthreads();
+    // kept peaks: one ballot per k, then one scan over (k, warp) gives every
+    // kept digit its rank in input order
+    uint32_t keep = 0u;
+#pragma unroll
+    for (int k = 0; k < kCfPerThread; ++k) {
+      bool kp = false;
+      if (w[k] != kNoDigit) {
+        const int p = w_pad(w[k]), t = w_time(w[k]);
+        kp = bit_at(bits, p * nt + t) && !suppressed(map, bits, np, nt, p, t, P.valley_delta);
+      }
+      const uint32_t ball = __ballot_sync(0xffffffffu, kp);
+      if (lane == 0) s_ball[k][warp] = ball;
+      keep |= (kp ? 1u : 0u) << k;
     }
     __syncthreads();
-    // kept peaks, compacted in input order
-    int count = 0;
-    for (int64_t base = b; base < e; base += kCfThreads) {
-      const int64_t i = base + tid;
-      bool keep = false;
-      if (i < e) {
-        const int p = P.pad[i], t = P.time[i];
-        keep = p < np && t < nt && bit_at(bits, p * nt + t) &&
-               !suppressed(map, bits, np, nt, p, t, P.valley_delta);
-      }
-      const uint32_t ball = __ballot_sync(0xffffffffu, keep);
-      if (lane == 0) s_warp[warp] = __popc(ball);
-      __syncthreads();
-      if (warp == 0) {
-        const int v = s_warp[lane];
-        int incl = v;
+    if (warp == 0) {
+      // lane j owns the (k, warp) entries [16 j, 16 j + 16) of the k-major list
+      constexpr int kPer = kCfPerThread * (kCfThreads / 32) / 32;
+      int loc[kPer], sum = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int u = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += u;
-        }
-        s_warp[lane] = incl - v;                 // exclusive prefix of the warps
-        if (lane == 31) s_base = incl;           // block total (read below, before the next write)
+      for (int u = 0; u < kPer; ++u) {
+        const int f = lane * kPer + u;
+        loc[u] = sum;
+        sum += __popc(s_ball[f / (kCfThreads / 32)][f % (kCfThreads / 32)]);
       }
-      __syncthreads();
-      if (keep) {
-        const int rank = count + s_warp[warp] + __popc(ball & ((1u << lane) - 1u));
-        if (rank < kCfMaxPeaks) peaks[rank] = (int)(i - b);
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
       }
-      count += (int)s_base;
-      __syncthreads();
+      const int excl = incl - sum;
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int f = lane * kPer + u;
+        s_pref[f / (kCfThreads / 32)][f % (kCfThreads / 32)] = excl + loc[u];
+      }
+      if (lane == 31) s_count = incl;
     }
+    __syncthreads();
+    const int count = s_count;
+#pragma unroll
+    for (int k = 0; k < kCfPerThread; ++k)
+      if ((keep >> k) & 1u) {
+        const int rank = s_pref[k][warp] + __popc(s_ball[k][warp] & lanes_below);
+        if (rank < kCfMaxPeaks) peaks[rank] = w[k];
+      }
     if (count > kCfMaxPeaks && tid == 0) atomicOr(O.status, TPCT_CF_ROW_OVERFLOW);
 
-    // decoupled look-back: publish the count, add the predecessors' counts
-    // until an inclusive prefix is found, publish the inclusive prefix
-    if (tid == 0) {
+    // decoupled look-back, one warp: publish the row's count, then read the
+    // states of the 32 preceding rows at once; the nearest one with an
+    // inclusive prefix ends the walk (all nearer ones must have published
+    // their counts), otherwise add all 32 counts and move 32 rows back;
+    // finally publish this row's inclusive prefix
+    if (warp == 0) {
       long long prefix = 0;
-      if (row == 0) {
+      if (lane == 0) {
         __threadfence();
-        atomicExch((unsigned long long*)&P.lookback[0], (unsigned long long)(kLbInc | (uint64_t)count));
-      } else {
-        __threadfence();
-        atomicExch((unsigned long long*)&P.lookback[row], (unsigned long long)(kLbAgg | (uint64_t)count));
-        int j = row - 1, spins = 0;
-        while (j >= 0) {
-          const uint64_t v = ld_volatile(&P.lookback[j]);
-          const uint64_t st = v >> 62;
-          if (st == 0) {
-            if (++spins > kCfMaxSpins) { atomicOr(O.status, TPCT_CF_TIMEOUT); break; }
+        atomicExch((unsigned long long*)&P.lookback[row],
+                   (unsigned long long)((row == 0 ? kLbInc : kLbAgg) | (uint64_t)count));
+      }
+      if (row > 0) {
+        int j0 = row - 1, spins = 0;
+        while (true) {
+          const int j = j0 - lane;
+          const uint64_t v = j >= 0 ? ld_volatile(&P.lookback[j]) : kLbInc;   // before row 0: prefix 0
+          const uint32_t st = (uint32_t)(v >> 62);
+          const uint32_t inc = __ballot_sync(0xffffffffu, st == 2u);
+          const uint32_t unset = __ballot_sync(0xffffffffu, st == 0u);
+          const int first = inc ? __ffs(inc) - 1 : 32;
+          const uint32_t upto = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
+          if (unset & upto) {
+            if (++spins > kCfMaxSpins) {
+              if (lane == 0) atomicOr(O.status, TPCT_CF_TIMEOUT);
+              break;
+            }
             __nanosleep(64);
             continue;
           }
-          prefix += (long long)(v & kLbMask);
-          if (st == 2) break;
-          --j;
+          long long val = lane <= first ? (long long)(v & kLbMask) : 0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
+          prefix += __shfl_sync(0xffffffffu, val, 0);
+          if (first < 32) break;
+          j0 -= 32;
         }
-        __threadfence();
-        atomicExch((unsigned long long*)&P.lookback[row],
-                   (unsigned long long)(kLbInc | (uint64_t)(prefix + count)));
+        if (lane == 0) {
+          __threadfence();
+          atomicExch((unsigned long long*)&P.lookback[row],
+                     (unsigned long long)(kLbInc | (uint64_t)(prefix + count)));
+        }
       }
-      s_base = prefix;
-      if (r == 0 && O.inst_offsets) O.inst_offsets[inst] = prefix;
-      if (row == n_rows_total - 1) {
-        *O.n_clusters = (int32_t)min(prefix + count, (long long)0x7fffffff);
-        if (O.inst_offsets) O.inst_offsets[P.n_inst] = prefix + count;
-        if (prefix + count > O.capacity) atomicOr(O.status, TPCT_CF_CAPACITY);
+      if (lane == 0) {
+        s_base = prefix;
+        if (r == 0 && O.inst_offsets) O.inst_offsets[inst] = prefix;
+        if (row == n_rows_total - 1) {
+          *O.n_clusters = (int32_t)min(prefix + count, (long long)0x7fffffff);
+          if (O.inst_offsets) O.inst_offsets[P.n_inst] = prefix + count;
+          if (prefix + count > O.capacity) atomicOr(O.status, TPCT_CF_CAPACITY);
+        }
       }
     }
     __syncthreads();
@@ -207,8 +259,8 @@ __global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_consta
     for (int k = tid; k < nk; k += kCfThreads) {
       const long long slot = base_out + k;
       if (slot >= O.capacity) break;
-      const int64_t i = b + peaks[k];
-      const int p = P.pad[i], t = P.time[i];
+      const uint32_t pw = peaks[k];
+      const int p = w_pad(pw), t = w_time(pw);
       int s0 = 0, sp = 0, st = 0, spp = 0, stt = 0;
 #pragma unroll
       for (int dt = -2; dt <= 2; ++dt)
@@ -234,20 +286,19 @@ __global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_consta
       O.y[slot] = (cp + 0.5f - 0.5f * (float)np) * pitch;
       O.z[slot] = side * (P.z_max - (ct + 0.5f) * P.time_bin);
       O.q_tot[slot] = (uint32_t)s0;
-      O.q_max[slot] = (uint16_t)map[p * nt + t];
+      O.q_max[slot] = (uint16_t)w_adc(pw);
       O.row[slot] = (uint8_t)r;
       O.flags[slot] = (uint8_t)((p == 0 || p == np - 1 ? 1 : 0) | (t == 0 || t == nt - 1 ? 2 : 0));
     }
     __syncthreads();
     // clear the row's cells and peak bits
-    for (int64_t i = b + tid; i < e; i += kCfThreads) {
-      const int p = P.pad[i], t = P.time[i];
-      if (p < np && t < nt) {
-        const int cell = p * nt + t;
+#pragma unroll
+    for (int k = 0; k < kCfPerThread; ++k)
+      if (w[k] != kNoDigit) {
+        const int cell = w_pad(w[k]) * nt + w_time(w[k]);
         map[cell] = 0;
         bits[cell >> 5] = 0u;
       }
-    }
     __syncthreads();
   }
 }
@@ -271,7 +322,7 @@ size_t cf_smem_bytes(int np_max, int n_time) {
 int enqueue_clusters(const double* row_x, int n_rows, double tan_half, double z_max, const tpct_cf_params& prm,
                      const tpct_digits& dg, void* ws, size_t ws_bytes, const tpct_cf_out& out, cudaStream_t s,
                      cudaError_t* err) {
-  if (n_rows < 1 || n_rows > kMaxRows || prm.n_time < 1 || prm.n_time > 65535 || !(prm.time_bin > 0) ||
+  if (n_rows < 1 || n_rows > kMaxRows || prm.n_time < 1 || prm.n_time > 512 || !(prm.time_bin > 0) ||
       !(prm.pad_pitch_inner > 0) || !(prm.pad_pitch_outer > 0))
     return -1;
   CfDev P{};
@@ -279,7 +330,7 @@ int enqueue_clusters(const double* row_x, int n_rows, double tan_half, double z_
   for (int r = 0; r < n_rows; ++r) {
     const double pitch = r < prm.n_inner_rows ? prm.pad_pitch_inner : prm.pad_pitch_outer;
     const int np = cf_pads(row_x[r], tan_half, pitch);
-    if (np < 1 || np > 32767) return -1;
+    if (np < 1 || np > 256) return -1;
     P.n_pad[r] = (int16_t)np;
     P.pitch[r] = (float)pitch;
     P.row_x[r] = (float)row_x[r];
