@@ -49,41 +49,44 @@ struct CfDev {
   tpct_cf_out out;
 };
 
-__device__ __forceinline__ int qat(const uint16_t* map, int np, int nt, int p, int t) {
-  return (p < 0 || p >= np || t < 0 || t >= nt) ? 0 : (int)map[p * nt + t];
-}
-__device__ __forceinline__ bool before(int p1, int t1, int p0, int t0) { return t1 < t0 || (t1 == t0 && p1 < p0); }
+// The row map has a border of two empty cells on every side: cell (p, t) of
+// the row lives at (p + 2) * W + (t + 2) with W = n_time + 4, so every
+// neighbourhood read up to distance 2 stays inside the map without a bounds
+// test (border and unused cells hold 0; the peak bitmap has the same layout).
+__device__ __forceinline__ bool before(int dp, int dt) { return dt < 0 || (dt == 0 && dp < 0); }
 __device__ __forceinline__ int half_step(int d) { return d == 2 ? 1 : (d == -2 ? -1 : 0); }
 __device__ __forceinline__ bool bit_at(const uint32_t* bits, int cell) { return (bits[cell >> 5] >> (cell & 31)) & 1u; }
 
-__device__ bool peak_test(const uint16_t* map, int np, int nt, int p, int t, int qmin) {
-  const int q = qat(map, np, nt, p, t);
+__device__ __forceinline__ bool peak_test(const uint16_t* map, int W, int c, int qmin) {
+  const int q = map[c];
   if (q < qmin) return false;
+  bool ok = true;
 #pragma unroll
   for (int dt = -1; dt <= 1; ++dt)
 #pragma unroll
     for (int dp = -1; dp <= 1; ++dp) {
       if (dp == 0 && dt == 0) continue;
-      const int qn = qat(map, np, nt, p + dp, t + dt);
-      if (dt < 0 || (dt == 0 && dp < 0) ? !(q > qn) : !(q >= qn)) return false;
+      const int qn = map[c + dp * W + dt];
+      ok &= before(dp, dt) ? q > qn : q >= qn;
     }
-  return true;
+  return ok;
 }
 
-__device__ bool suppressed(const uint16_t* map, const uint32_t* bits, int np, int nt, int p, int t, int delta) {
-  const int q = qat(map, np, nt, p, t);
+__device__ __forceinline__ bool suppressed(const uint16_t* map, const uint32_t* bits, int W, int c, int delta) {
+  const int q = map[c];
+  bool sup = false;
 #pragma unroll
   for (int dt = -2; dt <= 2; ++dt)
 #pragma unroll
     for (int dp = -2; dp <= 2; ++dp) {
       if (dp > -2 && dp < 2 && dt > -2 && dt < 2) continue;   // the Chebyshev-2 ring only
-      const int p2 = p + dp, t2 = t + dt;
-      if (p2 < 0 || p2 >= np || t2 < 0 || t2 >= nt || !bit_at(bits, p2 * nt + t2)) continue;
-      const int q2 = map[p2 * nt + t2];
-      if (!(q2 > q || (q2 == q && before(p2, t2, p, t)))) continue;
-      if (qat(map, np, nt, p + half_step(dp), t + half_step(dt)) >= q - delta) return true;
+      const int c2 = c + dp * W + dt;
+      if (!bit_at(bits, c2)) continue;
+      const int q2 = map[c2];
+      if (!(q2 > q || (q2 == q && before(dp, dt)))) continue;
+      sup |= (int)map[c + half_step(dp) * W + half_step(dt)] >= q - delta;
     }
-  return false;
+  return sup;
 }
 
 __device__ __forceinline__ uint64_t ld_volatile(const uint64_t* a) {
@@ -96,32 +99,93 @@ __device__ __forceinline__ int w_pad(uint32_t w) { return (int)(w >> 24); }
 __device__ __forceinline__ int w_time(uint32_t w) { return (int)((w >> 15) & 511u); }
 __device__ __forceinline__ int w_adc(uint32_t w) { return (int)(w & 32767u); }
 
+struct Cluster {
+  float cp, ct, sp, st;
+  uint32_t qtot;
+  uint32_t packed;   // the peak digit
+};
+
+__device__ __forceinline__ Cluster build_cluster(const uint16_t* map, int W, uint32_t pw) {
+  const int p = w_pad(pw), t = w_time(pw);
+  const int c = (p + 2) * W + (t + 2);
+  int s0 = 0, sp = 0, st = 0, spp = 0, stt = 0;
+#pragma unroll
+  for (int dt = -2; dt <= 2; ++dt)
+#pragma unroll
+    for (int dp = -2; dp <= 2; ++dp) {
+      const int qc = map[c + dp * W + dt];
+      const bool outer = dp == 2 || dp == -2 || dt == 2 || dt == -2;
+      const bool take = qc > 0 && (!outer || qc <= (int)map[c + half_step(dp) * W + half_step(dt)]);
+      const int q = take ? qc : 0;
+      s0 += q; sp += q * dp; st += q * dt; spp += q * dp * dp; stt += q * dt * dt;
+    }
+  const float fs0 = (float)s0;
+  const float mp = __fdiv_rn((float)sp, fs0), mt = __fdiv_rn((float)st, fs0);
+  Cluster k;
+  k.cp = (float)p + mp;
+  k.ct = (float)t + mt;
+  k.sp = sqrtf(fmaxf(__fdiv_rn((float)spp, fs0) - mp * mp, 0.f));
+  k.st = sqrtf(fmaxf(__fdiv_rn((float)stt, fs0) - mt * mt, 0.f));
+  k.qtot = (uint32_t)s0;
+  k.packed = pw;
+  return k;
+}
+
+__device__ __forceinline__ void store_cluster(const tpct_cf_out& O, long long slot, const Cluster& k, float row_x,
+                                              float pitch, int np, int nt, float side, float z_max, float time_bin,
+                                              int r) {
+  const int p = w_pad(k.packed), t = w_time(k.packed);
+  O.pad[slot] = k.cp;
+  O.time[slot] = k.ct;
+  O.sigma_pad[slot] = k.sp;
+  O.sigma_time[slot] = k.st;
+  O.x[slot] = row_x;
+  O.y[slot] = (k.cp + 0.5f - 0.5f * (float)np) * pitch;
+  O.z[slot] = side * (z_max - (k.ct + 0.5f) * time_bin);
+  O.q_tot[slot] = k.qtot;
+  O.q_max[slot] = (uint16_t)w_adc(k.packed);
+  O.row[slot] = (uint8_t)r;
+  O.flags[slot] = (uint8_t)((p == 0 || p == np - 1 ? 1 : 0) | (t == 0 || t == nt - 1 ? 2 : 0));
+}
+
 __global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_constant__ CfDev P) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint16_t* map = reinterpret_cast<uint16_t*>(smem);
   uint32_t* bits = smem + P.map_words;
   uint32_t* peaks = bits + P.bit_words;          // kept peaks of the row (packed digits), in input order
-  __shared__ int s_row;
+  __shared__ int s_next[2];                     // row of this / the next iteration (by parity)
+  __shared__ long long s_nb[2], s_ne[2];
   __shared__ uint32_t s_ball[kCfPerThread][kCfThreads / 32];
   __shared__ int s_pref[kCfPerThread][kCfThreads / 32];
   __shared__ int s_count;
   __shared__ long long s_base;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lanes_below = (1u << lane) - 1u;
-  const int nt = P.n_time;
+  const int nt = P.n_time, W = nt + 4;
   const int n_rows_total = P.n_inst * P.n_rows;
   const tpct_cf_out& O = P.out;
 
   for (uint32_t i = tid; i < P.map_words + P.bit_words; i += kCfThreads) smem[i] = 0u;
+  if (tid == 0) {
+    const int r0 = (int)atomicAdd(P.work, 1u);
+    s_next[0] = r0;
+    if (r0 < n_rows_total) { s_nb[0] = P.row_offsets[r0]; s_ne[0] = P.row_offsets[r0 + 1]; }
+  }
   __syncthreads();
 
-  while (true) {
-    if (tid == 0) s_row = (int)atomicAdd(P.work, 1u);
-    __syncthreads();
-    const int row = s_row;
+  for (int it = 0;; ++it) {
+    const int cur = it & 1, nxt = cur ^ 1;
+    const int row = s_next[cur];
     if (row >= n_rows_total) break;
+    const int64_t b = s_nb[cur], e = s_ne[cur];
+    // the next row's index and range, fetched while this row is processed
+    // (the other parity slot: every thread read it before the last barrier)
+    if (tid == 0) {
+      const int nx = (int)atomicAdd(P.work, 1u);
+      s_next[nxt] = nx;
+      if (nx < n_rows_total) { s_nb[nxt] = P.row_offsets[nx]; s_ne[nxt] = P.row_offsets[nx + 1]; }
+    }
     const int r = row % P.n_rows, inst = row / P.n_rows;
-    const int64_t b = P.row_offsets[row], e = P.row_offsets[row + 1];
     const int np = P.n_pad[r];
     if (tid == 0 && e - b > (int64_t)kCfPerThread * kCfThreads) atomicOr(O.status, TPCT_CF_ROW_OVERFLOW);
 
@@ -139,14 +203,14 @@ __global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_consta
     }
 #pragma unroll
     for (int k = 0; k < kCfPerThread; ++k)
-      if (w[k] != kNoDigit) map[w_pad(w[k]) * nt + w_time(w[k])] = (uint16_t)w_adc(w[k]);
+      if (w[k] != kNoDigit) map[(w_pad(w[k]) + 2) * W + w_time(w[k]) + 2] = (uint16_t)w_adc(w[k]);
     __syncthreads();
     // peaks
 #pragma unroll
     for (int k = 0; k < kCfPerThread; ++k)
-      if (w[k] != kNoDigit && peak_test(map, np, nt, w_pad(w[k]), w_time(w[k]), P.q_peak_min)) {
-        const int cell = w_pad(w[k]) * nt + w_time(w[k]);
-        atomicOr(&bits[cell >> 5], 1u << (cell & 31));
+      if (w[k] != kNoDigit) {
+        const int c = (w_pad(w[k]) + 2) * W + w_time(w[k]) + 2;
+        if (peak_test(map, W, c, P.q_peak_min)) atomicOr(&bits[c >> 5], 1u << (c & 31));
       }
     __syncthreads();
     // kept peaks: one ballot per k, then one scan over (k, warp) gives every
@@ -156,8 +220,8 @@ __global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_consta
     for (int k = 0; k < kCfPerThread; ++k) {
       bool kp = false;
       if (w[k] != kNoDigit) {
-        const int p = w_pad(w[k]), t = w_time(w[k]);
-        kp = bit_at(bits, p * nt + t) && !suppressed(map, bits, np, nt, p, t, P.valley_delta);
+        const int c = (w_pad(w[k]) + 2) * W + w_time(w[k]) + 2;
+        kp = bit_at(bits, c) && !suppressed(map, bits, W, c, P.valley_delta);
       }
       const uint32_t ball = __ballot_sync(0xffffffffu, kp);
       if (lane == 0) s_ball[k][warp] = ball;
@@ -165,7 +229,7 @@ __global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_consta
     }
     __syncthreads();
     if (warp == 0) {
-      // lane j owns the (k, warp) entries [16 j, 16 j + 16) of the k-major list
+      // lane j owns the (k, warp) entries [kPer j, kPer (j + 1)) of the k-major list
       constexpr int kPer = kCfPerThread * (kCfThreads / 32) / 32;
       int loc[kPer], sum = 0;
 #pragma unroll
@@ -197,13 +261,19 @@ __global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_consta
         if (rank < kCfMaxPeaks) peaks[rank] = w[k];
       }
     if (count > kCfMaxPeaks && tid == 0) atomicOr(O.status, TPCT_CF_ROW_OVERFLOW);
+    __syncthreads();
 
-    // decoupled look-back, one warp: publish the row's count, then read the
-    // states of the 32 preceding rows at once; the nearest one with an
-    // inclusive prefix ends the walk (all nearer ones must have published
-    // their counts), otherwise add all 32 counts and move 32 rows back;
-    // finally publish this row's inclusive prefix
-    if (warp == 0) {
+    // The last warp runs the decoupled look-back (publish the row's count,
+    // read the states of the 32 preceding rows at once; the nearest one with
+    // an inclusive prefix ends the walk, all nearer ones must have published
+    // their counts; else add all 32 counts and move 32 rows back; publish the
+    // inclusive prefix) while the other warps build their first clusters.
+    const int nk = min(count, kCfMaxPeaks);
+    constexpr int kBuilders = kCfThreads - 32;
+    Cluster mine;
+    const bool have = warp < kCfThreads / 32 - 1 && tid < nk;
+    if (have) mine = build_cluster(map, W, peaks[tid]);
+    if (warp == kCfThreads / 32 - 1) {
       long long prefix = 0;
       if (lane == 0) {
         __threadfence();
@@ -253,51 +323,23 @@ __global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_consta
     }
     __syncthreads();
     const long long base_out = s_base;
-    const int nk = min(count, kCfMaxPeaks);
-    const float pitch = P.pitch[r];
+    const float pitch = P.pitch[r], xr = P.row_x[r];
     const float side = P.inst_sector[inst] >= 18 ? -1.f : 1.f;
-    for (int k = tid; k < nk; k += kCfThreads) {
-      const long long slot = base_out + k;
-      if (slot >= O.capacity) break;
-      const uint32_t pw = peaks[k];
-      const int p = w_pad(pw), t = w_time(pw);
-      int s0 = 0, sp = 0, st = 0, spp = 0, stt = 0;
-#pragma unroll
-      for (int dt = -2; dt <= 2; ++dt)
-#pragma unroll
-        for (int dp = -2; dp <= 2; ++dp) {
-          const int qc = qat(map, np, nt, p + dp, t + dt);
-          if (qc <= 0) continue;
-          if ((dp == 2 || dp == -2 || dt == 2 || dt == -2) &&
-              !(qc <= qat(map, np, nt, p + half_step(dp), t + half_step(dt))))
-            continue;
-          s0 += qc; sp += qc * dp; st += qc * dt; spp += qc * dp * dp; stt += qc * dt * dt;
-        }
-      const float fs0 = (float)s0;
-      const float mp = __fdiv_rn((float)sp, fs0), mt = __fdiv_rn((float)st, fs0);
-      const float vp = fmaxf(__fdiv_rn((float)spp, fs0) - mp * mp, 0.f);
-      const float vt = fmaxf(__fdiv_rn((float)stt, fs0) - mt * mt, 0.f);
-      const float cp = (float)p + mp, ct = (float)t + mt;
-      O.pad[slot] = cp;
-      O.time[slot] = ct;
-      O.sigma_pad[slot] = sqrtf(vp);
-      O.sigma_time[slot] = sqrtf(vt);
-      O.x[slot] = P.row_x[r];
-      O.y[slot] = (cp + 0.5f - 0.5f * (float)np) * pitch;
-      O.z[slot] = side * (P.z_max - (ct + 0.5f) * P.time_bin);
-      O.q_tot[slot] = (uint32_t)s0;
-      O.q_max[slot] = (uint16_t)w_adc(pw);
-      O.row[slot] = (uint8_t)r;
-      O.flags[slot] = (uint8_t)((p == 0 || p == np - 1 ? 1 : 0) | (t == 0 || t == nt - 1 ? 2 : 0));
+    if (have && base_out + tid < O.capacity)
+      store_cluster(O, base_out + tid, mine, xr, pitch, np, nt, side, P.z_max, P.time_bin, r);
+    for (int k = kBuilders + tid; k < nk; k += kCfThreads) {   // rows with more clusters than builders
+      if (base_out + k >= O.capacity) break;
+      store_cluster(O, base_out + k, build_cluster(map, W, peaks[k]), xr, pitch, np, nt, side, P.z_max,
+                    P.time_bin, r);
     }
     __syncthreads();
     // clear the row's cells and peak bits
 #pragma unroll
     for (int k = 0; k < kCfPerThread; ++k)
       if (w[k] != kNoDigit) {
-        const int cell = w_pad(w[k]) * nt + w_time(w[k]);
-        map[cell] = 0;
-        bits[cell >> 5] = 0u;
+        const int c = (w_pad(w[k]) + 2) * W + w_time(w[k]) + 2;
+        map[c] = 0;
+        bits[c >> 5] = 0u;
       }
     __syncthreads();
   }
@@ -311,10 +353,11 @@ int cf_pads(double row_x, double tan_half, double pitch) {
   return 2 * (int)std::ceil(row_x * tan_half / pitch - 1e-9);
 }
 
+// map: (np_max + 4) x (n_time + 4) u16 with a two-cell empty border; bitmap: one bit per map cell
+size_t cf_map_cells(int np_max, int n_time) { return (size_t)(np_max + 4) * (n_time + 4); }
 size_t cf_smem_bytes(int np_max, int n_time) {
-  const size_t map_words = ((size_t)np_max * n_time + 1) / 2;
-  const size_t bit_words = ((size_t)np_max * n_time + 31) / 32;
-  return 4 * (map_words + bit_words) + 4 * (size_t)kCfMaxPeaks;
+  const size_t cells = cf_map_cells(np_max, n_time);
+  return 4 * ((cells + 1) / 2 + (cells + 31) / 32) + 4 * (size_t)kCfMaxPeaks;
 }
 
 // Enqueue cluster finding; returns the kernels launched, or -1 (invalid
@@ -349,8 +392,8 @@ int enqueue_clusters(const double* row_x, int n_rows, double tan_half, double z_
   P.n_inst = dg.n_instances; P.n_rows = n_rows; P.n_time = prm.n_time; P.np_max = np_max;
   P.q_peak_min = prm.q_peak_min; P.valley_delta = prm.valley_delta;
   P.z_max = (float)z_max; P.time_bin = (float)prm.time_bin;
-  P.map_words = (uint32_t)(((size_t)np_max * prm.n_time + 1) / 2);
-  P.bit_words = (uint32_t)(((size_t)np_max * prm.n_time + 31) / 32);
+  P.map_words = (uint32_t)((cf_map_cells(np_max, prm.n_time) + 1) / 2);
+  P.bit_words = (uint32_t)((cf_map_cells(np_max, prm.n_time) + 31) / 32);
   P.work = (uint32_t*)ws;
   P.lookback = (uint64_t*)((char*)ws + 256);
   P.out = out;
