@@ -337,6 +337,100 @@ def serving_leg(args, ev, G, capacity_cps):
     return out
 
 
+def publishing_leg(args, ev, G, capacity_cps, n_frames=48):
+    """An offline source publishing frames of 8-32 collisions cut from the
+    batch into the serving runtime (3 slots), followed by a serial host
+    consumer that fetches every frame's tracks and spends 1.25x the frame's
+    GPU time on it (the slower serial stage of Section 3), driven by the
+    native pacer with the naive policy (in-flight limit only) and with
+    publishing-rate smoothing.  Latency = publication -> consumed."""
+    import torch
+    ne, spe, offs = ev.n_events, ev.sectors_per_event, ev.sector_offsets
+    rng = np.random.default_rng(5000)
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(ev, k))).pin_memory()
+           for k in ("x", "y", "z", "charge", "row")}
+    frames = []
+    for _ in range(n_frames):
+        k = int(rng.integers(8, min(32, ne) + 1))
+        c0 = int(rng.integers(0, ne - k + 1))
+        a, b = int(offs[c0 * spe]), int(offs[(c0 + k) * spe])
+        so = torch.from_numpy((offs[c0 * spe:(c0 + k) * spe + 1] - a).astype(np.int64)).pin_memory()
+        frames.append(dict(x=pin["x"][a:b], y=pin["y"][a:b], z=pin["z"][a:b], charge=pin["charge"][a:b],
+                           row=pin["row"][a:b], sector_offsets=so))
+    sizes = np.array([f["y"].shape[0] for f in frames], np.float64)
+    cost = 1.25 * sizes / capacity_cps
+    cuts = G.default_cuts(sig_readout=ev.sigma.at_readout, sig_cathode=ev.sigma.at_cathode)
+    limit = 12
+    out = {"frames": n_frames, "mean_frame_clusters": float(sizes.mean()), "max_in_flight": limit,
+           "consumer_s_per_frame": float(cost.mean())}
+    for policy in ("naive", "smooth"):
+        srv = G.Server(n_slots=3, budget_bytes=int(args.serve_budget_gb * (1 << 30)), precision=args.precision,
+                       bz=ev.bz, cuts=cuts)
+        for f in frames[:2]:                      # warm-up
+            srv.wait(srv.submit(f))
+        for tk in list(srv._frames):
+            srv.release(tk)
+        pacer = G.Pacer(policy, max_in_flight=limit, initial_delay_s=float(cost.mean()) * 0.25)
+        lock = threading.Lock()
+        tks, t_pub, t_done = [], [], [0.0] * n_frames
+        state = {"consumed": 0}
+        done0 = srv.stats()["completed"]
+
+        def backlog():
+            st = srv.stats()
+            waiting = (st["completed"] - done0) - state["consumed"]
+            return st["queued"] + max(0, waiting - 2)
+
+        def consumer():
+            for i in range(n_frames):
+                while True:
+                    with lock:
+                        if len(tks) > i:
+                            tk = tks[i]
+                            break
+                    time.sleep(0.0005)
+                srv.wait(tk)
+                srv.fetch(tk)
+                time.sleep(cost[i])
+                srv.release(tk)
+                now = time.perf_counter()
+                with lock:
+                    t_done[i] = now
+                    state["consumed"] += 1
+                    pacer.on_consumed(now, len(tks) - state["consumed"], backlog())
+
+        th = threading.Thread(target=consumer)
+        t0 = time.perf_counter()
+        th.start()
+        samples = []
+        while len(tks) < n_frames:
+            now = time.perf_counter()
+            with lock:
+                inflight = len(tks) - state["consumed"]
+                ok, wait = pacer.try_publish(now, inflight, backlog())
+                if ok:
+                    tks.append(srv.submit(frames[len(tks)]))
+                    t_pub.append(now)
+            samples.append(inflight)
+            if not ok:
+                time.sleep(min(wait, 0.002) if wait > 0 else 0.001)
+        while th.is_alive():
+            with lock:
+                samples.append(len(tks) - state["consumed"])
+            time.sleep(0.001)
+        th.join()
+        t_end = max(t_done)
+        lat = (np.array(t_done) - np.array(t_pub)) * 1e3
+        st = srv.stats()
+        out[policy] = {"makespan_s": t_end - t0, "clusters_per_s": float(sizes.sum() / (t_end - t0)),
+                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                       "mean_in_flight": float(np.mean(samples)), "peak_gb": st["peak_bytes"] / 2 ** 30,
+                       "final_delay_s": pacer.delay, "pressure_events": pacer.pressure_events}
+        srv.close()
+        del srv
+    return out
+
+
 def _oracle_chunk(payload):
     import oracle
     import synth
@@ -631,6 +725,7 @@ def main():
 
     if not args.no_serving and args.workload == "batch":
         line["serving"] = serving_leg(args, ev, G, value / world)
+        line["publishing"] = publishing_leg(args, ev, G, value / world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, par, idx = cpu_baseline(ev, gout, gdbg)

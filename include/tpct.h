@@ -374,6 +374,46 @@ size_t tpct_cf_workspace_bytes(int32_t n_instances, int32_t n_rows);
 tpct_status tpct_find_clusters(tpct_ctx* ctx, const tpct_digits* digits, const tpct_cf_params* params,
                                void* workspace, size_t workspace_bytes, tpct_cf_out* out, tpct_stream stream);
 
+/* ---------------------------------------------------------------- publishing-rate control */
+/* Pacing of an offline source that feeds frames into a processing chain
+ * (host-side; no device code).  Section 3 of the paper: publishing as fast as
+ * possible and throttling only by the collisions in flight makes work arrive
+ * in waves that leave stages idle behind a slower serial one; ALICE smooths
+ * the publishing rate with a heuristic that slowly shortens the delay between
+ * publications until back pressure appears.  Reading implemented here:
+ *   NAIVE   publish whenever fewer than max_in_flight frames are in flight
+ *           (published and not yet consumed);
+ *   SMOOTH  also wait until `delay` has passed since the last publication
+ *           and no frames wait downstream (backlog == 0);
+ *           after every consumed frame delay *= (1 - decrease) if no back
+ *           pressure was seen since the previous one, else delay *=
+ *           (1 + increase); back pressure = a publication attempt met the
+ *           in-flight limit or frames waiting downstream (backlog > 0);
+ *           delay stays in [min_delay_s, max_delay_s].
+ * The caller passes its own clock (seconds); the pacer keeps no thread. */
+typedef enum { TPCT_PUBLISH_NAIVE = 0, TPCT_PUBLISH_SMOOTH = 1 } tpct_publish_policy;
+typedef struct {
+  tpct_publish_policy policy;  /* (SMOOTH) */
+  int32_t max_in_flight;       /* (8) */
+  double initial_delay_s;      /* (0.05) */
+  double decrease;             /* (0.02) */
+  double increase;             /* (0.05) */
+  double min_delay_s, max_delay_s;   /* (0, 10) */
+} tpct_pacer_config;
+typedef struct tpct_pacer tpct_pacer;
+void tpct_default_pacer_config(tpct_pacer_config* config);
+/* TPCT_E_INVALID for a bad configuration. */
+tpct_status tpct_pacer_create(const tpct_pacer_config* config, tpct_pacer** out);
+void tpct_pacer_destroy(tpct_pacer* pacer);
+/* 1: publish now (recorded as published); 0: not now, *wait_s = the time
+ * until the delay has passed (0 when waiting for a consumed frame). */
+int tpct_pacer_try_publish(tpct_pacer* pacer, double now_s, int32_t in_flight, int32_t backlog, double* wait_s);
+/* A frame left the chain; adapts the delay (SMOOTH). */
+void tpct_pacer_on_consumed(tpct_pacer* pacer, double now_s, int32_t in_flight, int32_t backlog);
+double tpct_pacer_delay(const tpct_pacer* pacer);
+/* Number of times back pressure started. */
+int64_t tpct_pacer_pressure_events(const tpct_pacer* pacer);
+
 /* ---------------------------------------------------------------- serving */
 /* A serving runtime: time frames (batches of sector instances) submitted from
  * host memory are tracked concurrently in up to n_slots streams.  A frame is

@@ -419,6 +419,43 @@ class Tracker:
         return int(B.load().tpct_kernel_launches(self._h))
 
 
+class Pacer:
+    """Publishing-rate control of an offline source (native, host-side):
+    policy "naive" (in-flight limit only) or "smooth" (adaptive delay)."""
+
+    def __init__(self, policy="smooth", **over):
+        lib = B.load()
+        c = B.PacerConfig()
+        lib.tpct_default_pacer_config(ctypes.byref(c))
+        c.policy = {"naive": B.TPCT_PUBLISH_NAIVE, "smooth": B.TPCT_PUBLISH_SMOOTH}[policy]
+        for k, v in over.items():
+            setattr(c, k, v)
+        h = ctypes.c_void_p()
+        B.check(lib.tpct_pacer_create(ctypes.byref(c), ctypes.byref(h)), "tpct_pacer_create")
+        self._h, self._lib = h, lib
+
+    def try_publish(self, now, in_flight, backlog):
+        w = ctypes.c_double(0.0)
+        ok = self._lib.tpct_pacer_try_publish(self._h, float(now), int(in_flight), int(backlog), ctypes.byref(w))
+        return bool(ok), w.value
+
+    def on_consumed(self, now, in_flight, backlog):
+        self._lib.tpct_pacer_on_consumed(self._h, float(now), int(in_flight), int(backlog))
+
+    @property
+    def delay(self):
+        return self._lib.tpct_pacer_delay(self._h)
+
+    @property
+    def pressure_events(self):
+        return int(self._lib.tpct_pacer_pressure_events(self._h))
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.tpct_pacer_destroy(self._h)
+            self._h = None
+
+
 def probe_fma(use_fp64, blocks, iters, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     ms = ctypes.c_float()

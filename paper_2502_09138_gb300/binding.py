@@ -81,6 +81,13 @@ class CfOut(ctypes.Structure):
 
 
 TPCT_CF_BAD_DIGIT, TPCT_CF_TIMEOUT, TPCT_CF_ROW_OVERFLOW, TPCT_CF_CAPACITY = 1, 2, 4, 8
+TPCT_PUBLISH_NAIVE, TPCT_PUBLISH_SMOOTH = 0, 1
+
+
+class PacerConfig(ctypes.Structure):
+    _fields_ = [("policy", c_int), ("max_in_flight", c_int32), ("initial_delay_s", c_double),
+                ("decrease", c_double), ("increase", c_double), ("min_delay_s", c_double),
+                ("max_delay_s", c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -141,6 +148,13 @@ EXPORTS = {
                            ctypes.POINTER(MergeCuts), c_void_p, c_size_t, ctypes.POINTER(ChainsOut), c_void_p]),
     "tpct_get_tuning": (c_int, [c_void_p, ctypes.POINTER(Tuning)]),
     "tpct_default_cf_params": (None, [ctypes.POINTER(CfParams)]),
+    "tpct_default_pacer_config": (None, [ctypes.POINTER(PacerConfig)]),
+    "tpct_pacer_create": (c_int, [ctypes.POINTER(PacerConfig), ctypes.POINTER(c_void_p)]),
+    "tpct_pacer_destroy": (None, [c_void_p]),
+    "tpct_pacer_try_publish": (c_int, [c_void_p, c_double, c_int32, c_int32, ctypes.POINTER(c_double)]),
+    "tpct_pacer_on_consumed": (None, [c_void_p, c_double, c_int32, c_int32]),
+    "tpct_pacer_delay": (c_double, [c_void_p]),
+    "tpct_pacer_pressure_events": (c_int64, [c_void_p]),
     "tpct_cf_workspace_bytes": (c_size_t, [c_int32, c_int32]),
     "tpct_find_clusters": (c_int, [c_void_p, ctypes.POINTER(Digits), ctypes.POINTER(CfParams), c_void_p, c_size_t,
                                    ctypes.POINTER(CfOut), c_void_p]),
