@@ -37,10 +37,10 @@ STAGES = ["grid", "neighbours", "clean_start", "tracklets", "selection", "refit"
 # FP64 flops of the mixed-precision tracklet filter: a helix step transports
 # the covariance (51 multiply-adds) and adds the float increments to the
 # double state (3 adds); a chi2 test forms the double residuals (2 adds, the
-# chi2 itself is float); an update forms S (2), det (2), the refined 1/det
-# (2 multiply-adds), S^-1 (3), the gain (10 + 10), the covariance (30
-# multiply-adds) and adds the state increments (5)
-FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 2 * 51 + 3, 2, 2 + 3 + 4 + 3 + 30 + 60 + 5
+# chi2 itself is float); an update forms S (2), det (3), 1/det (1), S^-1 (3),
+# the gain (10 + 10), the covariance (30 multiply-adds) and adds the state
+# increments (5)
+FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 2 * 51 + 3, 2, 2 + 3 + 1 + 3 + 30 + 60 + 5
 
 
 def parse():

@@ -268,10 +268,12 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
 
 // Mixed tracklet filter (double state and covariance, float transport): the
 // chi2 decision in float (1e-6 relative at most, inside the 1e-5 near-cut
-// band), 1/det from the float reciprocal refined by one Newton step in double
-// (relative error ~1e-14), the state increment K r in float (1e-7 of an
-// increment far smaller than the state); the gain and the covariance update,
-// whose subtraction cancels, in double.
+// band) and the state increment K r in float (1e-7 of an increment far
+// smaller than the state); 1/det, the gain and the covariance update, whose
+// subtraction cancels, in double.  (A float reciprocal of det refined by one
+// Newton step in double changed 4 of ~190 k tracklet lists of the
+// 128-collision batch: when S is large and its y-z correlation strong, the
+// float det loses digits and one step does not recover them.)
 __device__ __forceinline__ bool kf_test_update_mixed(double* p, double* m, double r0, double r1, float v,
                                                      float chi2_max) {
   const float f00 = narrow(m[0]) + v, f01 = narrow(m[1]), f11 = narrow(m[2]) + v;
@@ -281,9 +283,7 @@ __device__ __forceinline__ bool kf_test_update_mixed(double* p, double* m, doubl
   if (!(chi2 <= chi2_max)) return false;
   const double vd = widen(v);
   const double s00 = m[0] + vd, s01 = m[1], s11 = m[2] + vd;
-  const double det = s00 * s11 - s01 * s01;
-  double idet = widen(1.0f / fdet);
-  idet = fma(idet, fma(-det, idet, 1.0), idet);
+  const double idet = 1.0 / (s00 * s11 - s01 * s01);
   const double i00 = s11 * idet, i01 = -s01 * idet, i11 = s00 * idet;
   const double c0[5] = {m[0], m[1], m[3], m[6], m[10]};
   const double c1[5] = {m[1], m[2], m[4], m[7], m[11]};

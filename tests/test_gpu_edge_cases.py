@@ -34,7 +34,9 @@ def test_full_batch_sampled_parity():
     rng = np.random.default_rng(11)
     sizes = np.diff(ev.sector_offsets)
     cand = np.nonzero(sizes > 0)[0]
-    idx = np.sort(rng.choice(cand, 40, replace=False))
+    # ~300 of the 4608 sector instances (~3.5 M clusters): enough to meet the
+    # rare long tracklets whose decisions are sensitive to the filter's precision
+    idx = np.sort(rng.choice(cand, 300, replace=False))
     sub = ev.select_instances(idx)
     rep = compare(sub, oracle.track_event(sub), *slice_instances(ev, gtr, gdbg, idx)[::-1])
     assert rep["pass"], rep
