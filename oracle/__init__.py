@@ -15,6 +15,9 @@ Parity status of each oracle function (what pins it, in tests/test_oracle_*):
   whole tracker     generator truth (efficiency, fake rate, chi2/ndf, pulls);
                     the absolute efficiency level is parity unpinned (the paper
                     prints no tracking-efficiency number)
+  compression       hand-encoded fixture (tests/golden/tm_hand_fixture.json);
+                    exact round trip of the quantised clusters; parabola
+                    residuals of noiseless helices within one grid unit
   cluster finding   hand-computed fixture (tests/golden/cf_hand_fixture.json);
                     generator truth of isolated crossings (efficiency,
                     centroid residuals, charge); translation and input-order
@@ -29,6 +32,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tpct_oracle.c")
 _SRC_CF = os.path.join(_HERE, "cluster_oracle.c")
+_SRC_TM = os.path.join(_HERE, "compress_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libtpct_oracle.so")
 _lib = None
 
@@ -48,10 +52,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(_SRC_CF), os.path.getmtime(os.path.join(_HERE, "tpct_oracle.h"))):
+            os.path.getmtime(_SRC), os.path.getmtime(_SRC_CF), os.path.getmtime(_SRC_TM),
+            os.path.getmtime(os.path.join(_HERE, "tpct_oracle.h"))):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, _SRC_CF, "-lm"])
+                               "-fno-fast-math", "-o", tmp, _SRC, _SRC_CF, _SRC_TM, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -437,3 +442,93 @@ def find_clusters(digits, params: CfParams = None, geometry=None) -> ClusterResu
     finally:
         L.orc_cf_free(h)
     return ClusterResult(out)
+
+
+# ---------------------------------------------------------------- track-model compression
+class _TmGeom(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int), ("row_x", ctypes.POINTER(ctypes.c_double))]
+
+
+class TmStream:
+    """An encoded frame: bytes, per-track and per-(instance, row) block offsets."""
+
+    def __init__(self, data, track_off, row_off):
+        self.data, self.track_off, self.row_off = data, track_off, row_off
+
+    @property
+    def nbytes(self):
+        return int(self.data.shape[0])
+
+
+def _tm_lib():
+    L = lib()
+    if not getattr(L, "_tm_ready", False):
+        L.orc_tm_encode.restype = ctypes.c_void_p
+        L.orc_tm_encode.argtypes = [ctypes.POINTER(_TmGeom), ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        for f in ("orc_tm_bytes",):
+            getattr(L, f).restype = ctypes.c_int64
+            getattr(L, f).argtypes = [ctypes.c_void_p]
+        for f in ("orc_tm_data", "orc_tm_track_offsets", "orc_tm_row_offsets"):
+            getattr(L, f).restype = ctypes.c_void_p
+            getattr(L, f).argtypes = [ctypes.c_void_p]
+        L.orc_tm_free.argtypes = [ctypes.c_void_p]
+        L.orc_tm_decode.restype = ctypes.c_int64
+        L.orc_tm_decode.argtypes = [ctypes.POINTER(_TmGeom), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L._tm_ready = True
+    return L
+
+
+def _tm_geom(geometry):
+    from synth import default_geometry
+    g = geometry or default_geometry()
+    rx = np.ascontiguousarray(g.row_x, dtype=np.float64)
+    return _TmGeom(g.n_rows, rx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), rx, g.n_rows
+
+
+def tm_encode(ev, tr_offset, tr_ncl, tr_ids, geometry=None) -> TmStream:
+    """Track-model encoding of an Event's clusters given its tracks (cluster
+    positions, rows ascending): see compress_oracle.c for the format."""
+    L = _tm_lib()
+    g, rx, nr = _tm_geom(geometry)
+    y = np.ascontiguousarray(ev.y, dtype=np.float32)
+    z = np.ascontiguousarray(ev.z, dtype=np.float32)
+    q = np.ascontiguousarray(ev.charge, dtype=np.uint16) if ev.charge is not None else None
+    row = np.ascontiguousarray(ev.row, dtype=np.uint8)
+    io = np.ascontiguousarray(ev.sector_offsets, dtype=np.int64)
+    off = np.ascontiguousarray(tr_offset, dtype=np.int32)
+    ncl = np.ascontiguousarray(tr_ncl, dtype=np.int32)
+    ids = np.ascontiguousarray(tr_ids, dtype=np.int32)
+    nt = int(ncl.shape[0])
+    h = L.orc_tm_encode(ctypes.byref(g), int(ev.n), int(io.shape[0] - 1), _ptr(io), _ptr(y), _ptr(z), _ptr(q),
+                        _ptr(row), nt, _ptr(off), _ptr(ncl), _ptr(ids))
+    if not h:
+        raise MemoryError("oracle encoding failed")
+    try:
+        nb = int(L.orc_tm_bytes(h))
+        nblk = (io.shape[0] - 1) * nr
+        cp = lambda p, n, dt: np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(np.ctypeslib.as_ctypes_type(dt))),
+                                                    shape=(n,)).copy()
+        data = cp(L.orc_tm_data(h), nb, np.uint8) if nb else np.zeros(0, np.uint8)
+        return TmStream(data, cp(L.orc_tm_track_offsets(h), nt + 1, np.int64),
+                        cp(L.orc_tm_row_offsets(h), nblk + 1, np.int64))
+    finally:
+        L.orc_tm_free(h)
+
+
+def tm_decode(stream: TmStream, n_max, geometry=None):
+    """Decode a stream: dict of x, y, z (float32), charge (uint16), row (uint8)."""
+    L = _tm_lib()
+    g, rx, nr = _tm_geom(geometry)
+    out = {"x": np.zeros(n_max, np.float32), "y": np.zeros(n_max, np.float32), "z": np.zeros(n_max, np.float32),
+           "charge": np.zeros(n_max, np.uint16), "row": np.zeros(n_max, np.uint8)}
+    data = np.ascontiguousarray(stream.data) if stream.nbytes else np.zeros(1, np.uint8)
+    n = L.orc_tm_decode(ctypes.byref(g), _ptr(data), int(stream.track_off.shape[0] - 1), _ptr(stream.track_off),
+                        int(stream.row_off.shape[0] - 1), _ptr(stream.row_off), int(n_max), _ptr(out["x"]),
+                        _ptr(out["y"]), _ptr(out["z"]), _ptr(out["charge"]), _ptr(out["row"]))
+    if n < 0:
+        raise ValueError("decoded more clusters than n_max")
+    return {k: v[:n] for k, v in out.items()}
