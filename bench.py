@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-merge", action="store_true")
     ap.add_argument("--no-clusters", action="store_true")
+    ap.add_argument("--no-compression", action="store_true")
     ap.add_argument("--only-clusters", action="store_true",
                     help="time only the cluster-finding leg (central-event digits x4)")
     ap.add_argument("--tuning-cache", default=None, help="autotuner cache file (default: a fresh temp file)")
@@ -235,6 +236,48 @@ def merge_leg(args, ev, G, trk, dc, out, stream):
     n_chains = int(ch.counts[0].item())
     return {"ms": mms, "tracks_in": n_tracks, "chains": n_chains,
             "tracks_per_s": n_tracks / (mms * 1e-3), "device_status": trk.device_status()}
+
+
+def compression_leg(args, ev, G, trk, dc, out, stream, reps=5):
+    """Track-model compression of the batch's clusters with its tracks, and
+    the GPU decoding of the stream: size per cluster, mean CUDA-event times,
+    and the decoder's HBM roofline (algorithmic bytes: the stream read, 15 B
+    written per cluster)."""
+    import torch
+    st = trk.tm_encode(dc, out)
+    torch.cuda.synchronize()
+    nt = int(out.counts[0].item())
+    nb = int(st["n_bytes"].item())
+    cap = st["data"].numel()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        trk.tm_encode(dc, out, capacity_bytes=cap)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        trk.tm_encode(dc, out, capacity_bytes=cap)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    enc_ms = e0.elapsed_time(e1) / reps
+    d = trk.tm_decode(st["data"], st["track_offsets"], nt, st["row_offsets"], ev.n_instances, ev.n)
+    for _ in range(2):
+        trk.tm_decode(st["data"], st["track_offsets"], nt, st["row_offsets"], ev.n_instances, ev.n)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        trk.tm_decode(st["data"], st["track_offsets"], nt, st["row_offsets"], ev.n_instances, ev.n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dec_ms = e0.elapsed_time(e1) / reps
+    ok = int(d["n"].item()) == ev.n
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    dec_bytes = nb + 15.0 * ev.n
+    return {"clusters": ev.n, "tracks": nt, "bytes": nb, "bytes_per_cluster": nb / ev.n,
+            "raw_bytes_per_cluster": 15, "encode_ms": enc_ms, "decode_ms": dec_ms,
+            "encode_clusters_per_s": ev.n / (enc_ms * 1e-3), "decode_clusters_per_s": ev.n / (dec_ms * 1e-3),
+            "decoded_all": ok,
+            "decode_roofline": {"bound": "hbm", "kernel": "k_td_decode", "achieved": dec_bytes / (dec_ms * 1e-3) / 1e9,
+                                "peak": peak, "unit": "GB/s", "frac": dec_bytes / (dec_ms * 1e-3) / 1e9 / peak}}
 
 
 def cluster_leg(args, G, dev, stream, copies=4, reps=10):
@@ -687,6 +730,8 @@ def main():
         line["merge"] = merge_leg(args, ev, G, trk, dc, out, stream)
     if not args.no_clusters:
         line["cluster_finding"] = cluster_leg(args, G, dev, stream)
+    if not args.no_compression:
+        line["compression"] = compression_leg(args, ev, G, trk, dc, out, stream)
 
     variants = {}
     for vp in [v for v in args.variants.split(",") if v and v != args.precision]:

@@ -374,6 +374,48 @@ size_t tpct_cf_workspace_bytes(int32_t n_instances, int32_t n_rows);
 tpct_status tpct_find_clusters(tpct_ctx* ctx, const tpct_digits* digits, const tpct_cf_params* params,
                                void* workspace, size_t workspace_bytes, tpct_cf_out* out, tpct_stream stream);
 
+/* ---------------------------------------------------------------- track-model compression */
+/* Compression of a frame's clusters with the tracks as the model, and its
+ * decoding (the paper counts compression inside "TPC Processing (Tracking,
+ * Clustering, Compression)", Table 1, and reports a 1.2-3 % faster offline
+ * reconstruction from GPU track-model decoding, Section 2; the format is a
+ * reading): positions on a 50 um grid (Y = rint(200 y), Z = rint(200 z), row
+ * X = rint(200 x_r)); per track (clusters rows ascending): count, first row,
+ * Y0, Z0, charge, then per cluster the rows skipped, the residuals of Y and Z
+ * against the value predicted from the track's previous decoded clusters
+ * (previous value; the line through two; the parabola through three, exact
+ * integer arithmetic, quotient rounded half away from zero) and the charge;
+ * clusters in no track, per (instance, row) sorted by (Y, Z, charge): count,
+ * Y (first absolute, then differences), Z, charge; every value a LEB128
+ * varint (signed: zigzag); tracks first, then the rows.  Decoding returns
+ * x = row radius, y = Y/200, z = Z/200 (float), charge, row, in the order
+ * tracks (clusters row-ascending) then rows. */
+typedef struct {
+  int64_t capacity;            /* bytes of data */
+  uint8_t* data;
+  int64_t* n_bytes;            /* [1] the stream's size, always written (may exceed capacity: nothing written) */
+  int64_t* track_offsets;      /* [tracks->capacity_tracks + 1] byte offset of every track, then the end of the tracks */
+  int64_t* row_offsets;        /* [n_instances * n_rows + 1] byte offset of every (instance, row) block, then the end */
+} tpct_tm_stream;
+typedef struct {
+  int64_t capacity;            /* clusters */
+  int64_t* n;                  /* [1] clusters decoded, always written */
+  float *x, *y, *z;
+  uint16_t* charge;
+  uint8_t* row;
+} tpct_tm_decoded;
+size_t tpct_tm_encode_workspace_bytes(int64_t n_clusters, int32_t capacity_tracks, int32_t n_instances, int32_t n_rows);
+/* Encode the clusters (device; row[] required) with the tracks of
+ * tpct_track / tpct_track_batch on them (device; n_tracks read on the device).
+ * TPCT_E_NOMEM if the workspace is too small. */
+tpct_status tpct_tm_encode(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n, const tpct_tracks_out* tracks,
+                           void* workspace, size_t workspace_bytes, tpct_tm_stream* out, tpct_stream stream);
+size_t tpct_tm_decode_workspace_bytes(int32_t n_tracks, int32_t n_instances, int32_t n_rows);
+/* Decode a stream (device data and offsets; counts on the host). */
+tpct_status tpct_tm_decode(tpct_ctx* ctx, const uint8_t* data, const int64_t* track_offsets, int32_t n_tracks,
+                           const int64_t* row_offsets, int32_t n_instances, void* workspace, size_t workspace_bytes,
+                           tpct_tm_decoded* out, tpct_stream stream);
+
 /* ---------------------------------------------------------------- publishing-rate control */
 /* Pacing of an offline source that feeds frames into a processing chain
  * (host-side; no device code).  Section 3 of the paper: publishing as fast as

@@ -393,6 +393,54 @@ class Tracker:
                 "tpct_find_clusters", self._h)
         return out
 
+    def _scratch(self, name, nbytes):
+        buf = getattr(self, name, None)
+        if buf is None or buf.numel() < nbytes + 256:
+            buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            setattr(self, name, buf)
+        return (buf.data_ptr() + 255) // 256 * 256
+
+    def tm_encode(self, clusters: "DeviceClusters", tracks: "Tracks", capacity_bytes=None, stream=None):
+        """Track-model encoding of the clusters with the tracks found on them:
+        dict of device tensors data (uint8), n_bytes, track_offsets, row_offsets."""
+        lib = B.load()
+        ni = clusters.n_instances
+        nb = int(lib.tpct_tm_encode_workspace_bytes(clusters.n, tracks.capacity_tracks, ni, self.n_rows))
+        base = self._scratch("_tmws", nb)
+        cap = int(capacity_bytes if capacity_bytes is not None else 16 * clusters.n + 4 * ni * self.n_rows + 1024)
+        st = {"data": torch.empty(max(1, cap), dtype=torch.uint8, device=self.device),
+              "n_bytes": torch.zeros(1, dtype=torch.int64, device=self.device),
+              "track_offsets": torch.zeros(tracks.capacity_tracks + 1, dtype=torch.int64, device=self.device),
+              "row_offsets": torch.zeros(ni * self.n_rows + 1, dtype=torch.int64, device=self.device)}
+        ts = B.TmStream(cap, _ptr(st["data"]), _ptr(st["n_bytes"]), _ptr(st["track_offsets"]), _ptr(st["row_offsets"]))
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        cs, os_ = clusters.as_struct(), tracks.as_struct()
+        self._keep_tm = (clusters, tracks, st)
+        B.check(lib.tpct_tm_encode(self._h, ctypes.byref(cs), clusters.n, ctypes.byref(os_), ctypes.c_void_p(base), nb,
+                                   ctypes.byref(ts), ctypes.c_void_p(s.cuda_stream)), "tpct_tm_encode", self._h)
+        return st
+
+    def tm_decode(self, data, track_offsets, n_tracks, row_offsets, n_instances, capacity, stream=None):
+        """Decode a stream (device tensors): dict of x, y, z, charge, row tensors and n."""
+        lib = B.load()
+        nb = int(lib.tpct_tm_decode_workspace_bytes(int(n_tracks), int(n_instances), self.n_rows))
+        base = self._scratch("_tdws", nb)
+        c = max(1, int(capacity))
+        d = {"n": torch.zeros(1, dtype=torch.int64, device=self.device),
+             "x": torch.empty(c, dtype=torch.float32, device=self.device),
+             "y": torch.empty(c, dtype=torch.float32, device=self.device),
+             "z": torch.empty(c, dtype=torch.float32, device=self.device),
+             "charge": torch.empty(c, dtype=torch.int16, device=self.device),
+             "row": torch.empty(c, dtype=torch.uint8, device=self.device)}
+        ds = B.TmDecoded(int(capacity), _ptr(d["n"]), _ptr(d["x"]), _ptr(d["y"]), _ptr(d["z"]), _ptr(d["charge"]),
+                         _ptr(d["row"]))
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._keep_td = (data, track_offsets, row_offsets, d)
+        B.check(lib.tpct_tm_decode(self._h, _ptr(data), _ptr(track_offsets), int(n_tracks), _ptr(row_offsets),
+                                   int(n_instances), ctypes.c_void_p(base), nb, ctypes.byref(ds),
+                                   ctypes.c_void_p(s.cuda_stream)), "tpct_tm_decode", self._h)
+        return d
+
     def set_stage_events(self, events):
         """events: 7 torch.cuda.Event (created with enable_timing) or None to disable."""
         if events is None:

@@ -84,6 +84,16 @@ TPCT_CF_BAD_DIGIT, TPCT_CF_TIMEOUT, TPCT_CF_ROW_OVERFLOW, TPCT_CF_CAPACITY = 1, 
 TPCT_PUBLISH_NAIVE, TPCT_PUBLISH_SMOOTH = 0, 1
 
 
+class TmStream(ctypes.Structure):
+    _fields_ = [("capacity", c_int64), ("data", c_void_p), ("n_bytes", c_void_p), ("track_offsets", c_void_p),
+                ("row_offsets", c_void_p)]
+
+
+class TmDecoded(ctypes.Structure):
+    _fields_ = [("capacity", c_int64), ("n", c_void_p), ("x", c_void_p), ("y", c_void_p), ("z", c_void_p),
+                ("charge", c_void_p), ("row", c_void_p)]
+
+
 class PacerConfig(ctypes.Structure):
     _fields_ = [("policy", c_int), ("max_in_flight", c_int32), ("initial_delay_s", c_double),
                 ("decrease", c_double), ("increase", c_double), ("min_delay_s", c_double),
@@ -149,6 +159,12 @@ EXPORTS = {
     "tpct_get_tuning": (c_int, [c_void_p, ctypes.POINTER(Tuning)]),
     "tpct_default_cf_params": (None, [ctypes.POINTER(CfParams)]),
     "tpct_default_pacer_config": (None, [ctypes.POINTER(PacerConfig)]),
+    "tpct_tm_encode_workspace_bytes": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
+    "tpct_tm_encode": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut), c_void_p,
+                               c_size_t, ctypes.POINTER(TmStream), c_void_p]),
+    "tpct_tm_decode_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
+    "tpct_tm_decode": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_size_t,
+                               ctypes.POINTER(TmDecoded), c_void_p]),
     "tpct_pacer_create": (c_int, [ctypes.POINTER(PacerConfig), ctypes.POINTER(c_void_p)]),
     "tpct_pacer_destroy": (None, [c_void_p]),
     "tpct_pacer_try_publish": (c_int, [c_void_p, c_double, c_int32, c_int32, ctypes.POINTER(c_double)]),

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtpct.so")
-SOURCES = ["api.cu", "grid_links.cu", "tracklet.cu", "select_refit.cu", "serve.cu", "autotune.cu", "merge.cu", "clusterer.cu", "pacer.cu"]
+SOURCES = ["api.cu", "grid_links.cu", "tracklet.cu", "select_refit.cu", "serve.cu", "autotune.cu", "merge.cu", "clusterer.cu", "pacer.cu", "compress.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -535,6 +535,47 @@ tpct_status tpct_find_clusters(tpct_ctx* ctx, const tpct_digits* dg, const tpct_
   return TPCT_OK;
 }
 
+size_t tpct_tm_encode_workspace_bytes(int64_t n, int32_t capacity_tracks, int32_t n_instances, int32_t n_rows) {
+  if (n < 0 || capacity_tracks < 0 || n_instances < 0 || n_rows < 1) return 0;
+  return tm_encode_workspace_bytes(n, capacity_tracks, n_instances * n_rows);
+}
+
+tpct_status tpct_tm_encode(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const tpct_tracks_out* tr, void* ws,
+                           size_t ws_bytes, tpct_tm_stream* out, tpct_stream stream) {
+  if (!ctx || !cl || !tr || !ws || !out || n < 0 || n > INT32_MAX || ((uintptr_t)ws % kAlign)) return TPCT_E_INVALID;
+  if (cl->n_instances < 1 || !cl->sector_offsets || (n > 0 && (!cl->y || !cl->z || !cl->row))) return TPCT_E_INVALID;
+  if (tr->capacity_tracks < 0 || !tr->n_tracks || (tr->capacity_tracks > 0 && (!tr->offset || !tr->n_cl ||
+                                                                               !tr->cluster_ids)))
+    return TPCT_E_INVALID;
+  if (!out->n_bytes || out->capacity < 0 || (out->capacity > 0 && !out->data)) return TPCT_E_INVALID;
+  const int k = enqueue_tm_encode(ctx->row_x.data(), ctx->n_rows, *cl, n, *tr, ws, ws_bytes, *out,
+                                  (cudaStream_t)stream);
+  if (k < 0) return TPCT_E_NOMEM;
+  ctx->launches += k;
+  return fail_cuda(ctx, cudaGetLastError());
+}
+
+size_t tpct_tm_decode_workspace_bytes(int32_t n_tracks, int32_t n_instances, int32_t n_rows) {
+  if (n_tracks < 0 || n_instances < 0 || n_rows < 1) return 0;
+  return tm_decode_workspace_bytes(n_tracks, n_instances * n_rows);
+}
+
+tpct_status tpct_tm_decode(tpct_ctx* ctx, const uint8_t* data, const int64_t* track_off, int32_t n_tracks,
+                           const int64_t* row_off, int32_t n_instances, void* ws, size_t ws_bytes,
+                           tpct_tm_decoded* out, tpct_stream stream) {
+  if (!ctx || !ws || !out || n_tracks < 0 || n_instances < 0 || ((uintptr_t)ws % kAlign)) return TPCT_E_INVALID;
+  if ((n_tracks > 0 && !track_off) || (n_instances > 0 && !row_off) || ((n_tracks > 0 || n_instances > 0) && !data))
+    return TPCT_E_INVALID;
+  if (!out->n || out->capacity < 0 ||
+      (out->capacity > 0 && (!out->x || !out->y || !out->z || !out->charge || !out->row)))
+    return TPCT_E_INVALID;
+  const int k = enqueue_tm_decode(ctx->row_x.data(), ctx->n_rows, data, track_off, n_tracks, row_off,
+                                  n_instances * ctx->n_rows, ws, ws_bytes, *out, (cudaStream_t)stream);
+  if (k < 0) return TPCT_E_NOMEM;
+  ctx->launches += k;
+  return fail_cuda(ctx, cudaGetLastError());
+}
+
 tpct_status tpct_get_tuning(const tpct_ctx* ctx, tpct_tuning* t) {
   if (!ctx || !t) return TPCT_E_INVALID;
   t->clusters_per_bin = ctx->clusters_per_bin;

@@ -206,6 +206,13 @@ int enqueue_clusters(const double* row_x, int n_rows, double tan_half, double z_
                      const tpct_digits& dg, void* ws, size_t ws_bytes, const tpct_cf_out& out, cudaStream_t s,
                      cudaError_t* err);
 size_t cf_workspace_bytes(int32_t n_instances, int32_t n_rows);
+size_t tm_encode_workspace_bytes(int64_t n, int32_t cap_tracks, int32_t n_blocks);
+size_t tm_decode_workspace_bytes(int32_t n_tracks, int32_t n_blocks);
+int enqueue_tm_encode(const double* row_x, int n_rows, const tpct_clusters& cl, int64_t n, const tpct_tracks_out& tr,
+                      void* ws, size_t ws_bytes, const tpct_tm_stream& out, cudaStream_t s);
+int enqueue_tm_decode(const double* row_x, int n_rows, const uint8_t* data, const int64_t* track_off, int32_t n_tracks,
+                      const int64_t* row_off, int32_t n_blocks, void* ws, size_t ws_bytes, const tpct_tm_decoded& out,
+                      cudaStream_t s);
 void launch_own(const Params& P, cudaStream_t s);
 void launch_emit(const Params& P, cudaStream_t s);
 // stage 0: all refit passes; 1: all but the last (PS/PE/PC types); 2: the last
