@@ -110,6 +110,8 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   q.trk_st = (int32_t*)take(4 * (size_t)pl.tcap);
   q.trk_tl = (int32_t*)take(4 * pl.tcap);
   q.trk_pos = (int32_t*)take(4 * n);
+  q.trk_order = (int32_t*)take(4 * (size_t)pl.tcap);
+  q.len_cnt = (int32_t*)take(4 * (size_t)kLenClasses);
   q.scan_tmp = (uint64_t*)take(8 * scan_tmp);
   if (P) {
     P->status = q.status; P->work = q.work; P->rx = q.rx; P->rxf = q.rxf;
@@ -124,6 +126,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
     P->tl_hits = q.tl_hits; P->tl_par = q.tl_par; P->tl_sel = q.tl_sel; P->tl_sel_scan = q.tl_sel_scan;
     P->tl_cnt = q.tl_cnt; P->trk_tl = q.trk_tl;
     P->trk_est = q.trk_est; P->trk_x = q.trk_x; P->trk_st = q.trk_st; P->trk_pos = q.trk_pos; P->scan_tmp = q.scan_tmp;
+    P->trk_order = q.trk_order; P->len_cnt = q.len_cnt;
   }
   return off;
 }
@@ -260,6 +263,8 @@ int enqueue_track(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
   launch_scan_u64(P.tl_sel, P.tl_sel_scan, P.tcap, P.scan_tmp, s); k += scan_k;
   launch_emit(P, s); ++k;
   mark(5);
+  cudaMemsetAsync(P.len_cnt, 0, sizeof(int32_t) * kLenClasses, s);
+  launch_refit_order(P, s); k += 3;
   if ((mode == 1 || mode == 3) && P.n_refit >= 2) {
     // leading passes in double-float, the last pass in double
     launch_refit(P, mode, 1, ctx->refit_block, ctx->rf_blocks, s); ++k;

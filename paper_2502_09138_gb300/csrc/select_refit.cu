@@ -141,10 +141,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
       if (lane == leader) base = (int)atomicAdd(P.work + 1 + (STAGE == 2 ? 1 : 0), (uint32_t)__popc(want));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
-        const int mine = base + __popc(want & lanes_below);
-        if (mine >= n_trk) {
+        const int slot = base + __popc(want & lanes_below);
+        if (slot >= n_trk) {
           exhausted = true;
         } else {
+          const int mine = P.trk_order[slot];
           const int nn = O.n_cl[mine], off = O.offset[mine];
           if (nn >= 1 && off >= 0 && off + nn <= O.capacity_ids) {   // ids of overflowing tracks were not written
             k = mine;
@@ -231,6 +232,43 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
   }
 }
 
+// Refit work order: output tracks by cluster count, longest first (a
+// counting sort over kLenClasses classes).  Every track's refit is
+// independent, so the order changes no result; longest-first keeps the
+// lanes of the persistent refit busy until the queue's end (the last tracks
+// taken are the short ones).
+__device__ __forceinline__ int refit_track_count(const Params& P) {
+  return min((int)(P.tl_sel_scan[P.tcap] >> 32), P.out.capacity_tracks);
+}
+
+__global__ void k_order_count(const __grid_constant__ Params P) {
+  const int n = refit_track_count(P);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    atomicAdd(&P.len_cnt[min(max(P.out.n_cl[k], 0), kLenClasses - 1)], 1);
+}
+
+// one block of kLenClasses threads: cursor[L] = tracks in longer classes
+__global__ void __launch_bounds__(kLenClasses) k_order_scan(const __grid_constant__ Params P) {
+  __shared__ int sh[kLenClasses];
+  const int L = threadIdx.x;
+  const int cnt = P.len_cnt[L];
+  sh[L] = cnt;
+  __syncthreads();
+  for (int off = 1; off < kLenClasses; off <<= 1) {
+    const int v = L + off < kLenClasses ? sh[L + off] : 0;
+    __syncthreads();
+    sh[L] += v;
+    __syncthreads();
+  }
+  P.len_cnt[L] = sh[L] - cnt;
+}
+
+__global__ void k_order_fill(const __grid_constant__ Params P) {
+  const int n = refit_track_count(P);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    P.trk_order[atomicAdd(&P.len_cnt[min(max(P.out.n_cl[k], 0), kLenClasses - 1)], 1)] = k;
+}
+
 __global__ void k_export_tracklets(const __grid_constant__ Params P, tpct_debug_out D) {
   const int n_tl = tracklet_count(P);
   const int R = P.n_rows;
@@ -287,6 +325,11 @@ void launch_own(const Params& P, cudaStream_t s) {
 }
 void launch_emit(const Params& P, cudaStream_t s) {
   k_emit<<<blocks_for(P.tcap, kBlock), kBlock, 0, s>>>(P);
+}
+void launch_refit_order(const Params& P, cudaStream_t s) {
+  k_order_count<<<blocks_for(P.tcap, kBlock), kBlock, 0, s>>>(P);
+  k_order_scan<<<1, kLenClasses, 0, s>>>(P);
+  k_order_fill<<<blocks_for(P.tcap, kBlock), kBlock, 0, s>>>(P);
 }
 void launch_refit(const Params& P, int mode, int stage, int block, int blocks, cudaStream_t s) {
   if (block <= 0 || block > kMaxBlock) block = 128;

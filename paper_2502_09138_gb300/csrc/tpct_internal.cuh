@@ -20,6 +20,7 @@ constexpr int kRankBits = 20;                  // selection weight = nhits << 20
 constexpr uint32_t kRankMask = (1u << kRankBits) - 1u;
 constexpr int kStageEvents = 7;               // step boundaries timed by tpct_set_stage_events
 constexpr int kMaxBlock = 256;                 // largest tracklet / refit block
+constexpr int kLenClasses = 256;               // track-length classes of the refit order
 constexpr double kKbPerTesla = 0.299792458e-2; // curvature [1/cm] per (q/pT [c/GeV]) per tesla
 
 enum StopReason { kStopEnd = 0, kStopProp = 1, kStopEdge = 2, kStopMiss = 3, kStopSinphi = 4 };
@@ -91,6 +92,8 @@ struct Params {
   int32_t* trk_st;             // [tcap] transport failure in the leading passes
   int32_t* trk_tl;             // [cap_tracks] tracklet of each output track
   int32_t* trk_pos;            // [cap_ids]    sorted position of each output cluster
+  int32_t* trk_order;          // [tcap] output tracks, longest first (the refit's work order)
+  int32_t* len_cnt;            // [kLenClasses] tracks per length class, then cursors
   uint64_t* scan_tmp;          // block sums of the scans
   // output (device, caller-owned)
   tpct_tracks_out out;
@@ -202,6 +205,7 @@ void launch_tracklets(const Params& P, int mode, int block, int blocks, cudaStre
 int tracklet_blocks_per_sm(int mode, int block);
 int refit_blocks_per_sm(int mode, int block);
 void launch_weights(const Params& P, cudaStream_t s);
+void launch_refit_order(const Params& P, cudaStream_t s);
 int enqueue_clusters(const double* row_x, int n_rows, double tan_half, double z_max, const tpct_cf_params& prm,
                      const tpct_digits& dg, void* ws, size_t ws_bytes, const tpct_cf_out& out, cudaStream_t s,
                      cudaError_t* err);
