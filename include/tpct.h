@@ -327,8 +327,7 @@ typedef struct {
   double pad_pitch_outer;      /* [cm] (0.6) */
   int32_t n_inner_rows;        /* rows with the inner pitch (63) */
   double time_bin;             /* drift length per time bin [cm] (0.5) */
-  int32_t n_time;              /* time bins per row (500); at most 512, every row at most 256 pads, and
-                                  n_pad x n_time of the widest row must fit in one block's shared memory */
+  int32_t n_time;              /* time bins per row (500); at most 512, every row at most 252 pads */
   int32_t q_peak_min;          /* (7) */
   int32_t valley_delta;        /* (2) */
 } tpct_cf_params;
@@ -336,8 +335,10 @@ void tpct_default_cf_params(tpct_cf_params* p);
 
 /* Digits (device, caller-owned, read-only): SoA, grouped by (instance, row),
  * any order inside a row, each (pad, time) cell at most once per row, ADC
- * values below 32768, at most 8192 digits per row (more: TPCT_CF_ROW_OVERFLOW,
- * the rest ignored). */
+ * values below 32768.  The kernel works on tiles of 128 time bins of a row:
+ * at most 4096 digits of a row within 132 consecutive time bins (a tile and
+ * two bins on each side) and at most 2048 clusters with their peak in one
+ * tile (more: TPCT_CF_ROW_OVERFLOW, the rest ignored). */
 typedef struct {
   const uint16_t *pad, *time, *adc;   /* [row_offsets[last]]; may be NULL when there are no digits */
   const int64_t* row_offsets;  /* [n_instances * n_rows + 1] */
@@ -346,7 +347,7 @@ typedef struct {
 } tpct_digits;
 
 /* Clusters (device, caller-owned): SoA in (instance, row) order, inside a
- * row in the input order of the peak digits; x, y, z are the tracker's
+ * row in (time, pad) order of the peaks; x, y, z are the tracker's
  * cluster input (tpct_clusters) for these instances. */
 typedef struct {
   int32_t capacity;
@@ -359,12 +360,17 @@ typedef struct {
   int64_t* inst_offsets;       /* [n_instances + 1] first cluster of each instance (may be NULL) */
 } tpct_cf_out;
 #define TPCT_CF_BAD_DIGIT 1u      /* a digit outside its row's pads or time bins, or ADC >= 32768 (skipped) */
-#define TPCT_CF_TIMEOUT 2u        /* a bounded wait for a preceding row gave up (offsets invalid) */
-#define TPCT_CF_ROW_OVERFLOW 4u   /* a row had more than 8192 digits or 8192 clusters (the rest dropped) */
-#define TPCT_CF_CAPACITY 8u       /* more clusters than capacity (the rest not written) */
+#define TPCT_CF_TIMEOUT 2u        /* (not raised: the kernels do not wait for one another) */
+#define TPCT_CF_ROW_OVERFLOW 4u   /* a tile of a row held more digits or clusters than the limits above */
+#define TPCT_CF_WORKSPACE 16u     /* the workspace was sized for fewer digits than the rows hold (rows skipped) */
+#define TPCT_CF_CAPACITY 8u       /* more clusters than capacity: *n_clusters is the size needed, the
+                                     output arrays hold no defined result */
 
-/* Device workspace of tpct_find_clusters for n_instances instances. */
-size_t tpct_cf_workspace_bytes(int32_t n_instances, int32_t n_rows);
+/* Device workspace of tpct_find_clusters for n_digits digits (the sum over
+ * all rows) of n_instances instances and an output of `capacity` clusters
+ * (the digits are sorted by time bin and the clusters staged there before
+ * they are put in order). */
+size_t tpct_cf_workspace_bytes(int64_t n_digits, int32_t n_instances, int32_t n_rows, int32_t capacity);
 
 /* Find the clusters of all rows of all instances; asynchronous on `stream`.
  * TPCT_E_INVALID for bad arguments or readout parameters whose largest row

@@ -29,8 +29,8 @@
  *       on the first or last time bin.  Position: y = (pad + 0.5 - n_pad / 2)
  *       * pitch, drift length (time + 0.5) * time_bin, z = +-(z_max - drift)
  *       on side A / C (sector < 18 / >= 18), x = row radius.
- *   Order: clusters of a row in the input order of their peak digits; rows
- *       in (instance, row) order.
+ *   Order: clusters of a row in (time, pad) order of their peaks; rows in
+ *       (instance, row) order.
  *
  * Everything is integer except the final means, variances and positions,
  * which are FP64.
@@ -106,6 +106,14 @@ static int before(int p1, int t1, int p0, int t0) { return t1 < t0 || (t1 == t0 
 /* one step from 0 towards an offset d in {-2..2}: +-1 where |d| == 2, else 0 */
 static int half_step(int d) { return d == 2 ? 1 : (d == -2 ? -1 : 0); }
 
+/* (time, pad) order of two digits (qsort over digit indices) */
+static const uint16_t *g_pad, *g_time;
+static int cmp_time_pad(const void* a, const void* b) {
+  const int64_t i = *(const int64_t*)a, j = *(const int64_t*)b;
+  if (g_time[i] != g_time[j]) return g_time[i] < g_time[j] ? -1 : 1;
+  return (g_pad[i] > g_pad[j]) - (g_pad[i] < g_pad[j]);
+}
+
 /* CF1 */
 static int is_peak(const int* map, int np, int nt, int p, int t, int qmin) {
   int q = Q(map, np, nt, p, t);
@@ -153,7 +161,11 @@ orc_cf_result* orc_find_clusters(const orc_cf_params* P, int64_t n_inst, const i
   const int nt = P->n_time;
   int* map = (int*)calloc((size_t)np_max * nt, sizeof(int));
   unsigned char* pk = (unsigned char*)calloc((size_t)np_max * nt, 1);
-  if (!map || !pk) { free(map); free(pk); orc_cf_free(res); *err = 4; return NULL; }
+  int64_t max_row = 1;
+  for (int64_t k = 0; k < n_inst * P->n_rows; ++k)
+    if (row_offsets[k + 1] - row_offsets[k] > max_row) max_row = row_offsets[k + 1] - row_offsets[k];
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)max_row);
+  if (!map || !pk || !order) { free(map); free(pk); free(order); orc_cf_free(res); *err = 4; return NULL; }
   for (int64_t inst = 0; inst < n_inst; ++inst) {
     const int side_c = inst_sector[inst] >= 18;
     for (int r = 0; r < P->n_rows; ++r) {
@@ -168,9 +180,17 @@ orc_cf_result* orc_find_clusters(const orc_cf_params* P, int64_t n_inst, const i
       }
       for (int64_t i = b; i < e; ++i)
         pk[pad[i] * nt + time[i]] = (unsigned char)is_peak(map, np, nt, pad[i], time[i], P->q_peak_min);
+      /* kept peaks of the row, in (time, pad) order */
+      int64_t nk = 0;
       for (int64_t i = b; i < e; ++i) {
         const int p = pad[i], t = time[i];
-        if (!pk[p * nt + t] || suppressed(map, pk, np, nt, p, t, P->valley_delta)) continue;
+        if (pk[p * nt + t] && !suppressed(map, pk, np, nt, p, t, P->valley_delta)) order[nk++] = i;
+      }
+      g_pad = pad; g_time = time;
+      qsort(order, (size_t)nk, sizeof(int64_t), cmp_time_pad);
+      for (int64_t kq = 0; kq < nk; ++kq) {
+        const int64_t i = order[kq];
+        const int p = pad[i], t = time[i];
         /* CF3 */
         int64_t s0 = 0, sp = 0, st = 0, spp = 0, stt = 0;
         for (int dt = -2; dt <= 2; ++dt)
@@ -216,10 +236,12 @@ orc_cf_result* orc_find_clusters(const orc_cf_params* P, int64_t n_inst, const i
   }
   free(map);
   free(pk);
+  free(order);
   return res;
 fail:
   free(map);
   free(pk);
+  free(order);
   orc_cf_free(res);
   return NULL;
 }

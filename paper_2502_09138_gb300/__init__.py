@@ -378,13 +378,13 @@ class Tracker:
         """Cluster finding on device digits (rows of this tracker's geometry)."""
         params = params or default_cf_params()
         lib = B.load()
-        nb = int(lib.tpct_cf_workspace_bytes(digits.n_instances, self.n_rows))
-        if getattr(self, "_cfws", None) is None or self._cfws.numel() < nb + 256:
-            self._cfws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
-        base = (self._cfws.data_ptr() + 255) // 256 * 256
         if out is None:
             out = ClusterOut(capacity if capacity is not None else digits.n // 4 + 1024, digits.n_instances,
                              self.device)
+        nb = int(lib.tpct_cf_workspace_bytes(digits.n, digits.n_instances, self.n_rows, out.capacity))
+        if getattr(self, "_cfws", None) is None or self._cfws.numel() < nb + 256:
+            self._cfws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        base = (self._cfws.data_ptr() + 255) // 256 * 256
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._keep_cf = (digits, out)
         ds, os_ = digits.as_struct(), out.as_struct()

@@ -80,7 +80,7 @@ class CfOut(ctypes.Structure):
                 ("flags", c_void_p), ("inst_offsets", c_void_p)]
 
 
-TPCT_CF_BAD_DIGIT, TPCT_CF_TIMEOUT, TPCT_CF_ROW_OVERFLOW, TPCT_CF_CAPACITY = 1, 2, 4, 8
+TPCT_CF_BAD_DIGIT, TPCT_CF_TIMEOUT, TPCT_CF_ROW_OVERFLOW, TPCT_CF_CAPACITY, TPCT_CF_WORKSPACE = 1, 2, 4, 8, 16
 TPCT_PUBLISH_NAIVE, TPCT_PUBLISH_SMOOTH = 0, 1
 
 
@@ -171,7 +171,7 @@ EXPORTS = {
     "tpct_pacer_on_consumed": (None, [c_void_p, c_double, c_int32, c_int32]),
     "tpct_pacer_delay": (c_double, [c_void_p]),
     "tpct_pacer_pressure_events": (c_int64, [c_void_p]),
-    "tpct_cf_workspace_bytes": (c_size_t, [c_int32, c_int32]),
+    "tpct_cf_workspace_bytes": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
     "tpct_find_clusters": (c_int, [c_void_p, ctypes.POINTER(Digits), ctypes.POINTER(CfParams), c_void_p, c_size_t,
                                    ctypes.POINTER(CfOut), c_void_p]),
     "tpct_autotune": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut), c_void_p,

@@ -516,9 +516,9 @@ void tpct_default_cf_params(tpct_cf_params* p) {
   p->time_bin = 0.5; p->n_time = 500; p->q_peak_min = 7; p->valley_delta = 2;
 }
 
-size_t tpct_cf_workspace_bytes(int32_t n_instances, int32_t n_rows) {
-  if (n_instances < 0 || n_rows < 1) return 0;
-  return cf_workspace_bytes(n_instances, n_rows);
+size_t tpct_cf_workspace_bytes(int64_t n_digits, int32_t n_instances, int32_t n_rows, int32_t capacity) {
+  if (n_digits < 0 || n_instances < 0 || n_rows < 1 || capacity < 0) return 0;
+  return cf_workspace_bytes(n_digits, n_instances, n_rows, capacity);
 }
 
 tpct_status tpct_find_clusters(tpct_ctx* ctx, const tpct_digits* dg, const tpct_cf_params* prm, void* ws,

@@ -10,49 +10,72 @@
 //             q - valley_delta;
 //   cluster   the 3x3 cells around a kept peak plus each outer-ring cell whose
 //             inner neighbour towards the peak holds at least its charge.
-// Clusters of a row come in the input order of their peak digits; rows in
-// (instance, row) order.
+// Clusters come in (instance, row) order, inside a row in (time, pad) order
+// of their peaks.
 //
-// GB300 mapping: a persistent kernel with one 1024-thread CTA per SM.  A CTA
-// takes whole pad rows from a device work counter and keeps the row's charge
-// map (n_pad x n_time u16, 140 KB for the outermost row) and a peak bitmap in
-// shared memory: digits are scattered in once from HBM (coalesced), every
-// neighbourhood test then reads shared memory only, and the map is cleared by
-// re-scattering zeros at the same cells.  Output positions come from a
-// single-pass decoupled look-back over the rows (each row publishes its
-// cluster count, then its inclusive prefix), so clusters are written once,
-// densely and in order.  Waits in the look-back are bounded; a timeout sets a
-// status bit.
+// GB300 mapping, three kernels and a scan:
+//   k_cf_sort    one CTA per pad row: a counting sort of the row's digits by
+//                time bin (shared-memory histogram and scan) into packed
+//                32-bit words, and the row's time-bin starts;
+//   k_clusterer  persistent, 256-thread CTAs, four per SM; a work item is one
+//                pad row and one tile of kTileT time bins, whose digits (plus
+//                three bins on each side) are now one contiguous range.  The
+//                CTA scatters them into a shared-memory charge map with a zero
+//                border (no bounds tests), tests peaks and valleys there, ranks
+//                the kept peaks in (time, pad) order by one scan over a kept-peak
+//                bitmap and writes the clusters to a staging area at slots taken
+//                with one atomic per item: CTAs never wait for one another;
+//   scan, k_cf_emit  the items' counts give every item its place in the
+//                output; a warp per item moves its staged clusters there and
+//                derives x, y, z and the flags.
 #include "tpct_internal.cuh"
 
 namespace tpct {
 namespace {
 
-constexpr int kCfThreads = 1024;
-constexpr int kCfMaxPeaks = 8192;          // kept peaks per row held in shared memory
-constexpr int kCfPerThread = 8;            // digits per thread: rows of up to 8192 digits
-constexpr int kCfMaxSpins = 1 << 22;       // look-back polls before giving up
-constexpr uint64_t kLbAgg = 1ull << 62, kLbInc = 2ull << 62, kLbMask = (1ull << 62) - 1;
+constexpr int kCfThreads = 256;
+constexpr int kCfWarps = kCfThreads / 32;
+constexpr int kTileT = 128;                // time bins per work item
+constexpr int kHalo = 3;                   // map rows kept on each side of a tile
+constexpr int kMapRows = kTileT + 2 * kHalo;
+constexpr int kWordsPer = kTileT * 256 / 32 / kCfThreads;   // kept-bitmap words per thread (pads <= 252)
+constexpr int kCfMaxPeaks = 2048;          // kept peaks of a tile
+constexpr int kCfPerSm = 4;                // resident CTAs per SM
+constexpr int kMaxTime = 512;              // time bins per row at most
+constexpr int kSortThreads = 256;
+constexpr int kSortU = 4;                  // digits per thread in flight in the sort passes
+constexpr int kScanPer = (kMaxTime + 1 + kSortThreads - 1) / kSortThreads;
+constexpr int kEmitThreads = 256;
+
+// A staged cluster: moments and charges, peak cell packed as p | t << 8 | q << 17.
+struct __align__(8) CfStage {
+  float cp, ct, sp, st;
+  uint32_t qtot, ptq;
+};
 
 struct CfDev {
   const uint16_t *pad, *time, *adc;
   const int64_t* row_offsets;
   const int32_t* inst_sector;
-  int32_t n_inst, n_rows, n_time, np_max;
+  int32_t n_inst, n_rows, n_time, n_tiles;
+  int32_t wp;                               // map row width: pads + 4, a multiple of 32
   int32_t q_peak_min, valley_delta;
   float z_max, time_bin;
-  uint32_t map_words, bit_words;            // shared-memory layout (32-bit words)
-  uint64_t* lookback;                       // [n_inst * n_rows]
-  uint32_t* work;                           // [1]
+  uint32_t* work;                           // [2] item counter, staging counter
+  uint32_t* srt;                            // [srt_cap] packed digits, sorted by time inside each row
+  int64_t srt_cap;
+  int32_t* tpos;                            // [rows][kMaxTime + 1] time-bin starts in the sorted row
+  int32_t *item_cnt, *item_at, *item_dst;   // [n_items] clusters, staging slot, output slot (+1: total)
+  CfStage* stage;                           // [out.capacity]
   int16_t n_pad[kMaxRows];
   float pitch[kMaxRows], row_x[kMaxRows];
   tpct_cf_out out;
 };
 
-// The row map has a border of two empty cells on every side: cell (p, t) of
-// the row lives at (p + 2) * W + (t + 2) with W = n_time + 4, so every
-// neighbourhood read up to distance 2 stays inside the map without a bounds
-// test (border and unused cells hold 0; the peak bitmap has the same layout).
+// The tile map: cell (p, t) of the row, t in [t0 - 3, t0 + kTileT + 3), lives
+// at (t - t0 + 3) * wp + (p + 2).  Pads -2, -1 and >= n_pad and time bins
+// outside the row hold 0, so every neighbourhood read up to distance 2 of a
+// cell in [t0 - 1, t0 + kTileT + 1) stays inside the map without a bounds test.
 __device__ __forceinline__ bool before(int dp, int dt) { return dt < 0 || (dt == 0 && dp < 0); }
 __device__ __forceinline__ int half_step(int d) { return d == 2 ? 1 : (d == -2 ? -1 : 0); }
 __device__ __forceinline__ bool bit_at(const uint32_t* bits, int cell) { return (bits[cell >> 5] >> (cell & 31)) & 1u; }
@@ -66,7 +89,7 @@ __device__ __forceinline__ bool peak_test(const uint16_t* map, int W, int c, int
 #pragma unroll
     for (int dp = -1; dp <= 1; ++dp) {
       if (dp == 0 && dt == 0) continue;
-      const int qn = map[c + dp * W + dt];
+      const int qn = map[c + dt * W + dp];
       ok &= before(dp, dt) ? q > qn : q >= qn;
     }
   return ok;
@@ -80,61 +103,51 @@ __device__ __forceinline__ bool suppressed(const uint16_t* map, const uint32_t* 
 #pragma unroll
     for (int dp = -2; dp <= 2; ++dp) {
       if (dp > -2 && dp < 2 && dt > -2 && dt < 2) continue;   // the Chebyshev-2 ring only
-      const int c2 = c + dp * W + dt;
+      const int c2 = c + dt * W + dp;
       if (!bit_at(bits, c2)) continue;
       const int q2 = map[c2];
       if (!(q2 > q || (q2 == q && before(dp, dt)))) continue;
-      sup |= (int)map[c + half_step(dp) * W + half_step(dt)] >= q - delta;
+      sup |= (int)map[c + half_step(dt) * W + half_step(dp)] >= q - delta;
     }
   return sup;
 }
 
-__device__ __forceinline__ uint64_t ld_volatile(const uint64_t* a) {
-  return *reinterpret_cast<const volatile unsigned long long*>(a);
-}
-
-// A digit in one register: pad (8 bits) | time (9 bits) | adc (15 bits).
-constexpr uint32_t kNoDigit = 0xffffffffu;
-__device__ __forceinline__ int w_pad(uint32_t w) { return (int)(w >> 24); }
-__device__ __forceinline__ int w_time(uint32_t w) { return (int)((w >> 15) & 511u); }
-__device__ __forceinline__ int w_adc(uint32_t w) { return (int)(w & 32767u); }
-
 struct Cluster {
   float cp, ct, sp, st;
   uint32_t qtot;
-  uint32_t packed;   // the peak digit
+  int p, t, q;
 };
 
-__device__ __forceinline__ Cluster build_cluster(const uint16_t* map, int W, uint32_t pw) {
-  const int p = w_pad(pw), t = w_time(pw);
-  const int c = (p + 2) * W + (t + 2);
+__device__ __forceinline__ Cluster build_cluster(const uint16_t* map, int W, int c, int t0) {
+  const int p = c % W - 2, tl = c / W;
   int s0 = 0, sp = 0, st = 0, spp = 0, stt = 0;
 #pragma unroll
   for (int dt = -2; dt <= 2; ++dt)
 #pragma unroll
     for (int dp = -2; dp <= 2; ++dp) {
-      const int qc = map[c + dp * W + dt];
+      const int qc = map[c + dt * W + dp];
       const bool outer = dp == 2 || dp == -2 || dt == 2 || dt == -2;
-      const bool take = qc > 0 && (!outer || qc <= (int)map[c + half_step(dp) * W + half_step(dt)]);
+      const bool take = qc > 0 && (!outer || qc <= (int)map[c + half_step(dt) * W + half_step(dp)]);
       const int q = take ? qc : 0;
       s0 += q; sp += q * dp; st += q * dt; spp += q * dp * dp; stt += q * dt * dt;
     }
   const float fs0 = (float)s0;
   const float mp = __fdiv_rn((float)sp, fs0), mt = __fdiv_rn((float)st, fs0);
   Cluster k;
+  k.p = p;
+  k.t = t0 + tl - kHalo;
+  k.q = map[c];
   k.cp = (float)p + mp;
-  k.ct = (float)t + mt;
+  k.ct = (float)k.t + mt;
   k.sp = sqrtf(fmaxf(__fdiv_rn((float)spp, fs0) - mp * mp, 0.f));
   k.st = sqrtf(fmaxf(__fdiv_rn((float)stt, fs0) - mt * mt, 0.f));
   k.qtot = (uint32_t)s0;
-  k.packed = pw;
   return k;
 }
 
 __device__ __forceinline__ void store_cluster(const tpct_cf_out& O, long long slot, const Cluster& k, float row_x,
                                               float pitch, int np, int nt, float side, float z_max, float time_bin,
                                               int r) {
-  const int p = w_pad(k.packed), t = w_time(k.packed);
   O.pad[slot] = k.cp;
   O.time[slot] = k.ct;
   O.sigma_pad[slot] = k.sp;
@@ -143,205 +156,303 @@ __device__ __forceinline__ void store_cluster(const tpct_cf_out& O, long long sl
   O.y[slot] = (k.cp + 0.5f - 0.5f * (float)np) * pitch;
   O.z[slot] = side * (z_max - (k.ct + 0.5f) * time_bin);
   O.q_tot[slot] = k.qtot;
-  O.q_max[slot] = (uint16_t)w_adc(k.packed);
+  O.q_max[slot] = (uint16_t)k.q;
   O.row[slot] = (uint8_t)r;
-  O.flags[slot] = (uint8_t)((p == 0 || p == np - 1 ? 1 : 0) | (t == 0 || t == nt - 1 ? 2 : 0));
+  O.flags[slot] = (uint8_t)((k.p == 0 || k.p == np - 1 ? 1 : 0) | (k.t == 0 || k.t == nt - 1 ? 2 : 0));
 }
 
-__global__ void __launch_bounds__(kCfThreads, 1) k_clusterer(const __grid_constant__ CfDev P) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  uint16_t* map = reinterpret_cast<uint16_t*>(smem);
-  uint32_t* bits = smem + P.map_words;
-  uint32_t* peaks = bits + P.bit_words;          // kept peaks of the row (packed digits), in input order
-  __shared__ int s_next[2];                     // row of this / the next iteration (by parity)
-  __shared__ long long s_nb[2], s_ne[2];
-  __shared__ uint32_t s_ball[kCfPerThread][kCfThreads / 32];
-  __shared__ int s_pref[kCfPerThread][kCfThreads / 32];
-  __shared__ int s_count;
-  __shared__ long long s_base;
+// Pass 1, one CTA per pad row: counting sort of the row's digits by time bin
+// into packed words (pad | time << 8 | ADC << 17), plus the row's time-bin
+// starts (tpos[t] = first sorted digit with time >= t, row-relative).  The
+// order inside a time bin is that of the atomics; nothing downstream depends
+// on it (cells are unique and the peaks are ranked from a bitmap).
+__global__ void __launch_bounds__(kSortThreads) k_cf_sort(const __grid_constant__ CfDev P) {
+  __shared__ int hist[kMaxTime + 1];
+  __shared__ int s_wsum[kSortThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t lanes_below = (1u << lane) - 1u;
-  const int nt = P.n_time, W = nt + 4;
+  const int nt = P.n_time;
   const int n_rows_total = P.n_inst * P.n_rows;
   const tpct_cf_out& O = P.out;
+  for (int row = blockIdx.x; row < n_rows_total; row += gridDim.x) {
+    const int64_t b = P.row_offsets[row];
+    int64_t e = P.row_offsets[row + 1];
+    if (e > P.srt_cap) {   // beyond the workspace: the row is left empty
+      if (tid == 0) atomicOr(O.status, TPCT_CF_WORKSPACE);
+      e = b;
+    }
+    const int np = P.n_pad[row % P.n_rows];
+    for (int t = tid; t <= kMaxTime; t += kSortThreads) hist[t] = 0;
+    __syncthreads();
+    // both passes load kSortU digits per thread before using any
+    for (int64_t base = b; base < e; base += kSortThreads * kSortU) {
+      uint32_t pv[kSortU], tv[kSortU], qv[kSortU];
+#pragma unroll
+      for (int u = 0; u < kSortU; ++u) {
+        const int64_t i = base + u * kSortThreads + tid;
+        pv[u] = i < e ? P.pad[i] : 0u;
+        tv[u] = i < e ? P.time[i] : 0u;
+        qv[u] = i < e ? P.adc[i] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kSortU; ++u) {
+        if (base + u * kSortThreads + tid >= e) break;
+        if ((int)pv[u] < np && (int)tv[u] < nt && qv[u] < 32768u) atomicAdd(&hist[tv[u]], 1);
+        else atomicOr(O.status, TPCT_CF_BAD_DIGIT);
+      }
+    }
+    __syncthreads();
+    // exclusive scan of hist[0, kMaxTime]: kScanPer bins per thread
+    int v[kScanPer], sum = 0;
+#pragma unroll
+    for (int u = 0; u < kScanPer; ++u) {
+      const int t = tid * kScanPer + u;
+      v[u] = t <= kMaxTime ? hist[t] : 0;
+      sum += v[u];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += x;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    int run = incl - sum;
+#pragma unroll
+    for (int q = 0; q < kSortThreads / 32; ++q) run += q < warp ? s_wsum[q] : 0;
+    int32_t* tp = P.tpos + (int64_t)row * (kMaxTime + 1);
+#pragma unroll
+    for (int u = 0; u < kScanPer; ++u) {
+      const int t = tid * kScanPer + u;
+      if (t <= kMaxTime) {
+        hist[t] = run;     // becomes the bin's cursor
+        tp[t] = run;
+      }
+      run += v[u];
+    }
+    __syncthreads();
+    for (int64_t base = b; base < e; base += kSortThreads * kSortU) {
+      uint32_t pv[kSortU], tv[kSortU], qv[kSortU];
+#pragma unroll
+      for (int u = 0; u < kSortU; ++u) {
+        const int64_t i = base + u * kSortThreads + tid;
+        pv[u] = i < e ? P.pad[i] : 0u;
+        tv[u] = i < e ? P.time[i] : 0u;
+        qv[u] = i < e ? P.adc[i] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kSortU; ++u) {
+        if (base + u * kSortThreads + tid >= e) break;
+        if ((int)pv[u] < np && (int)tv[u] < nt && qv[u] < 32768u) {
+          const int at = atomicAdd(&hist[tv[u]], 1);
+          P.srt[b + at] = pv[u] | (tv[u] << 8) | (qv[u] << 17);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
 
-  for (uint32_t i = tid; i < P.map_words + P.bit_words; i += kCfThreads) smem[i] = 0u;
+__device__ __forceinline__ int w_cell(uint32_t w, int t0, int W) {
+  return ((int)((w >> 8) & 511u) - t0 + kHalo) * W + (int)(w & 255u) + 2;
+}
+
+// Pass 2: one (row, time tile) per work item, its digits a contiguous range
+// of the sorted row.
+__global__ void __launch_bounds__(kCfThreads, kCfPerSm) k_clusterer(const __grid_constant__ CfDev P) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int W = P.wp;
+  const int map_words = kMapRows * W / 2, bit_words = kMapRows * W / 32;
+  uint16_t* map = reinterpret_cast<uint16_t*>(smem);
+  uint32_t* peak_bits = smem + map_words;
+  uint32_t* kept_bits = peak_bits + bit_words;
+  uint32_t* peaks = kept_bits + bit_words;        // map cells of the kept peaks, in (time, pad) order
+  // an item's row start and sorted ranges: the map (tile +- 3 bins), the
+  // peak tests (+- 2), the core; kept by parity like the item index
+  __shared__ int s_item[2];
+  __shared__ long long s_rb[2];
+  __shared__ int s_rng[2][6];
+  __shared__ int s_at;
+  __shared__ int s_wsum[kCfWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nt = P.n_time;
+  const int n_items = P.n_inst * P.n_rows * P.n_tiles;
+  const tpct_cf_out& O = P.out;
+  // tid 0 reads an item's row start and ranges (two independent loads deep)
+  auto item_ranges = [&](int itm, long long& rb_o, int* rng) {
+    const int rw = itm / P.n_tiles, tl = itm % P.n_tiles;
+    const int a = tl * kTileT, z = min(a + kTileT, nt);
+    const int32_t* tq = P.tpos + (int64_t)rw * (kMaxTime + 1);
+    rb_o = P.row_offsets[rw];
+    rng[0] = tq[max(a - 3, 0)]; rng[1] = tq[min(z + 3, nt)];
+    rng[2] = tq[max(a - 2, 0)]; rng[3] = tq[min(z + 2, nt)];
+    rng[4] = tq[a];             rng[5] = tq[z];
+  };
+
+  for (int i = tid; i < map_words + 2 * bit_words; i += kCfThreads) smem[i] = 0u;
   if (tid == 0) {
-    const int r0 = (int)atomicAdd(P.work, 1u);
-    s_next[0] = r0;
-    if (r0 < n_rows_total) { s_nb[0] = P.row_offsets[r0]; s_ne[0] = P.row_offsets[r0 + 1]; }
+    const int it0 = (int)atomicAdd(&P.work[0], 1u);
+    s_item[0] = it0;
+    if (it0 < n_items) {
+      long long rb0;
+      int rng0[6];
+      item_ranges(it0, rb0, rng0);
+      s_rb[0] = rb0;
+      for (int q = 0; q < 6; ++q) s_rng[0][q] = rng0[q];
+    }
   }
   __syncthreads();
 
   for (int it = 0;; ++it) {
     const int cur = it & 1, nxt = cur ^ 1;
-    const int row = s_next[cur];
-    if (row >= n_rows_total) break;
-    const int64_t b = s_nb[cur], e = s_ne[cur];
-    // the next row's index and range, fetched while this row is processed
-    // (the other parity slot: every thread read it before the last barrier)
+    const int item = s_item[cur];
+    if (item >= n_items) break;
+    // the next item, taken now (no CTA waits for another, so holding it costs
+    // nothing); tid 0 reads its ranges during this item and hands them over
+    // at its end
+    int nx = 0;
+    long long nx_rb = 0;
+    int nx_rng[6] = {0, 0, 0, 0, 0, 0};
+    if (tid == 0) nx = (int)atomicAdd(&P.work[0], 1u);
+    const int tile = item % P.n_tiles;
+    const int t0 = tile * kTileT, t1 = min(t0 + kTileT, nt);
+    const int core_lo = kHalo * W, core_hi = (t1 - t0 + kHalo) * W;
+    const uint32_t* sd = P.srt + s_rb[cur];
+    const int m_lo = s_rng[cur][0], m_hi = s_rng[cur][1];
+    const int p_lo = s_rng[cur][2], p_hi = s_rng[cur][3];
+    const int c_lo = s_rng[cur][4], c_hi = s_rng[cur][5];
+
+    for (int k = m_lo + tid; k < m_hi; k += kCfThreads) {
+      const uint32_t w = sd[k];
+      map[w_cell(w, t0, W)] = (uint16_t)(w >> 17);
+    }
+    __syncthreads();
+    if (tid == 0 && nx < n_items) item_ranges(nx, nx_rb, nx_rng);   // used at the end of this item
+    for (int k = p_lo + tid; k < p_hi; k += kCfThreads) {
+      const int c = w_cell(sd[k], t0, W);
+      if (peak_test(map, W, c, P.q_peak_min)) atomicOr(&peak_bits[c >> 5], 1u << (c & 31));
+    }
+    __syncthreads();
+    for (int k = c_lo + tid; k < c_hi; k += kCfThreads) {
+      const int c = w_cell(sd[k], t0, W);
+      if (bit_at(peak_bits, c) && !suppressed(map, peak_bits, W, c, P.valley_delta))
+        atomicOr(&kept_bits[c >> 5], 1u << (c & 31));
+    }
+    __syncthreads();
+    // rank the kept peaks in cell order = (time, pad) order: one scan over the
+    // bitmap words of the tile's time bins (W is a multiple of 32, so a word
+    // never straddles two time bins)
+    const int w_lo = core_lo >> 5, w_hi = core_hi >> 5;
+    int sum = 0;
+#pragma unroll
+    for (int u = 0; u < kWordsPer; ++u) {
+      const int wi = w_lo + tid * kWordsPer + u;
+      sum += wi < w_hi ? __popc(kept_bits[wi]) : 0;
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    int wbase = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < kCfWarps; ++q) {
+      const int v = s_wsum[q];
+      wbase += q < warp ? v : 0;
+      total += v;
+    }
+    int rank = wbase + incl - sum;
+#pragma unroll
+    for (int u = 0; u < kWordsPer; ++u) {
+      const int wi = w_lo + tid * kWordsPer + u;
+      if (wi >= w_hi) break;
+      uint32_t m = kept_bits[wi];
+      while (m) {
+        const int bpos = __ffs(m) - 1;
+        m &= m - 1;
+        if (rank < kCfMaxPeaks) peaks[rank] = (uint32_t)(wi * 32 + bpos);
+        ++rank;
+      }
+    }
+    __syncthreads();   // peaks[] complete
+    // staging slots: one atomic per item, issued before the first cluster is
+    // built (from shared memory, into registers) and read after it
+    const int nk = min(total, kCfMaxPeaks);
+    int at_mine = 0;
     if (tid == 0) {
-      const int nx = (int)atomicAdd(P.work, 1u);
-      s_next[nxt] = nx;
-      if (nx < n_rows_total) { s_nb[nxt] = P.row_offsets[nx]; s_ne[nxt] = P.row_offsets[nx + 1]; }
+      if (total > kCfMaxPeaks) atomicOr(O.status, TPCT_CF_ROW_OVERFLOW);
+      at_mine = nk > 0 ? (int)atomicAdd(&P.work[1], (uint32_t)nk) : 0;
     }
-    const int r = row % P.n_rows, inst = row / P.n_rows;
-    const int np = P.n_pad[r];
-    if (tid == 0 && e - b > (int64_t)kCfPerThread * kCfThreads) atomicOr(O.status, TPCT_CF_ROW_OVERFLOW);
-
-    // the row's digits, k-major (digit b + k * 1024 + tid), loaded once
-    uint32_t w[kCfPerThread];
-#pragma unroll
-    for (int k = 0; k < kCfPerThread; ++k) {
-      const int64_t i = b + (int64_t)k * kCfThreads + tid;
-      w[k] = kNoDigit;
-      if (i < e) {
-        const uint32_t p = P.pad[i], t = P.time[i], q = P.adc[i];
-        if ((int)p < np && (int)t < nt && q < 32768u) w[k] = (p << 24) | (t << 15) | q;
-        else atomicOr(O.status, TPCT_CF_BAD_DIGIT);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kCfPerThread; ++k)
-      if (w[k] != kNoDigit) map[(w_pad(w[k]) + 2) * W + w_time(w[k]) + 2] = (uint16_t)w_adc(w[k]);
-    __syncthreads();
-    // peaks
-#pragma unroll
-    for (int k = 0; k < kCfPerThread; ++k)
-      if (w[k] != kNoDigit) {
-        const int c = (w_pad(w[k]) + 2) * W + w_time(w[k]) + 2;
-        if (peak_test(map, W, c, P.q_peak_min)) atomicOr(&bits[c >> 5], 1u << (c & 31));
-      }
-    __syncthreads();
-    // kept peaks: one ballot per k, then one scan over (k, warp) gives every
-    // kept digit its rank in input order
-    uint32_t keep = 0u;
-#pragma unroll
-    for (int k = 0; k < kCfPerThread; ++k) {
-      bool kp = false;
-      if (w[k] != kNoDigit) {
-        const int c = (w_pad(w[k]) + 2) * W + w_time(w[k]) + 2;
-        kp = bit_at(bits, c) && !suppressed(map, bits, W, c, P.valley_delta);
-      }
-      const uint32_t ball = __ballot_sync(0xffffffffu, kp);
-      if (lane == 0) s_ball[k][warp] = ball;
-      keep |= (kp ? 1u : 0u) << k;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      // lane j owns the (k, warp) entries [kPer j, kPer (j + 1)) of the k-major list
-      constexpr int kPer = kCfPerThread * (kCfThreads / 32) / 32;
-      int loc[kPer], sum = 0;
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) {
-        const int f = lane * kPer + u;
-        loc[u] = sum;
-        sum += __popc(s_ball[f / (kCfThreads / 32)][f % (kCfThreads / 32)]);
-      }
-      int incl = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-      }
-      const int excl = incl - sum;
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) {
-        const int f = lane * kPer + u;
-        s_pref[f / (kCfThreads / 32)][f % (kCfThreads / 32)] = excl + loc[u];
-      }
-      if (lane == 31) s_count = incl;
-    }
-    __syncthreads();
-    const int count = s_count;
-#pragma unroll
-    for (int k = 0; k < kCfPerThread; ++k)
-      if ((keep >> k) & 1u) {
-        const int rank = s_pref[k][warp] + __popc(s_ball[k][warp] & lanes_below);
-        if (rank < kCfMaxPeaks) peaks[rank] = w[k];
-      }
-    if (count > kCfMaxPeaks && tid == 0) atomicOr(O.status, TPCT_CF_ROW_OVERFLOW);
-    __syncthreads();
-
-    // The last warp runs the decoupled look-back (publish the row's count,
-    // read the states of the 32 preceding rows at once; the nearest one with
-    // an inclusive prefix ends the walk, all nearer ones must have published
-    // their counts; else add all 32 counts and move 32 rows back; publish the
-    // inclusive prefix) while the other warps build their first clusters.
-    const int nk = min(count, kCfMaxPeaks);
-    constexpr int kBuilders = kCfThreads - 32;
     Cluster mine;
-    const bool have = warp < kCfThreads / 32 - 1 && tid < nk;
-    if (have) mine = build_cluster(map, W, peaks[tid]);
-    if (warp == kCfThreads / 32 - 1) {
-      long long prefix = 0;
-      if (lane == 0) {
-        __threadfence();
-        atomicExch((unsigned long long*)&P.lookback[row],
-                   (unsigned long long)((row == 0 ? kLbInc : kLbAgg) | (uint64_t)count));
-      }
-      if (row > 0) {
-        int j0 = row - 1, spins = 0;
-        while (true) {
-          const int j = j0 - lane;
-          const uint64_t v = j >= 0 ? ld_volatile(&P.lookback[j]) : kLbInc;   // before row 0: prefix 0
-          const uint32_t st = (uint32_t)(v >> 62);
-          const uint32_t inc = __ballot_sync(0xffffffffu, st == 2u);
-          const uint32_t unset = __ballot_sync(0xffffffffu, st == 0u);
-          const int first = inc ? __ffs(inc) - 1 : 32;
-          const uint32_t upto = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
-          if (unset & upto) {
-            if (++spins > kCfMaxSpins) {
-              if (lane == 0) atomicOr(O.status, TPCT_CF_TIMEOUT);
-              break;
-            }
-            __nanosleep(64);
-            continue;
-          }
-          long long val = lane <= first ? (long long)(v & kLbMask) : 0;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
-          prefix += __shfl_sync(0xffffffffu, val, 0);
-          if (first < 32) break;
-          j0 -= 32;
-        }
-        if (lane == 0) {
-          __threadfence();
-          atomicExch((unsigned long long*)&P.lookback[row],
-                     (unsigned long long)(kLbInc | (uint64_t)(prefix + count)));
-        }
-      }
-      if (lane == 0) {
-        s_base = prefix;
-        if (r == 0 && O.inst_offsets) O.inst_offsets[inst] = prefix;
-        if (row == n_rows_total - 1) {
-          *O.n_clusters = (int32_t)min(prefix + count, (long long)0x7fffffff);
-          if (O.inst_offsets) O.inst_offsets[P.n_inst] = prefix + count;
-          if (prefix + count > O.capacity) atomicOr(O.status, TPCT_CF_CAPACITY);
-        }
-      }
+    if (tid < nk) mine = build_cluster(map, W, (int)peaks[tid], t0);
+    if (tid == 0) {
+      s_at = at_mine;
+      P.item_cnt[item] = nk;
+      P.item_at[item] = at_mine;
     }
     __syncthreads();
-    const long long base_out = s_base;
+    const long long at = s_at;
+    auto stage = [&](int k, const Cluster& c) {
+      if (at + k >= O.capacity) return;   // the output is too small: reported by the emit pass
+      CfStage g;
+      g.cp = c.cp; g.ct = c.ct; g.sp = c.sp; g.st = c.st; g.qtot = c.qtot;
+      g.ptq = (uint32_t)c.p | ((uint32_t)c.t << 8) | ((uint32_t)c.q << 17);
+      P.stage[at + k] = g;
+    };
+    if (tid < nk) stage(tid, mine);
+    for (int k = kCfThreads + tid; k < nk; k += kCfThreads) stage(k, build_cluster(map, W, (int)peaks[k], t0));
+    __syncthreads();
+    // clear what this item set: the map cells of its digits and the bitmap
+    // words holding their bits
+    for (int k = m_lo + tid; k < m_hi; k += kCfThreads) {
+      const int c = w_cell(sd[k], t0, W);
+      map[c] = 0;
+      peak_bits[c >> 5] = 0u;
+      kept_bits[c >> 5] = 0u;
+    }
+    if (tid == 0) {   // the other parity slot: read by all before this item's first barrier
+      s_item[nxt] = nx;
+      s_rb[nxt] = nx_rb;
+      for (int q = 0; q < 6; ++q) s_rng[nxt][q] = nx_rng[q];
+    }
+    __syncthreads();
+  }
+}
+
+// One warp per item: the staged clusters to their place in the output.
+__global__ void __launch_bounds__(kEmitThreads) k_cf_emit(const __grid_constant__ CfDev P) {
+  const int lane = threadIdx.x & 31;
+  const int n_items = P.n_inst * P.n_rows * P.n_tiles;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const tpct_cf_out& O = P.out;
+  const long long cap = O.capacity;
+  for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < n_items; item += warps) {
+    const int cnt = P.item_cnt[item];
+    const long long src = P.item_at[item], dst = P.item_dst[item];
+    const int row = item / P.n_tiles, tile = item % P.n_tiles;
+    const int r = row % P.n_rows, inst = row / P.n_rows;
+    if (lane == 0 && r == 0 && tile == 0 && O.inst_offsets) O.inst_offsets[inst] = dst;
+    if (cnt == 0) continue;
+    const int np = P.n_pad[r];
     const float pitch = P.pitch[r], xr = P.row_x[r];
     const float side = P.inst_sector[inst] >= 18 ? -1.f : 1.f;
-    if (have && base_out + tid < O.capacity)
-      store_cluster(O, base_out + tid, mine, xr, pitch, np, nt, side, P.z_max, P.time_bin, r);
-    for (int k = kBuilders + tid; k < nk; k += kCfThreads) {   // rows with more clusters than builders
-      if (base_out + k >= O.capacity) break;
-      store_cluster(O, base_out + k, build_cluster(map, W, peaks[k]), xr, pitch, np, nt, side, P.z_max,
-                    P.time_bin, r);
+    for (int k = lane; k < cnt; k += 32) {
+      if (src + k >= cap || dst + k >= cap) break;
+      const CfStage g = P.stage[src + k];
+      Cluster c;
+      c.cp = g.cp; c.ct = g.ct; c.sp = g.sp; c.st = g.st; c.qtot = g.qtot;
+      c.p = (int)(g.ptq & 255u); c.t = (int)((g.ptq >> 8) & 511u); c.q = (int)(g.ptq >> 17);
+      store_cluster(O, dst + k, c, xr, pitch, np, P.n_time, side, P.z_max, P.time_bin, r);
     }
-    __syncthreads();
-    // clear the row's cells and peak bits
-#pragma unroll
-    for (int k = 0; k < kCfPerThread; ++k)
-      if (w[k] != kNoDigit) {
-        const int c = (w_pad(w[k]) + 2) * W + w_time(w[k]) + 2;
-        map[c] = 0;
-        bits[c >> 5] = 0u;
-      }
-    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const long long total = P.item_dst[n_items];
+    *O.n_clusters = (int32_t)total;
+    if (O.inst_offsets) O.inst_offsets[P.n_inst] = total;
+    if (total > cap) atomicOr(O.status, TPCT_CF_CAPACITY);
   }
 }
 
@@ -353,12 +464,37 @@ int cf_pads(double row_x, double tan_half, double pitch) {
   return 2 * (int)std::ceil(row_x * tan_half / pitch - 1e-9);
 }
 
-// map: (np_max + 4) x (n_time + 4) u16 with a two-cell empty border; bitmap: one bit per map cell
-size_t cf_map_cells(int np_max, int n_time) { return (size_t)(np_max + 4) * (n_time + 4); }
-size_t cf_smem_bytes(int np_max, int n_time) {
-  const size_t cells = cf_map_cells(np_max, n_time);
-  return 4 * ((cells + 1) / 2 + (cells + 31) / 32) + 4 * (size_t)kCfMaxPeaks;
+size_t cf_smem_bytes(int wp) {
+  return 4 * ((size_t)kMapRows * wp / 2 + 2 * (size_t)kMapRows * wp / 32 + kCfMaxPeaks);
 }
+
+namespace {
+// Workspace: counters | item counts | staging slots | output slots (+ total) |
+// scan temporaries | sorted digits | time-bin starts | staging area.
+size_t cf_carve(char* base, int64_t n_digits, size_t n_rows_total, size_t n_items, int32_t capacity, CfDev* P,
+                uint64_t** tmp) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* q = base ? base + off : nullptr;
+    off += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  uint32_t* work = (uint32_t*)take(256);
+  int32_t* cnt = (int32_t*)take(4 * std::max<size_t>(n_items, 1));
+  int32_t* at = (int32_t*)take(4 * std::max<size_t>(n_items, 1));
+  int32_t* dst = (int32_t*)take(4 * (n_items + 1));
+  uint64_t* t = (uint64_t*)take(8 * ((size_t)scan_tmp_elems((int64_t)n_items) + 32));
+  int32_t* tpos = (int32_t*)take(4 * (size_t)(kMaxTime + 1) * std::max<size_t>(n_rows_total, 1));
+  CfStage* stage = (CfStage*)take(sizeof(CfStage) * (size_t)std::max(capacity, 1));
+  uint32_t* srt = (uint32_t*)take(4 * (size_t)std::max<int64_t>(n_digits, 1));   // last: sized by the caller
+  if (P) {
+    P->work = work; P->item_cnt = cnt; P->item_at = at; P->item_dst = dst; P->stage = stage;
+    P->srt = srt; P->tpos = tpos;
+    *tmp = t;
+  }
+  return off;
+}
+}  // namespace
 
 // Enqueue cluster finding; returns the kernels launched, or -1 (invalid
 // readout), -2 (workspace too small), -3 (shared memory too large), -4 (CUDA).
@@ -373,46 +509,60 @@ int enqueue_clusters(const double* row_x, int n_rows, double tan_half, double z_
   for (int r = 0; r < n_rows; ++r) {
     const double pitch = r < prm.n_inner_rows ? prm.pad_pitch_inner : prm.pad_pitch_outer;
     const int np = cf_pads(row_x[r], tan_half, pitch);
-    if (np < 1 || np > 256) return -1;
+    if (np < 1 || np > 252) return -1;
     P.n_pad[r] = (int16_t)np;
     P.pitch[r] = (float)pitch;
     P.row_x[r] = (float)row_x[r];
     np_max = np > np_max ? np : np_max;
   }
-  const size_t smem = cf_smem_bytes(np_max, prm.n_time);
+  const int wp = (np_max + 4 + 31) / 32 * 32;
+  const size_t smem = cf_smem_bytes(wp);
   int dev = 0, max_optin = 0, n_sm = 0;
   if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return -4;
   if ((*err = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return -4;
   if ((*err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return -4;
-  if (smem + 2048 > (size_t)max_optin) return -3;
+  if (smem + 1024 > (size_t)max_optin) return -3;
+  const int n_tiles = (prm.n_time + kTileT - 1) / kTileT;
   const size_t n_rows_total = (size_t)dg.n_instances * n_rows;
-  const size_t need = 8 * n_rows_total + 256;
-  if (ws_bytes < need) return -2;
+  const size_t n_items = n_rows_total * n_tiles;
+  // the sorted digits take the rest of the workspace (rows that end beyond
+  // it are skipped and reported on the device)
+  uint64_t* tmp = nullptr;
+  const size_t srt_at = cf_carve(nullptr, 1, n_rows_total, n_items, out.capacity, nullptr, nullptr) - 256;
+  if (ws_bytes < srt_at + 256) return -2;
+  cf_carve((char*)ws, 1, n_rows_total, n_items, out.capacity, &P, &tmp);
+  P.srt_cap = (int64_t)((ws_bytes - srt_at) / 4);
   P.pad = dg.pad; P.time = dg.time; P.adc = dg.adc; P.row_offsets = dg.row_offsets; P.inst_sector = dg.inst_sector;
-  P.n_inst = dg.n_instances; P.n_rows = n_rows; P.n_time = prm.n_time; P.np_max = np_max;
+  P.n_inst = dg.n_instances; P.n_rows = n_rows; P.n_time = prm.n_time; P.n_tiles = n_tiles; P.wp = wp;
   P.q_peak_min = prm.q_peak_min; P.valley_delta = prm.valley_delta;
   P.z_max = (float)z_max; P.time_bin = (float)prm.time_bin;
-  P.map_words = (uint32_t)((cf_map_cells(np_max, prm.n_time) + 1) / 2);
-  P.bit_words = (uint32_t)((cf_map_cells(np_max, prm.n_time) + 31) / 32);
-  P.work = (uint32_t*)ws;
-  P.lookback = (uint64_t*)((char*)ws + 256);
   P.out = out;
   if ((*err = cudaFuncSetAttribute(k_clusterer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return -4;
+  int per_sm = 0;
+  if ((*err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clusterer, kCfThreads, smem)) != cudaSuccess)
+    return -4;
   int k = 0;
-  cudaMemsetAsync(ws, 0, need, s);
+  cudaMemsetAsync(P.work, 0, 256, s);
   cudaMemsetAsync(out.status, 0, sizeof(uint32_t), s);
   cudaMemsetAsync(out.n_clusters, 0, sizeof(int32_t), s);
-  if (n_rows_total > 0) {
-    const int grid = (int)std::min<size_t>((size_t)n_sm, n_rows_total);
+  if (n_items > 0) {
+    k_cf_sort<<<(int)std::min<size_t>(n_rows_total, (size_t)n_sm * 8), kSortThreads, 0, s>>>(P); ++k;
+    const int grid = (int)std::min<size_t>((size_t)n_sm * std::max(per_sm, 1), n_items);
     k_clusterer<<<grid, kCfThreads, smem, s>>>(P); ++k;
   }
+  launch_scan_i32(P.item_cnt, P.item_dst, (int64_t)n_items, tmp, s); k += n_items > 0 ? 3 : 1;
+  const int emit_blocks = (int)std::max<size_t>(1, std::min<size_t>((n_items * 32 + kEmitThreads - 1) / kEmitThreads,
+                                                                      (size_t)n_sm * 16));
+  k_cf_emit<<<emit_blocks, kEmitThreads, 0, s>>>(P); ++k;
   *err = cudaGetLastError();
   return *err == cudaSuccess ? k : -4;
 }
 
-size_t cf_workspace_bytes(int32_t n_instances, int32_t n_rows) {
-  return 8 * (size_t)n_instances * n_rows + 256;
+size_t cf_workspace_bytes(int64_t n_digits, int32_t n_instances, int32_t n_rows, int32_t capacity) {
+  const size_t n_rows_total = (size_t)n_instances * n_rows;
+  return cf_carve(nullptr, n_digits, n_rows_total, n_rows_total * ((kMaxTime + kTileT - 1) / kTileT), capacity,
+                  nullptr, nullptr);
 }
 
 }  // namespace tpct

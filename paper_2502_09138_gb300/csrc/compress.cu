@@ -13,10 +13,14 @@
 //   count, Y (first absolute, then differences), Z, charge;
 //   every value a LEB128 varint, signed values zigzag-mapped; tracks first,
 //   then the rows; byte offsets per track and per row.
-// GPU mapping: one thread per track or per row block; a length pass, a
-// device scan of the lengths, a write pass (encoding); a count pass, a scan,
-// a decode pass (decoding).  Integer arithmetic only, so the GPU and any
-// other decoder agree to the bit.
+// GPU mapping (encoding): one warp per track or row block, one lane per
+// cluster -- a cluster's residuals depend only on the quantised input, so no
+// lane waits for another; a length pass (which also sorts each block in the
+// warp), a device scan of the lengths, a write pass in which a warp scan of
+// the clusters' lengths places every lane's bytes (coalesced stores).
+// Decoding: one thread per track or block (the predictor chains every
+// cluster to the decoded previous ones); a count pass, a scan, a decode pass.
+// Integer arithmetic only, so the GPU and any other decoder agree to the bit.
 #include "tpct_internal.cuh"
 
 namespace tpct {
@@ -41,17 +45,59 @@ struct TmDev {
   uint8_t* used;                 // [n]
   int32_t *blk_count, *blk_base, *blk_cursor;   // [n_inst * n_rows + 1]
   int32_t* blk_ids;              // [n] clusters in no track, grouped by block
+  int32_t* blk_sorted;           // [n] the same, each block sorted by (Y, Z, charge)
   uint64_t* len;                 // [n_cap + n_blocks + 1] byte lengths, then their exclusive scan
   uint64_t* off;
   // output stream
   tpct_tm_stream out;
 };
 
-__device__ __forceinline__ int64_t qpos(float v) { return (int64_t)rint((double)v * 200.0); }
+// rint(200 v) of a float v, from its IEEE-754 fields with integer
+// arithmetic only (the FP64 pipe is 1/64 of the FP32 rate on this part):
+// v = m 2^(E-150) with a 24-bit m, so 200 v = 25 m 2^(E-147) exactly; a right
+// shift rounds half to even like rint.  Values beyond the int64 shift range
+// and non-finite ones take the double expression.
+__device__ __forceinline__ int64_t qpos(float v) {
+  const uint32_t bits = __float_as_uint(v);
+  const int E = (int)((bits >> 23) & 0xffu);
+  if (E == 0) return 0;                              // |200 v| < 0.5
+  const int sh = E - 147;
+  if (E == 255 || sh > 34) return (int64_t)rint((double)v * 200.0);
+  const uint64_t P = 25ull * ((bits & 0x7fffffu) | 0x800000u);
+  uint64_t q;
+  if (sh >= 0) {
+    q = P << sh;
+  } else {
+    const int s = -sh;
+    if (s >= 31) return 0;                           // P < 2^29: below one half
+    q = P >> s;
+    const uint64_t rem = P & ((1ull << s) - 1u), half = 1ull << (s - 1);
+    if (rem > half || (rem == half && (q & 1u))) ++q;
+  }
+  return (bits >> 31) ? -(int64_t)q : (int64_t)q;
+}
+
+// floor(a / b): a quotient estimate from a float division, then the exact
+// correction by the remainder (the estimate is within 2 of the quotient when
+// the quotient is below 2^20); other operands use the 64-bit division.
+__device__ __forceinline__ uint64_t udiv(uint64_t a, uint64_t b) {
+  if (a < (1ull << 62) && b < (1ull << 40)) {
+    const float qf = __fdiv_rn(__ull2float_rn(a), __ull2float_rn(b));
+    if (qf < 1048576.f) {
+      int64_t q = (int64_t)qf;
+      int64_t r = (int64_t)a - q * (int64_t)b;
+      for (int k = 0; k < 4 && r < 0; ++k) { --q; r += (int64_t)b; }
+      for (int k = 0; k < 4 && r >= (int64_t)b; ++k) { ++q; r -= (int64_t)b; }
+      if (r >= 0 && r < (int64_t)b) return (uint64_t)q;
+    }
+  }
+  return a / b;
+}
 
 __device__ __forceinline__ int64_t div_round(int64_t n, int64_t d) {
   if (d < 0) { n = -n; d = -d; }
-  return n >= 0 ? (2 * n + d) / (2 * d) : -((-2 * n + d) / (2 * d));
+  return n >= 0 ? (int64_t)udiv((uint64_t)(2 * n + d), (uint64_t)(2 * d))
+                : -(int64_t)udiv((uint64_t)(-2 * n + d), (uint64_t)(2 * d));
 }
 
 // value at x predicted from the previous k (1..3) points, oldest first
@@ -72,22 +118,6 @@ __device__ __forceinline__ int vlen(uint64_t v) {
   return n;
 }
 
-// Writes (or, with dst == nullptr, only counts) a varint.
-struct Sink {
-  uint8_t* dst;
-  int64_t pos;
-  __device__ void u(uint64_t v) {
-    if (!dst) { pos += vlen(v); return; }
-    do {
-      uint8_t b = (uint8_t)(v & 127u);
-      v >>= 7;
-      if (v) b |= 128u;
-      dst[pos++] = b;
-    } while (v);
-  }
-  __device__ void s(int64_t v) { u(zig(v)); }
-};
-
 struct Source {
   const uint8_t* p;
   int64_t pos;
@@ -106,47 +136,206 @@ struct Source {
 
 __device__ __forceinline__ int track_count(const TmDev& T) { return min(*T.n_tracks, T.n_cap); }
 
-// one track's block (history shifts in from the right: xs[2] is the latest)
-__device__ void code_track(const TmDev& T, int k, Sink& o) {
-  const int32_t* c = T.tr_ids + T.tr_off[k];
-  const int m = T.tr_ncl[k];
-  int64_t xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
-  o.u((uint64_t)m);
-  for (int j = 0; j < m; ++j) {
-    const int32_t i = c[j];
-    const int r = T.row[i];
-    const int64_t X = T.X[r], Y = qpos(T.y[i]), Z = qpos(T.z[i]);
-    if (j == 0) {
-      o.u((uint64_t)r); o.s(Y); o.s(Z);
-    } else {
-      const int kk = j < 3 ? j : 3;
-      o.u((uint64_t)(r - (int)T.row[c[j - 1]] - 1));
-      o.s(Y - predict(xs, ys, kk, X));
-      o.s(Z - predict(xs, zs, kk, X));
-    }
-    o.u(T.charge ? T.charge[i] : 0u);
-    xs[0] = xs[1]; xs[1] = xs[2]; xs[2] = X;
-    ys[0] = ys[1]; ys[1] = ys[2]; ys[2] = Y;
-    zs[0] = zs[1]; zs[1] = zs[2]; zs[2] = Z;
+// Writes a varint at dst + pos (pos advanced).
+__device__ __forceinline__ void put_u(uint8_t* dst, int64_t& pos, uint64_t v) {
+  do {
+    uint8_t b = (uint8_t)(v & 127u);
+    v >>= 7;
+    if (v) b |= 128u;
+    dst[pos++] = b;
+  } while (v);
+}
+
+// The values one cluster of a work item contributes to the stream.  Every
+// value depends only on the quantised input (the predictor uses the exact
+// quantised positions the decoder reproduces), so the clusters of an item
+// are coded independently, one per lane.
+struct CodedCluster {
+  uint64_t v0;              // rows skipped (first cluster of a track: its row); blocks: Y or Y step
+  int64_t s1, s2;           // tracks: Y and Z residuals (first: Y, Z); blocks: s2 = Z, s1 unused
+  uint32_t q;
+  bool block;
+  __device__ int length() const {
+    return block ? vlen(v0) + vlen(zig(s2)) + vlen(q) : vlen(v0) + vlen(zig(s1)) + vlen(zig(s2)) + vlen(q);
   }
+  __device__ void write(uint8_t* dst, int64_t pos) const {
+    if (block) {
+      put_u(dst, pos, v0);
+      put_u(dst, pos, zig(s2));
+      put_u(dst, pos, q);
+    } else {
+      put_u(dst, pos, v0);
+      put_u(dst, pos, zig(s1));
+      put_u(dst, pos, zig(s2));
+      put_u(dst, pos, q);
+    }
+  }
+};
+
+// cluster j of track k (j < its count)
+__device__ CodedCluster code_track_cluster(const TmDev& T, const int32_t* c, int j) {
+  CodedCluster o;
+  o.block = false;
+  const int32_t i = c[j];
+  const int r = T.row[i];
+  o.q = T.charge ? T.charge[i] : 0u;
+  const int64_t Y = qpos(T.y[i]), Z = qpos(T.z[i]);
+  if (j == 0) {
+    o.v0 = (uint64_t)r;
+    o.s1 = Y;
+    o.s2 = Z;
+    return o;
+  }
+  // the previous kk points, oldest first in slots 3 - kk .. 2
+  const int kk = j < 3 ? j : 3;
+  int64_t xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
+  int r_prev = 0;
+#pragma unroll
+  for (int d = 1; d <= 3; ++d) {
+    if (d > kk) break;
+    const int32_t ip = c[j - d];
+    const int rp = T.row[ip];
+    if (d == 1) r_prev = rp;
+    xs[3 - d] = T.X[rp];
+    ys[3 - d] = qpos(T.y[ip]);
+    zs[3 - d] = qpos(T.z[ip]);
+  }
+  const int64_t X = T.X[r];
+  o.v0 = (uint64_t)(r - r_prev - 1);
+  o.s1 = Y - predict(xs, ys, kk, X);
+  o.s2 = Z - predict(xs, zs, kk, X);
+  return o;
+}
+
+// cluster j of a sorted block
+__device__ CodedCluster code_block_cluster(const TmDev& T, const int32_t* ids, int j) {
+  CodedCluster o;
+  o.block = true;
+  o.s1 = 0;
+  const int32_t i = ids[j];
+  const int64_t Y = qpos(T.y[i]);
+  o.v0 = j == 0 ? zig(Y) : (uint64_t)(Y - qpos(T.y[ids[j - 1]]));
+  o.s2 = qpos(T.z[i]);
+  o.q = T.charge ? T.charge[i] : 0u;
+  return o;
 }
 
 __device__ __forceinline__ bool ucl_less(int64_t y1, int64_t z1, int q1, int64_t y2, int64_t z2, int q2) {
   return y1 < y2 || (y1 == y2 && (z1 < z2 || (z1 == z2 && q1 < q2)));
 }
 
-__device__ void code_block(const TmDev& T, int b, Sink& o) {
-  const int32_t* ids = T.blk_ids + T.blk_base[b];
-  const int m = T.blk_count[b];
-  o.u((uint64_t)m);
-  int64_t prev = 0;
-  for (int j = 0; j < m; ++j) {
-    const int32_t i = ids[j];
-    const int64_t Y = qpos(T.y[i]);
-    if (j == 0) o.s(Y); else o.u((uint64_t)(Y - prev));
-    o.s(qpos(T.z[i]));
-    o.u(T.charge ? T.charge[i] : 0u);
-    prev = Y;
+// Warp-wide: the clusters (ids) of a block sorted by (Y, Z, charge) into
+// `out`; every element's rank is counted against all others (ties: the
+// earlier position), so any order of equal keys gives the same bytes.
+__device__ void warp_sort_block(const TmDev& T, const int32_t* ids, int m, int32_t* out, int lane) {
+  for (int a = lane; a - lane < m; a += 32) {
+    const bool mine = a < m;
+    const int32_t ia = mine ? ids[a] : 0;
+    const int64_t ya = mine ? qpos(T.y[ia]) : 0, za = mine ? qpos(T.z[ia]) : 0;
+    const int qa = mine && T.charge ? T.charge[ia] : 0;
+    int rank = 0;
+    for (int c0 = 0; c0 < m; c0 += 32) {
+      const int cj = c0 + lane;
+      const bool has = cj < m;
+      const int32_t ic = has ? ids[cj] : 0;
+      const int64_t yc = has ? qpos(T.y[ic]) : 0, zc = has ? qpos(T.z[ic]) : 0;
+      const int qc = has && T.charge ? T.charge[ic] : 0;
+      const int lim = min(32, m - c0);
+      for (int t = 0; t < lim; ++t) {
+        const int64_t yo = __shfl_sync(0xffffffffu, yc, t), zo = __shfl_sync(0xffffffffu, zc, t);
+        const int qo = __shfl_sync(0xffffffffu, qc, t);
+        const int jo = c0 + t;
+        rank += (ucl_less(yo, zo, qo, ya, za, qa) || (yo == ya && zo == za && qo == qa && jo < a)) ? 1 : 0;
+      }
+    }
+    if (mine) out[rank] = ia;
+  }
+}
+
+// Byte length of work item w (tracks first, then blocks); blocks are sorted
+// into blk_sorted here.  One warp per item.
+__global__ void __launch_bounds__(kBlockT) k_tm_len(const __grid_constant__ TmDev T) {
+  const int lane = threadIdx.x & 31;
+  const int nt = track_count(T);
+  const int nw = T.n_cap + T.n_inst * T.n_rows;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += warps) {
+    uint64_t l = 0;
+    if (w < T.n_cap) {
+      if (w < nt) {
+        const int32_t* c = T.tr_ids + T.tr_off[w];
+        const int m = T.tr_ncl[w];
+        for (int j = lane; j < m; j += 32) l += (uint64_t)code_track_cluster(T, c, j).length();
+        if (lane == 0) l += (uint64_t)vlen((uint64_t)m);
+      }
+    } else {
+      const int b = w - T.n_cap;
+      const int m = T.blk_count[b];
+      int32_t* sorted = T.blk_sorted + T.blk_base[b];
+      warp_sort_block(T, T.blk_ids + T.blk_base[b], m, sorted, lane);
+      __syncwarp();
+      for (int j = lane; j < m; j += 32) l += (uint64_t)code_block_cluster(T, sorted, j).length();
+      if (lane == 0) l += (uint64_t)vlen((uint64_t)m);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if (lane == 0) T.len[w] = l;
+  }
+}
+
+// Writes every item at its offset: the count, then each lane's cluster at
+// the position a warp scan of the cluster lengths gives.
+__global__ void __launch_bounds__(kBlockT) k_tm_write(const __grid_constant__ TmDev T) {
+  const int lane = threadIdx.x & 31;
+  const int nt = track_count(T);
+  const int nb = T.n_inst * T.n_rows;
+  const int nw = T.n_cap + nb;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += warps) {
+    const int64_t at = (int64_t)T.off[w];
+    bool track = w < T.n_cap;
+    if (lane == 0) {
+      if (track && w <= nt && T.out.track_offsets) T.out.track_offsets[w] = at;
+      if (!track && T.out.row_offsets) T.out.row_offsets[w - T.n_cap] = at;
+    }
+    if (track && w >= nt) continue;
+    if (at + (int64_t)T.len[w] > T.out.capacity) continue;
+    int m;
+    const int32_t* ids;
+    if (track) {
+      m = T.tr_ncl[w];
+      ids = T.tr_ids + T.tr_off[w];
+    } else {
+      m = T.blk_count[w - T.n_cap];
+      ids = T.blk_sorted + T.blk_base[w - T.n_cap];
+    }
+    int64_t pos = at + vlen((uint64_t)m);
+    if (lane == 0) {
+      int64_t p0 = at;
+      put_u(T.out.data, p0, (uint64_t)m);
+    }
+    for (int j0 = 0; j0 < m; j0 += 32) {
+      const int j = j0 + lane;
+      CodedCluster cc;
+      int len = 0;
+      if (j < m) {
+        cc = track ? code_track_cluster(T, ids, j) : code_block_cluster(T, ids, j);
+        len = cc.length();
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (j < m) cc.write(T.out.data, pos + incl - len);
+      pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *T.out.n_bytes = (int64_t)T.off[nw];
+    if (nt == T.n_cap && T.out.track_offsets) T.out.track_offsets[nt] = (int64_t)T.off[T.n_cap];
+    if (T.out.row_offsets) T.out.row_offsets[nb] = (int64_t)T.off[nw];
   }
 }
 
@@ -184,68 +373,6 @@ __global__ void k_tm_fill(const __grid_constant__ TmDev T) {
   }
 }
 
-// sort every block's clusters by (Y, Z, charge) (insertion sort: blocks hold
-// a few dozen clusters), then its encoded length
-__global__ void k_tm_block_len(const __grid_constant__ TmDev T) {
-  const int nb = T.n_inst * T.n_rows;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-    int32_t* ids = T.blk_ids + T.blk_base[b];
-    const int m = T.blk_count[b];
-    for (int j = 1; j < m; ++j) {
-      const int32_t v = ids[j];
-      const int64_t yv = qpos(T.y[v]), zv = qpos(T.z[v]);
-      const int qv = T.charge ? T.charge[v] : 0;
-      int a = j - 1;
-      while (a >= 0) {
-        const int32_t w = ids[a];
-        if (!ucl_less(yv, zv, qv, qpos(T.y[w]), qpos(T.z[w]), T.charge ? T.charge[w] : 0)) break;
-        ids[a + 1] = w;
-        --a;
-      }
-      ids[a + 1] = v;
-    }
-    Sink o{nullptr, 0};
-    code_block(T, b, o);
-    T.len[T.n_cap + b] = (uint64_t)o.pos;
-  }
-}
-
-__global__ void k_tm_track_len(const __grid_constant__ TmDev T) {
-  const int nt = track_count(T);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < T.n_cap; k += gridDim.x * blockDim.x) {
-    uint64_t l = 0;
-    if (k < nt) {
-      Sink o{nullptr, 0};
-      code_track(T, k, o);
-      l = (uint64_t)o.pos;
-    }
-    T.len[k] = l;
-  }
-}
-
-__global__ void k_tm_write(const __grid_constant__ TmDev T) {
-  const int nt = track_count(T);
-  const int nb = T.n_inst * T.n_rows;
-  const int64_t total = (int64_t)T.off[T.n_cap + nb];
-  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < T.n_cap + nb; w += gridDim.x * blockDim.x) {
-    const int64_t at = (int64_t)T.off[w];
-    if (w < T.n_cap) {
-      if (w <= nt && T.out.track_offsets) T.out.track_offsets[w] = at;
-      if (w >= nt) continue;
-    } else {
-      if (T.out.row_offsets) T.out.row_offsets[w - T.n_cap] = at;
-    }
-    if (at + (int64_t)T.len[w] > T.out.capacity) continue;
-    Sink o{T.out.data, at};
-    if (w < T.n_cap) code_track(T, w, o); else code_block(T, w - T.n_cap, o);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *T.out.n_bytes = total;
-    if (nt == T.n_cap && T.out.track_offsets) T.out.track_offsets[nt] = (int64_t)T.off[T.n_cap];
-    if (T.out.row_offsets) T.out.row_offsets[nb] = total;
-  }
-}
-
 // ---------------------------------------------------------------- decoding
 struct TdDev {
   int n_rows;
@@ -266,11 +393,19 @@ __global__ void k_td_count(const __grid_constant__ TdDev D) {
   }
 }
 
+// (float)(V / 200.0): for |V| < 2^24 the float V is exact and one correctly
+// rounded float division gives the same float (V / 200 is a dyadic rational
+// or has a binary expansion of period 20, so no double-rounding case exists).
+__device__ __forceinline__ float grid_to_cm(int64_t V) {
+  if (V > -(1 << 24) && V < (1 << 24)) return __fdiv_rn((float)V, 200.f);
+  return (float)((double)V / 200.0);
+}
+
 __device__ __forceinline__ void put_cluster(const TdDev& D, int64_t o, int r, int64_t Y, int64_t Z, uint64_t q) {
   if (o >= D.out.capacity) return;
   D.out.x[o] = D.xf[r];
-  D.out.y[o] = (float)((double)Y / 200.0);
-  D.out.z[o] = (float)((double)Z / 200.0);
+  D.out.y[o] = grid_to_cm(Y);
+  D.out.z[o] = grid_to_cm(Z);
   D.out.charge[o] = (uint16_t)q;
   D.out.row[o] = (uint8_t)r;
 }
@@ -332,11 +467,13 @@ size_t tm_carve(char* base, int64_t n, int32_t cap, int32_t n_blocks, TmDev* T) 
   int32_t* bas = (int32_t*)take(4 * ((size_t)n_blocks + 1));
   int32_t* cur = (int32_t*)take(4 * ((size_t)n_blocks + 1));
   int32_t* ids = (int32_t*)take(4 * (size_t)std::max<int64_t>(n, 1));
+  int32_t* srt = (int32_t*)take(4 * (size_t)std::max<int64_t>(n, 1));
   uint64_t* len = (uint64_t*)take(8 * nw);
   uint64_t* off2 = (uint64_t*)take(8 * nw);
   uint64_t* tmp = (uint64_t*)take(8 * ((size_t)scan_tmp_elems((int64_t)nw) + 32));
   if (T) {
     T->used = used; T->blk_count = cnt; T->blk_base = bas; T->blk_cursor = cur; T->blk_ids = ids;
+    T->blk_sorted = srt;
     T->len = len; T->off = off2;
   }
   (void)tmp;
@@ -376,10 +513,9 @@ int enqueue_tm_encode(const double* row_x, int n_rows, const tpct_clusters& cl, 
   k_tm_count<<<blocks_for_t(n), kBlockT, 0, s>>>(T); ++k;
   launch_scan_i32(T.blk_count, T.blk_base, nb, tmp, s); k += 3;
   k_tm_fill<<<blocks_for_t(n), kBlockT, 0, s>>>(T); ++k;
-  k_tm_block_len<<<blocks_for_t(nb), kBlockT, 0, s>>>(T); ++k;
-  k_tm_track_len<<<blocks_for_t(cap), kBlockT, 0, s>>>(T); ++k;
+  k_tm_len<<<blocks_for_t(((int64_t)cap + nb) * 32), kBlockT, 0, s>>>(T); ++k;
   launch_scan_u64(T.len, T.off, (int64_t)cap + nb, tmp, s); k += 3;
-  k_tm_write<<<blocks_for_t((int64_t)cap + nb), kBlockT, 0, s>>>(T); ++k;
+  k_tm_write<<<blocks_for_t(((int64_t)cap + nb) * 32), kBlockT, 0, s>>>(T); ++k;
   return k;
 }
 

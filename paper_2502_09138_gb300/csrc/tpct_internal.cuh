@@ -209,7 +209,7 @@ void launch_refit_order(const Params& P, cudaStream_t s);
 int enqueue_clusters(const double* row_x, int n_rows, double tan_half, double z_max, const tpct_cf_params& prm,
                      const tpct_digits& dg, void* ws, size_t ws_bytes, const tpct_cf_out& out, cudaStream_t s,
                      cudaError_t* err);
-size_t cf_workspace_bytes(int32_t n_instances, int32_t n_rows);
+size_t cf_workspace_bytes(int64_t n_digits, int32_t n_instances, int32_t n_rows, int32_t capacity);
 size_t tm_encode_workspace_bytes(int64_t n, int32_t cap_tracks, int32_t n_blocks);
 size_t tm_decode_workspace_bytes(int32_t n_tracks, int32_t n_blocks);
 int enqueue_tm_encode(const double* row_x, int n_rows, const tpct_clusters& cl, int64_t n, const tpct_tracks_out& tr,

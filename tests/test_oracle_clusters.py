@@ -73,11 +73,6 @@ def sector_digits():
     return D.generate_digits(0)
 
 
-def _sorted_clusters(dg, res):
-    key = np.lexsort((dg.pad[res.peak], dg.time[res.peak], res.row, res.instance))
-    return {f: getattr(res, f)[key] for f in ("q_tot", "q_max", "pad", "time", "y", "z", "sigma_pad", "flags")}
-
-
 def test_input_order_inside_a_row(sector_digits):
     dg = sector_digits
     res = oracle.find_clusters(dg)
@@ -89,9 +84,11 @@ def test_input_order_inside_a_row(sector_digits):
     dg2 = D.Digits(pad=dg.pad[perm], time=dg.time[perm], adc=dg.adc[perm], row_offsets=dg.row_offsets,
                    sectors=dg.sectors, readout=dg.readout, n_pad=dg.n_pad, truth=dg.truth)
     res2 = oracle.find_clusters(dg2)
-    s1, s2 = _sorted_clusters(dg, res), _sorted_clusters(dg2, res2)
-    for f in s1:
-        assert np.array_equal(s1[f], s2[f]), f
+    # the output order is (instance, row, peak time, peak pad): independent of the input order
+    for f in ("q_tot", "q_max", "pad", "time", "y", "z", "sigma_pad", "flags", "row", "instance"):
+        assert np.array_equal(getattr(res, f), getattr(res2, f)), f
+    key = np.lexsort((dg.pad[res.peak], dg.time[res.peak], res.row, res.instance))
+    assert np.array_equal(key, np.arange(res.n))
 
 
 def test_isolated_crossings_against_truth(sector_digits):
