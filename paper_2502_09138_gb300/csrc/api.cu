@@ -81,9 +81,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   q.row_start = (int32_t*)take(4 * nr1);
   q.row_tl_count = (int32_t*)take(4 * nr1);
   q.row_tl_base = (int32_t*)take(4 * nr1);
-  q.row_ext = (uint32_t*)take(16 * nr1);
   q.grid = (RowGrid*)take(sizeof(RowGrid) * nr1);
-  q.c_bin = (int32_t*)take(4 * n);
   q.c_ir = (int32_t*)take(4 * n);
   q.bin_count = (int32_t*)take(4 * (pl.nbin + 1));
   q.bin_start = (int32_t*)take(4 * (pl.nbin + 1));
@@ -118,7 +116,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
     P->rdx = q.rdx; P->rdxf = q.rdxf; P->edge = q.edge; P->edgef = q.edgef;
     P->row_count = q.row_count; P->row_start = q.row_start;
     P->row_tl_count = q.row_tl_count; P->row_tl_base = q.row_tl_base;
-    P->row_ext = q.row_ext; P->grid = q.grid; P->c_bin = q.c_bin; P->c_ir = q.c_ir;
+    P->grid = q.grid; P->c_ir = q.c_ir;
     P->bin_count = q.bin_count; P->bin_start = q.bin_start;
     P->sy = q.sy; P->sz = q.sz; P->sid = q.sid; P->srow = q.srow;
     P->up = q.up; P->down = q.down; P->upc = q.upc; P->sflag = q.sflag; P->W = q.W;
@@ -240,14 +238,9 @@ int enqueue_track(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
   const int scan_k = 3;
   mark(0);
   k_set_tables_v<<<1, 256, 0, s>>>(P, tab); ++k;
-  launch_rows(P, s); k += 2;
-  launch_scan_i32(P.row_count, P.row_start, nr, P.scan_tmp, s); k += scan_k;
-  launch_grid_dims(P, s); ++k;
-  cudaMemsetAsync(P.bin_count, 0, sizeof(int32_t) * (size_t)(P.nbin_cap + 1), s);
-  launch_bin_count(P, s); ++k;
-  launch_scan_i32(P.bin_count, P.bin_start, P.nbin_cap, P.scan_tmp, s); k += scan_k;
-  cudaMemsetAsync(P.bin_count, 0, sizeof(int32_t) * (size_t)(P.nbin_cap + 1), s);
-  launch_scatter(P, s); ++k;
+  launch_init_rows(P, s); ++k;
+  cudaMemsetAsync(P.work, 0, sizeof(uint32_t) * 4, s);
+  launch_grid_build(P, s); ++k;
   mark(1);
   launch_neighbours(P, mode, s); ++k;
   mark(2);

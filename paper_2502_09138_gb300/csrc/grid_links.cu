@@ -8,6 +8,8 @@ namespace tpct {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kGridThreads = 512;
+constexpr int kGridSmemBins = 16384;           // bin counters of one instance held in shared memory
 
 
 // ------------------------------------------------------------------ step 1: rows and grids
@@ -16,23 +18,7 @@ __global__ void k_init_rows(const __grid_constant__ Params P) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nr; i += gridDim.x * blockDim.x) {
     P.row_count[i] = 0;
     P.row_tl_count[i] = 0;
-    if (i < nr) {
-      P.row_ext[4 * i + 0] = 0xffffffffu;
-      P.row_ext[4 * i + 1] = 0u;
-      P.row_ext[4 * i + 2] = 0xffffffffu;
-      P.row_ext[4 * i + 3] = 0u;
-    }
   }
-}
-
-// instance of input cluster c: the largest i with inst_off[i] <= c
-__device__ __forceinline__ int instance_of(const Params& P, int c) {
-  int lo = 0, hi = P.n_inst - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (P.inst_off[mid] <= (int64_t)c) lo = mid; else hi = mid - 1;
-  }
-  return lo;
 }
 
 // row whose x is nearest to xc (ties to the lower row)
@@ -47,78 +33,151 @@ __device__ __forceinline__ int nearest_row(const Params& P, float xc) {
   return lo;
 }
 
-__global__ void k_rows(const __grid_constant__ Params P) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P.n; c += gridDim.x * blockDim.x) {
-    int inst = instance_of(P, c);
-    int r = P.row ? (int)P.row[c] : nearest_row(P, P.x[c]);
-    if (r >= P.n_rows) {
-      atomicOr(P.status, kDevCapacity);
-      r = P.n_rows - 1;
+// The whole of step 1 for one instance per CTA (rows, extents, grid
+// dimensions, bin counts, bin starts, the sorted copy): an instance's
+// clusters fill the sorted positions [inst_off[i], inst_off[i+1]) and its
+// bins the entries [ib(i), ib(i+1)) of bin_start, ib(i) = inst_off[i] / k +
+// 2 n_rows i, so no step needs a device-wide scan and the counters live in
+// shared memory (an instance whose bins exceed it counts in global memory).
+// row_start and bin_start hold what device-wide exclusive scans of the row
+// and bin counts would give; the bin grid of a row holds about k clusters
+// per bin with bins roughly square in cm, and its bin_start entries start at
+// row_start / k + 2 ir, which leaves room for max(1, n / k) bins plus the
+// end entry.
+__global__ void __launch_bounds__(kGridThreads) k_grid_build(const __grid_constant__ Params P) {
+  extern __shared__ int g_bins[];               // [kGridSmemBins]
+  __shared__ int r_cnt[kMaxRows], r_start[kMaxRows + 1];
+  __shared__ uint32_t r_ext[4][kMaxRows];
+  __shared__ RowGrid r_grid[kMaxRows];
+  __shared__ int s_wsum[kGridThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int s_inst;
+  const int k = P.clusters_per_bin;
+  // instances from a work counter (their sizes differ by two orders of magnitude)
+  if (tid == 0) s_inst = (int)atomicAdd(&P.work[0], 1u);
+  __syncthreads();
+  for (int inst = s_inst; inst < P.n_inst; inst = s_inst) {
+    const int c0 = (int)P.inst_off[inst], c1 = (int)P.inst_off[inst + 1];
+    for (int r = tid; r < P.n_rows; r += kGridThreads) {
+      r_cnt[r] = 0;
+      r_ext[0][r] = 0xffffffffu; r_ext[1][r] = 0u; r_ext[2][r] = 0xffffffffu; r_ext[3][r] = 0u;
     }
-    int ir = inst * P.n_rows + r;
-    P.c_ir[c] = ir;
-    atomicAdd(&P.row_count[ir], 1);
-    uint32_t ky = float_order_key(P.y[c]), kz = float_order_key(P.z[c]);
-    atomicMin(&P.row_ext[4 * ir + 0], ky);
-    atomicMax(&P.row_ext[4 * ir + 1], ky);
-    atomicMin(&P.row_ext[4 * ir + 2], kz);
-    atomicMax(&P.row_ext[4 * ir + 3], kz);
-  }
-}
-
-// Grid of each row: about clusters_per_bin clusters per bin, bins roughly
-// square in cm.  Bin arrays of row ir start at row_start/k + 2 ir, which
-// leaves room for max(1, n/k) bins plus the end entry without a scan.
-__global__ void k_grid_dims(const __grid_constant__ Params P) {
-  int nr = P.n_inst * P.n_rows;
-  int k = P.clusters_per_bin;
-  for (int ir = blockIdx.x * blockDim.x + threadIdx.x; ir < nr; ir += gridDim.x * blockDim.x) {
-    int n = P.row_count[ir];
-    int start = P.row_start[ir];
-    int nb = max(1, n / k);
-    float ymin = 0.f, ymax = 0.f, zmin = 0.f, zmax = 0.f;
-    if (n > 0) {
-      ymin = float_from_order_key(P.row_ext[4 * ir + 0]);
-      ymax = float_from_order_key(P.row_ext[4 * ir + 1]);
-      zmin = float_from_order_key(P.row_ext[4 * ir + 2]);
-      zmax = float_from_order_key(P.row_ext[4 * ir + 3]);
+    __syncthreads();
+    // pass A: rows, counts, extents
+    for (int c = c0 + tid; c < c1; c += kGridThreads) {
+      int r = P.row ? (int)P.row[c] : nearest_row(P, P.x[c]);
+      if (r >= P.n_rows) {
+        atomicOr(P.status, kDevCapacity);
+        r = P.n_rows - 1;
+      }
+      P.c_ir[c] = inst * P.n_rows + r;
+      atomicAdd(&r_cnt[r], 1);
+      const uint32_t ky = float_order_key(P.y[c]), kz = float_order_key(P.z[c]);
+      atomicMin(&r_ext[0][r], ky); atomicMax(&r_ext[1][r], ky);
+      atomicMin(&r_ext[2][r], kz); atomicMax(&r_ext[3][r], kz);
     }
-    float ly = fmaxf(ymax - ymin, 1e-3f), lz = fmaxf(zmax - zmin, 1e-3f);
-    int ny = (int)rintf(sqrtf((float)nb * ly / lz));
-    ny = min(max(ny, 1), min(nb, 32767));
-    int nz = min(max(nb / ny, 1), 32767);
-    RowGrid g;
-    g.y0 = ymin;
-    g.z0 = zmin;
-    g.idy = (float)ny / ly;
-    g.idz = (float)nz / lz;
-    g.bin_base = start / k + 2 * ir;
-    g.ny = (int16_t)ny;
-    g.nz = (int16_t)nz;
-    P.grid[ir] = g;
-  }
-}
-
-__global__ void k_bin_count(const __grid_constant__ Params P) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P.n; c += gridDim.x * blockDim.x) {
-    int ir = P.c_ir[c];
-    RowGrid g = P.grid[ir];
-    int b = g.bin_base + bin_z(g, P.z[c]) * g.ny + bin_y(g, P.y[c]);
-    P.c_bin[c] = b;
-    atomicAdd(&P.bin_count[b], 1);
-  }
-}
-
-// bin_count is zero again here and serves as the fill cursor
-__global__ void k_scatter(const __grid_constant__ Params P) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P.n; c += gridDim.x * blockDim.x) {
-    int b = P.c_bin[c];
-    int pos = P.bin_start[b] + atomicAdd(&P.bin_count[b], 1);
-    P.sy[pos] = P.y[c];
-    P.sz[pos] = P.z[c];
-    P.sid[pos] = c;
-    P.srow[pos] = (uint8_t)(P.c_ir[c] % P.n_rows);
-    P.W[pos] = 0u;
+    __syncthreads();
+    if (warp == 0) {   // exclusive scan of the row counts
+      int run = 0;
+      for (int r0 = 0; r0 < P.n_rows; r0 += 32) {
+        const int r = r0 + lane;
+        const int v = r < P.n_rows ? r_cnt[r] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int x = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += x;
+        }
+        if (r < P.n_rows) r_start[r] = run + incl - v;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) r_start[P.n_rows] = run;
+    }
+    __syncthreads();
+    // grid dimensions of every row (the same arithmetic as k_grid_dims)
+    for (int r = tid; r < P.n_rows; r += kGridThreads) {
+      const int ir = inst * P.n_rows + r;
+      const int n = r_cnt[r];
+      const int start = c0 + r_start[r];
+      const int nb = max(1, n / k);
+      float ymin = 0.f, ymax = 0.f, zmin = 0.f, zmax = 0.f;
+      if (n > 0) {
+        ymin = float_from_order_key(r_ext[0][r]);
+        ymax = float_from_order_key(r_ext[1][r]);
+        zmin = float_from_order_key(r_ext[2][r]);
+        zmax = float_from_order_key(r_ext[3][r]);
+      }
+      const float ly = fmaxf(ymax - ymin, 1e-3f), lz = fmaxf(zmax - zmin, 1e-3f);
+      int ny = (int)rintf(sqrtf((float)nb * ly / lz));
+      ny = min(max(ny, 1), min(nb, 32767));
+      const int nz = min(max(nb / ny, 1), 32767);
+      RowGrid g;
+      g.y0 = ymin;
+      g.z0 = zmin;
+      g.idy = (float)ny / ly;
+      g.idz = (float)nz / lz;
+      g.bin_base = start / k + 2 * ir;
+      g.ny = (int16_t)ny;
+      g.nz = (int16_t)nz;
+      r_grid[r] = g;
+      P.grid[ir] = g;
+      P.row_count[ir] = n;
+      P.row_start[ir] = start;
+    }
+    if (tid == 0) {
+      P.row_start[(inst + 1) * P.n_rows] = c1;   // also the next instance's first row (same value)
+      if (inst == P.n_inst - 1) P.row_count[P.n_inst * P.n_rows] = 0;
+    }
+    // this instance's bin entries [ib0, ib1]
+    const int ib0 = c0 / k + 2 * inst * P.n_rows, ib1 = c1 / k + 2 * (inst + 1) * P.n_rows;
+    const int span = ib1 - ib0;
+    int* cnt = span <= kGridSmemBins ? g_bins : P.bin_count + ib0;
+    for (int b = tid; b < span; b += kGridThreads) cnt[b] = 0;
+    __syncthreads();
+    // pass B: bin counts
+    for (int c = c0 + tid; c < c1; c += kGridThreads) {
+      const RowGrid g = r_grid[P.c_ir[c] - inst * P.n_rows];
+      const int b = g.bin_base - ib0 + bin_z(g, P.z[c]) * g.ny + bin_y(g, P.y[c]);
+      atomicAdd(&cnt[b], 1);
+    }
+    __syncthreads();
+    // exclusive scan of the counts in place (a contiguous chunk per thread)
+    const int per = (span + kGridThreads - 1) / kGridThreads;
+    const int b_lo = min(tid * per, span), b_hi = min(b_lo + per, span);
+    int sum = 0;
+    for (int b = b_lo; b < b_hi; ++b) sum += cnt[b];
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += x;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    int run = incl - sum;
+    for (int q = 0; q < warp; ++q) run += s_wsum[q];
+    for (int b = b_lo; b < b_hi; ++b) {
+      const int v = cnt[b];
+      cnt[b] = run;
+      P.bin_start[ib0 + b] = c0 + run;
+      run += v;
+    }
+    if (tid == 0) P.bin_start[ib1] = c1;   // also the next instance's first entry (same value)
+    __syncthreads();
+    // pass C: the sorted copy (the order inside a bin is that of the atomics)
+    for (int c = c0 + tid; c < c1; c += kGridThreads) {
+      const int r = P.c_ir[c] - inst * P.n_rows;
+      const RowGrid g = r_grid[r];
+      const int b = g.bin_base - ib0 + bin_z(g, P.z[c]) * g.ny + bin_y(g, P.y[c]);
+      const int pos = c0 + atomicAdd(&cnt[b], 1);
+      P.sy[pos] = P.y[c];
+      P.sz[pos] = P.z[c];
+      P.sid[pos] = c;
+      P.srow[pos] = (uint8_t)r;
+      P.W[pos] = 0u;
+    }
+    if (tid == 0) s_inst = (int)atomicAdd(&P.work[0], 1u);
+    __syncthreads();
   }
 }
 
@@ -396,22 +455,21 @@ int blocks_for(int64_t work, int block) {
 
 int64_t scan_tmp_elems(int64_t m) { return (m + kScanChunk - 1) / kScanChunk + 1; }
 
-void launch_rows(const Params& P, cudaStream_t s) {
-  const int nr = P.n_inst * P.n_rows;
-  k_init_rows<<<blocks_for(nr + 1, kBlock), kBlock, 0, s>>>(P);
-  k_rows<<<blocks_for(P.n, kBlock), kBlock, 0, s>>>(P);
+void launch_init_rows(const Params& P, cudaStream_t s) {
+  k_init_rows<<<blocks_for(P.n_inst * P.n_rows + 1, kBlock), kBlock, 0, s>>>(P);
 }
 
-void launch_grid_dims(const Params& P, cudaStream_t s) {
-  k_grid_dims<<<blocks_for(P.n_inst * P.n_rows, kBlock), kBlock, 0, s>>>(P);
-}
-
-void launch_bin_count(const Params& P, cudaStream_t s) {
-  k_bin_count<<<blocks_for(P.n, kBlock), kBlock, 0, s>>>(P);
-}
-
-void launch_scatter(const Params& P, cudaStream_t s) {
-  k_scatter<<<blocks_for(P.n, kBlock), kBlock, 0, s>>>(P);
+void launch_grid_build(const Params& P, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_grid_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kGridSmemBins);
+    attr = true;
+  }
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(P.n_inst, n_sm * 2));
+  k_grid_build<<<grid, kGridThreads, 4 * kGridSmemBins, s>>>(P);
 }
 
 template <class Tin, class T>

@@ -64,9 +64,7 @@ struct Params {
   uint32_t* work;              // [2] work-queue heads of the tracklet and refit kernels
   int32_t* row_count;          // [n_inst*n_rows + 1]
   int32_t* row_start;          // [n_inst*n_rows + 1]
-  uint32_t* row_ext;           // [n_inst*n_rows*4] ordered-int min y, max y, min z, max z
   RowGrid* grid;               // [n_inst*n_rows]
-  int32_t* c_bin;              // [n] bin of each input cluster
   int32_t* c_ir;               // [n] row key of each input cluster
   int32_t* bin_count;          // [nbin_cap + 1]
   int32_t* bin_start;          // [nbin_cap + 1]
@@ -191,10 +189,8 @@ __device__ __forceinline__ int bin_z(const RowGrid& g, float z) {
 }
 
 // Launch wrappers (defined in the .cu files).
-void launch_rows(const Params& P, cudaStream_t s);
-void launch_grid_dims(const Params& P, cudaStream_t s);
-void launch_bin_count(const Params& P, cudaStream_t s);
-void launch_scatter(const Params& P, cudaStream_t s);
+void launch_grid_build(const Params& P, cudaStream_t s);
+void launch_init_rows(const Params& P, cudaStream_t s);
 void launch_scan_i32(const int32_t* in, int32_t* out, int64_t m, uint64_t* tmp, cudaStream_t s);
 void launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t m, uint64_t* tmp, cudaStream_t s);
 int64_t scan_tmp_elems(int64_t m);
