@@ -9,6 +9,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kGridThreads = 512;
+constexpr int kNbDown = 8;                     // down candidates of a hit listed in shared memory
 constexpr int kGridSmemBins = 16384;           // bin counters of one instance held in shared memory
 
 
@@ -294,8 +295,10 @@ __device__ __forceinline__ void bin_range(const RowGrid& g, float c, float w, in
 }
 
 template <int MODE>
-__global__ void k_neighbours(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(kBlock) k_neighbours(const __grid_constant__ Params P) {
   using E = typename Prec<MODE>::E;
+  __shared__ float dn_y[kNbDown][kBlock], dn_z[kNbDown][kBlock];
+  __shared__ int dn_i[kNbDown][kBlock];
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int nr = P.n_inst * P.n_rows;
@@ -321,32 +324,62 @@ __global__ void k_neighbours(const __grid_constant__ Params P) {
       bin_range<E>(gd, zh, (float)wzd, dz0, dz1, false);
       E best = (E)0;
       int bu = -1, bd = -1, idu = -1, idd = -1;
-      for (int iz = uz0; iz <= uz1; ++iz) {
-        const int q0 = P.bin_start[gu.bin_base + iz * gu.ny + uy0];
-        const int q1 = P.bin_start[gu.bin_base + iz * gu.ny + uy1 + 1];
-        for (int q = q0; q < q1; ++q) {
-          const E ayu = (E)P.sy[q] - (E)yh, azu = (E)P.sz[q] - (E)zh;
-          if (!(fabs(ayu) <= wyu && fabs(azu) <= wzu)) continue;
-          for (int jz = dz0; jz <= dz1; ++jz) {
-            const int s0 = P.bin_start[gd.bin_base + jz * gd.ny + dy0];
-            const int s1 = P.bin_start[gd.bin_base + jz * gd.ny + dy1 + 1];
-            for (int s = s0; s < s1; ++s) {
-              const E ayd = (E)P.sy[s] - (E)yh, azd = (E)P.sz[s] - (E)zh;
-              if (!(fabs(ayd) <= wyd && fabs(azd) <= wzd)) continue;
-              const E ry = ayd + f * (ayu - ayd);
-              const E rz = azd + f * (azu - azd);
-              const E D = ry * ry + rz * rz;
-              bool better;
-              if (bu < 0 || D < best) {
-                better = true;
-              } else if (D == best) {
-                if (idu < 0) { idu = P.sid[bu]; idd = P.sid[bd]; }
-                const int iu = P.sid[q], id = P.sid[s];
-                better = iu < idu || (iu == idu && id < idd);
-              } else {
-                better = false;
+      // the pair (u, d) minimising D, ties to the smaller (id_u, id_d): the
+      // minimum of a strict total order, so the visiting order is free
+      auto consider = [&](E ayu, E azu, int q, E ayd, E azd, int s) {
+        const E ry = ayd + f * (ayu - ayd);
+        const E rz = azd + f * (azu - azd);
+        const E D = ry * ry + rz * rz;
+        bool better;
+        if (bu < 0 || D < best) {
+          better = true;
+        } else if (D == best) {
+          if (idu < 0) { idu = P.sid[bu]; idd = P.sid[bd]; }
+          const int iu = P.sid[q], id = P.sid[s];
+          better = iu < idu || (iu == idu && id < idd);
+        } else {
+          better = false;
+        }
+        if (better) { best = D; bu = q; bd = s; idu = -1; idd = -1; }
+      };
+      // the down candidates inside the window, gathered once per hit (up to
+      // kNbDown of them; more take the nested loop)
+      int nd = 0;
+      for (int jz = dz0; jz <= dz1 && nd <= kNbDown; ++jz) {
+        const int s0 = P.bin_start[gd.bin_base + jz * gd.ny + dy0];
+        const int s1 = P.bin_start[gd.bin_base + jz * gd.ny + dy1 + 1];
+        for (int s = s0; s < s1; ++s) {
+          const E ayd = (E)P.sy[s] - (E)yh, azd = (E)P.sz[s] - (E)zh;
+          if (!(fabs(ayd) <= wyd && fabs(azd) <= wzd)) continue;
+          if (nd < kNbDown) {
+            dn_y[nd][threadIdx.x] = (float)ayd;
+            dn_z[nd][threadIdx.x] = (float)azd;
+            dn_i[nd][threadIdx.x] = s;
+          }
+          if (++nd > kNbDown) break;
+        }
+      }
+      const bool listed = nd <= kNbDown;
+      if (nd > 0) {
+        for (int iz = uz0; iz <= uz1; ++iz) {
+          const int q0 = P.bin_start[gu.bin_base + iz * gu.ny + uy0];
+          const int q1 = P.bin_start[gu.bin_base + iz * gu.ny + uy1 + 1];
+          for (int q = q0; q < q1; ++q) {
+            const E ayu = (E)P.sy[q] - (E)yh, azu = (E)P.sz[q] - (E)zh;
+            if (!(fabs(ayu) <= wyu && fabs(azu) <= wzu)) continue;
+            if (listed) {
+              for (int i = 0; i < nd; ++i)
+                consider(ayu, azu, q, (E)dn_y[i][threadIdx.x], (E)dn_z[i][threadIdx.x], dn_i[i][threadIdx.x]);
+            } else {
+              for (int jz = dz0; jz <= dz1; ++jz) {
+                const int s0 = P.bin_start[gd.bin_base + jz * gd.ny + dy0];
+                const int s1 = P.bin_start[gd.bin_base + jz * gd.ny + dy1 + 1];
+                for (int s = s0; s < s1; ++s) {
+                  const E ayd = (E)P.sy[s] - (E)yh, azd = (E)P.sz[s] - (E)zh;
+                  if (!(fabs(ayd) <= wyd && fabs(azd) <= wzd)) continue;
+                  consider(ayu, azu, q, ayd, azd, s);
+                }
               }
-              if (better) { best = D; bu = q; bd = s; idu = -1; idd = -1; }
             }
           }
         }
