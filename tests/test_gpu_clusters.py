@@ -121,3 +121,41 @@ def test_bad_digits_and_capacity_are_reported(G, sector_digits):
     bad.pad[0] = 250                                              # beyond every row's pads
     g = _run(G, bad)
     assert g["status"] & 1                                        # TPCT_CF_BAD_DIGIT
+
+
+def test_workspace_sized_for_fewer_digits_skips_rows(G, sector_digits):
+    """A workspace sized for fewer digits than the rows hold: the rows that end
+    beyond it are skipped and TPCT_CF_WORKSPACE is raised; the rows before
+    them give the oracle's clusters."""
+    import ctypes
+    import torch
+    import paper_2502_09138_gb300.binding as B
+    dg = sector_digits
+    o = oracle.find_clusters(dg)
+    trk = G.Tracker(precision="mixed")
+    dd = G.DeviceDigits.from_digits(dg)
+    out = G.ClusterOut(o.n + 1024, dg.n_instances, trk.device)
+    lib = B.load()
+    half = int(dg.row_offsets[dg.row_offsets.shape[0] // 2])          # digits of the first half of the rows
+    nb = int(lib.tpct_cf_workspace_bytes(half, dg.n_instances, trk.n_rows, out.capacity))
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=trk.device)
+    base = (ws.data_ptr() + 255) // 256 * 256
+    prm = G.default_cf_params()
+    ds, os_ = dd.as_struct(), out.as_struct()
+    B.check(lib.tpct_find_clusters(trk._h, ctypes.byref(ds), ctypes.byref(prm), ctypes.c_void_p(base), nb,
+                                   ctypes.byref(os_), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+            "tpct_find_clusters", trk._h)
+    torch.cuda.synchronize()
+    g = out.to_host()
+    assert g["status"] == B.TPCT_CF_WORKSPACE
+    # every row that ends within the requested digits is complete; rows that
+    # end beyond them by more than the 256-byte rounding of the area are absent
+    ends = dg.row_offsets[1:]
+    rows_ok = np.nonzero(ends <= half)[0]
+    rows_out = np.nonzero(ends > half + 64)[0]
+    ir_o = o.instance.astype(np.int64) * trk.n_rows + o.row
+    ir_g = np.repeat(np.arange(dg.n_instances), np.diff(g["inst_offsets"])) * trk.n_rows + g["row"].astype(np.int64)
+    keep, sel = np.isin(ir_o, rows_ok), np.isin(ir_g, rows_ok)
+    assert sel.sum() == keep.sum() > 0
+    assert np.array_equal(g["q_tot"][sel].astype(np.int64), o.q_tot[keep].astype(np.int64))
+    assert not np.isin(ir_g, rows_out).any()
