@@ -42,7 +42,9 @@ struct TmDev {
   // tracks
   const int32_t *n_tracks, *tr_off, *tr_ncl, *tr_ids;
   // workspace
-  uint8_t* used;                 // [n]
+  uint32_t* used;                // [n] number of tracks listing each cluster
+  uint4* code;                   // [n] a cluster's bytes, coded once by the length pass (<= 16)
+  uint8_t* clen;                 // [n] their count; 0: not staged (coded again by the write pass)
   int32_t *blk_count, *blk_base, *blk_cursor;   // [n_inst * n_rows + 1]
   int32_t* blk_ids;              // [n] clusters in no track, grouped by block
   int32_t* blk_sorted;           // [n] the same, each block sorted by (Y, Z, charge)
@@ -158,6 +160,25 @@ struct CodedCluster {
   __device__ int length() const {
     return block ? vlen(v0) + vlen(zig(s2)) + vlen(q) : vlen(v0) + vlen(zig(s1)) + vlen(zig(s2)) + vlen(q);
   }
+  // the bytes in a 16-byte word (only for length() <= 16)
+  __device__ uint4 pack() const {
+    uint64_t lo = 0, hi = 0;
+    int pos = 0;
+    auto put = [&](uint64_t v) {
+      do {
+        uint64_t b = v & 127u;
+        v >>= 7;
+        if (v) b |= 128u;
+        if (pos < 8) lo |= b << (8 * pos); else hi |= b << (8 * (pos - 8));
+        ++pos;
+      } while (v);
+    };
+    put(v0);
+    if (!block) put(zig(s1));
+    put(zig(s2));
+    put(q);
+    return make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+  }
   __device__ void write(uint8_t* dst, int64_t pos) const {
     if (block) {
       put_u(dst, pos, v0);
@@ -252,6 +273,15 @@ __device__ void warp_sort_block(const TmDev& T, const int32_t* ids, int m, int32
   }
 }
 
+// Keeps a cluster's bytes for the write pass when they fit 16 bytes and the
+// cluster is coded in one place only (a cluster listed by two tracks is
+// coded again by each).
+__device__ __forceinline__ void stage_code(const TmDev& T, int32_t i, const CodedCluster& cc, int len, bool unique) {
+  const bool keep = unique && len <= 16;
+  if (keep) T.code[i] = cc.pack();
+  T.clen[i] = keep ? (uint8_t)len : (uint8_t)0;
+}
+
 // Byte length of work item w (tracks first, then blocks); blocks are sorted
 // into blk_sorted here.  One warp per item.
 __global__ void __launch_bounds__(kBlockT) k_tm_len(const __grid_constant__ TmDev T) {
@@ -265,7 +295,12 @@ __global__ void __launch_bounds__(kBlockT) k_tm_len(const __grid_constant__ TmDe
       if (w < nt) {
         const int32_t* c = T.tr_ids + T.tr_off[w];
         const int m = T.tr_ncl[w];
-        for (int j = lane; j < m; j += 32) l += (uint64_t)code_track_cluster(T, c, j).length();
+        for (int j = lane; j < m; j += 32) {
+          const CodedCluster cc = code_track_cluster(T, c, j);
+          const int len = cc.length();
+          stage_code(T, c[j], cc, len, T.used[c[j]] == 1u);
+          l += (uint64_t)len;
+        }
         if (lane == 0) l += (uint64_t)vlen((uint64_t)m);
       }
     } else {
@@ -274,7 +309,12 @@ __global__ void __launch_bounds__(kBlockT) k_tm_len(const __grid_constant__ TmDe
       int32_t* sorted = T.blk_sorted + T.blk_base[b];
       warp_sort_block(T, T.blk_ids + T.blk_base[b], m, sorted, lane);
       __syncwarp();
-      for (int j = lane; j < m; j += 32) l += (uint64_t)code_block_cluster(T, sorted, j).length();
+      for (int j = lane; j < m; j += 32) {
+        const CodedCluster cc = code_block_cluster(T, sorted, j);
+        const int len = cc.length();
+        stage_code(T, sorted[j], cc, len, true);
+        l += (uint64_t)len;
+      }
       if (lane == 0) l += (uint64_t)vlen((uint64_t)m);
     }
 #pragma unroll
@@ -318,9 +358,18 @@ __global__ void __launch_bounds__(kBlockT) k_tm_write(const __grid_constant__ Tm
       const int j = j0 + lane;
       CodedCluster cc;
       int len = 0;
+      uint4 staged = make_uint4(0u, 0u, 0u, 0u);
+      bool have = false;
       if (j < m) {
-        cc = track ? code_track_cluster(T, ids, j) : code_block_cluster(T, ids, j);
-        len = cc.length();
+        const int32_t i = ids[j];
+        len = T.clen[i];
+        have = len > 0 && (!track || T.used[i] == 1u);
+        if (have) {
+          staged = T.code[i];
+        } else {
+          cc = track ? code_track_cluster(T, ids, j) : code_block_cluster(T, ids, j);
+          len = cc.length();
+        }
       }
       int incl = len;
 #pragma unroll
@@ -328,7 +377,16 @@ __global__ void __launch_bounds__(kBlockT) k_tm_write(const __grid_constant__ Tm
         const int v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
       }
-      if (j < m) cc.write(T.out.data, pos + incl - len);
+      if (j < m) {
+        if (have) {
+          const uint64_t lo = (uint64_t)staged.x | ((uint64_t)staged.y << 32);
+          const uint64_t hi = (uint64_t)staged.z | ((uint64_t)staged.w << 32);
+          uint8_t* dst = T.out.data + pos + incl - len;
+          for (int b = 0; b < len; ++b) dst[b] = (uint8_t)(b < 8 ? lo >> (8 * b) : hi >> (8 * (b - 8)));
+        } else {
+          cc.write(T.out.data, pos + incl - len);
+        }
+      }
       pos += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
@@ -343,7 +401,7 @@ __global__ void k_tm_mark(const __grid_constant__ TmDev T) {
   const int nt = track_count(T);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nt; k += gridDim.x * blockDim.x) {
     const int32_t* c = T.tr_ids + T.tr_off[k];
-    for (int j = 0; j < T.tr_ncl[k]; ++j) T.used[c[j]] = 1;
+    for (int j = 0; j < T.tr_ncl[k]; ++j) atomicAdd(&T.used[c[j]], 1u);
   }
 }
 
@@ -462,7 +520,9 @@ size_t tm_carve(char* base, int64_t n, int32_t cap, int32_t n_blocks, TmDev* T) 
   size_t off = 0;
   auto take = [&](size_t b) -> char* { char* p = base ? base + off : nullptr; off += (b + 255) / 256 * 256 + 256; return p; };
   const size_t nw = (size_t)cap + n_blocks + 1;
-  uint8_t* used = (uint8_t*)take((size_t)std::max<int64_t>(n, 1));
+  uint32_t* used = (uint32_t*)take(4 * (size_t)std::max<int64_t>(n, 1));
+  uint4* code = (uint4*)take(16 * (size_t)std::max<int64_t>(n, 1));
+  uint8_t* clen = (uint8_t*)take((size_t)std::max<int64_t>(n, 1));
   int32_t* cnt = (int32_t*)take(4 * ((size_t)n_blocks + 1));
   int32_t* bas = (int32_t*)take(4 * ((size_t)n_blocks + 1));
   int32_t* cur = (int32_t*)take(4 * ((size_t)n_blocks + 1));
@@ -472,7 +532,7 @@ size_t tm_carve(char* base, int64_t n, int32_t cap, int32_t n_blocks, TmDev* T) 
   uint64_t* off2 = (uint64_t*)take(8 * nw);
   uint64_t* tmp = (uint64_t*)take(8 * ((size_t)scan_tmp_elems((int64_t)nw) + 32));
   if (T) {
-    T->used = used; T->blk_count = cnt; T->blk_base = bas; T->blk_cursor = cur; T->blk_ids = ids;
+    T->used = used; T->code = code; T->clen = clen; T->blk_count = cnt; T->blk_base = bas; T->blk_cursor = cur; T->blk_ids = ids;
     T->blk_sorted = srt;
     T->len = len; T->off = off2;
   }
@@ -506,7 +566,7 @@ int enqueue_tm_encode(const double* row_x, int n_rows, const tpct_clusters& cl, 
   // the scan's block sums follow the offsets array in the workspace layout
   uint64_t* tmp = (uint64_t*)((char*)T.off + ((8 * ((size_t)cap + nb + 1) + 255) / 256 * 256 + 256));
   int k = 0;
-  cudaMemsetAsync(T.used, 0, (size_t)std::max<int64_t>(n, 1), s);
+  cudaMemsetAsync(T.used, 0, 4 * (size_t)std::max<int64_t>(n, 1), s);
   cudaMemsetAsync(T.blk_count, 0, 4 * ((size_t)nb + 1), s);
   cudaMemsetAsync(T.blk_cursor, 0, 4 * ((size_t)nb + 1), s);
   k_tm_mark<<<blocks_for_t(cap), kBlockT, 0, s>>>(T); ++k;
