@@ -228,6 +228,96 @@ __device__ CodedCluster code_track_cluster(const TmDev& T, const int32_t* c, int
   return o;
 }
 
+// Keeps a cluster's bytes for the write pass when they fit 16 bytes and the
+// cluster is coded in one place only (a cluster listed by two tracks is
+// coded again by each).
+__device__ __forceinline__ void stage_code(const TmDev& T, int32_t i, const CodedCluster& cc, int len, bool unique) {
+  const bool keep = unique && len <= 16;
+  if (keep) T.code[i] = cc.pack();
+  T.clen[i] = keep ? (uint8_t)len : (uint8_t)0;
+}
+
+// The same coding from values already at hand: this cluster's row, Y, Z, X
+// and charge, and the previous three clusters' rows, X, Y, Z (slot 2 the
+// latest; slots before the track's start unused).
+__device__ __forceinline__ CodedCluster code_track_values(int j, int r, int64_t X, int64_t Y, int64_t Z, uint32_t q,
+                                                          int r_prev, const int64_t* xs, const int64_t* ys,
+                                                          const int64_t* zs) {
+  CodedCluster o;
+  o.block = false;
+  o.q = q;
+  if (j == 0) {
+    o.v0 = (uint64_t)r;
+    o.s1 = Y;
+    o.s2 = Z;
+    return o;
+  }
+  const int kk = j < 3 ? j : 3;
+  o.v0 = (uint64_t)(r - r_prev - 1);
+  o.s1 = Y - predict(xs, ys, kk, X);
+  o.s2 = Z - predict(xs, zs, kk, X);
+  return o;
+}
+
+__device__ __forceinline__ int64_t shfl_up64(int64_t v, int d) {
+  const uint32_t lo = __shfl_up_sync(0xffffffffu, (uint32_t)(uint64_t)v, d);
+  const uint32_t hi = __shfl_up_sync(0xffffffffu, (uint32_t)((uint64_t)v >> 32), d);
+  return (int64_t)(((uint64_t)hi << 32) | lo);
+}
+__device__ __forceinline__ int64_t shfl_idx64(int64_t v, int src) {
+  const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)(uint64_t)v, src);
+  const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)((uint64_t)v >> 32), src);
+  return (int64_t)(((uint64_t)hi << 32) | lo);
+}
+
+// Byte length of track k, one lane per cluster; every cluster's inputs are
+// loaded and quantised once, and its three predecessors come from the
+// neighbouring lanes (or, at a chunk's start, from the previous chunk's last
+// three lanes).  Stages the bytes like the block path.
+__device__ uint64_t track_length_warp(const TmDev& T, const int32_t* c, int m, int lane) {
+  uint64_t l = 0;
+  int64_t cx[3] = {0, 0, 0}, cy[3] = {0, 0, 0}, cz[3] = {0, 0, 0};   // clusters j0-3 .. j0-1
+  int cr = 0;                                                        // row of cluster j0-1
+  for (int j0 = 0; j0 < m; j0 += 32) {
+    const int j = j0 + lane;
+    const bool valid = j < m;
+    const int32_t i = valid ? c[j] : 0;
+    const int r = valid ? (int)T.row[i] : 0;
+    const int64_t X = T.X[r];
+    const int64_t Y = valid ? qpos(T.y[i]) : 0, Z = valid ? qpos(T.z[i]) : 0;
+    const uint32_t q = valid && T.charge ? T.charge[i] : 0u;
+    int64_t xs[3], ys[3], zs[3];
+    int r_prev;
+#pragma unroll
+    for (int d = 1; d <= 3; ++d) {
+      const int64_t xu = shfl_up64(X, d), yu = shfl_up64(Y, d), zu = shfl_up64(Z, d);
+      const int k = 3 + lane - d;          // carry slot when lane < d
+      const bool from_carry = lane < d;
+      xs[3 - d] = from_carry ? (k == 2 ? cx[2] : k == 1 ? cx[1] : cx[0]) : xu;
+      ys[3 - d] = from_carry ? (k == 2 ? cy[2] : k == 1 ? cy[1] : cy[0]) : yu;
+      zs[3 - d] = from_carry ? (k == 2 ? cz[2] : k == 1 ? cz[1] : cz[0]) : zu;
+    }
+    {
+      const int ru = __shfl_up_sync(0xffffffffu, r, 1);
+      r_prev = lane == 0 ? cr : ru;
+    }
+    if (valid) {
+      const CodedCluster cc = code_track_values(j, r, X, Y, Z, q, r_prev, xs, ys, zs);
+      const int len = cc.length();
+      stage_code(T, i, cc, len, T.used[i] == 1u);
+      l += (uint64_t)len;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {        // the next chunk's predecessors (full chunks only continue)
+      cx[k] = shfl_idx64(X, 29 + k);
+      cy[k] = shfl_idx64(Y, 29 + k);
+      cz[k] = shfl_idx64(Z, 29 + k);
+    }
+    cr = __shfl_sync(0xffffffffu, r, 31);
+  }
+  return l;
+}
+
 // cluster j of a sorted block
 __device__ CodedCluster code_block_cluster(const TmDev& T, const int32_t* ids, int j) {
   CodedCluster o;
@@ -273,15 +363,6 @@ __device__ void warp_sort_block(const TmDev& T, const int32_t* ids, int m, int32
   }
 }
 
-// Keeps a cluster's bytes for the write pass when they fit 16 bytes and the
-// cluster is coded in one place only (a cluster listed by two tracks is
-// coded again by each).
-__device__ __forceinline__ void stage_code(const TmDev& T, int32_t i, const CodedCluster& cc, int len, bool unique) {
-  const bool keep = unique && len <= 16;
-  if (keep) T.code[i] = cc.pack();
-  T.clen[i] = keep ? (uint8_t)len : (uint8_t)0;
-}
-
 // Byte length of work item w (tracks first, then blocks); blocks are sorted
 // into blk_sorted here.  One warp per item.
 __global__ void __launch_bounds__(kBlockT) k_tm_len(const __grid_constant__ TmDev T) {
@@ -295,12 +376,7 @@ __global__ void __launch_bounds__(kBlockT) k_tm_len(const __grid_constant__ TmDe
       if (w < nt) {
         const int32_t* c = T.tr_ids + T.tr_off[w];
         const int m = T.tr_ncl[w];
-        for (int j = lane; j < m; j += 32) {
-          const CodedCluster cc = code_track_cluster(T, c, j);
-          const int len = cc.length();
-          stage_code(T, c[j], cc, len, T.used[c[j]] == 1u);
-          l += (uint64_t)len;
-        }
+        l = track_length_warp(T, c, m, lane);
         if (lane == 0) l += (uint64_t)vlen((uint64_t)m);
       }
     } else {
