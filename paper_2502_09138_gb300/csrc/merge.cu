@@ -39,6 +39,8 @@ struct MParams {
   int32_t* inst_of;           // [n_events * 36]
   int32_t *first, *last;      // [n_inst] track range of each instance
   double *alpha, *rref, *xout, *inx, *iny, *outx, *outy;   // [cap tracks]
+  float4* fq;                  // [cap tracks] float copies for the prefilter: tan lambda, outx, outy, inx
+  float* fiy;                  // [cap tracks] iny
   uint64_t *best_out_chi, *best_in_chi;                      // [cap tracks] order-preserving chi2 bits
   int32_t *best_out, *best_in;                               // [cap tracks]
   int32_t* n_cand;                                           // [1]
@@ -228,6 +230,8 @@ __global__ void k_m_prep(const __grid_constant__ MParams M) {
     M.inx[k] = xa * ca - ya * sa; M.iny[k] = xa * sa + ya * ca;
     M.outx[k] = xb * ca - yb * sa; M.outy[k] = xb * sa + yb * ca;
     M.xout[k] = xb;
+    M.fq[k] = make_float4((float)M.trk.param[(int64_t)k * 5 + 3], (float)M.outx[k], (float)M.outy[k], (float)M.inx[k]);
+    M.fiy[k] = (float)M.iny[k];
   }
 }
 
@@ -245,6 +249,10 @@ __global__ void k_m_cand(const __grid_constant__ MParams M) {
   const int a0 = M.first[ia], na = M.last[ia] - a0;
   const int b0 = M.first[ib], nb = M.last[ib] - b0;
   if (na <= 0 || nb <= 0) return;
+  if ((int64_t)na * nb > 0x7fffffffll) {   // beyond the 32-bit pair index: reported, boundary skipped
+    if (threadIdx.x == 0) atomicOr(M.status, kDevCapacity);
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const int64_t total = (int64_t)na * nb;
   // every thread runs the same number of rounds, so whole warps reach the ballot
@@ -253,8 +261,18 @@ __global__ void k_m_cand(const __grid_constant__ MParams M) {
     bool pass = false;
     int I = 0, O = 0;
     if (q < total) {
-      const int a = a0 + (int)(q / nb), bb = b0 + (int)(q % nb);
-      if (!M.trk.status[a] && !M.trk.status[bb]) {
+      const int qi = (int)q;                       // na * nb < 2^31 (checked on entry)
+      const int a = a0 + qi / nb, bb = b0 + qi % nb;
+      // float pre-test: rejects only pairs outside both cuts by far more than
+      // float rounding (either track inner); the rest take the FP64 test
+      const float4 fa = M.fq[a], fb = M.fq[bb];
+      const float fya = M.fiy[a], fyb = M.fiy[bb];
+      const float gab_x = fa.y - fb.w, gab_y = fa.z - fyb;   // a inner
+      const float gba_x = fb.y - fa.w, gba_y = fb.z - fya;   // b inner
+      const float gcut = (float)M.max_gap + 1e-3f;
+      const bool far = fabsf(fa.x - fb.x) > (float)M.max_dtanl * (1.f + 1e-5f) + 1e-6f ||
+                       (gab_x * gab_x + gab_y * gab_y > gcut * gcut && gba_x * gba_x + gba_y * gba_y > gcut * gcut);
+      if (!far && !M.trk.status[a] && !M.trk.status[bb]) {
         I = a; O = bb;
         if (M.rref[bb] < M.rref[a] || (M.rref[bb] == M.rref[a] && bb < a)) { I = bb; O = a; }
         const double dt = fabs(M.trk.param[(int64_t)I * 5 + 3] - M.trk.param[(int64_t)O * 5 + 3]);
@@ -618,6 +636,8 @@ size_t merge_carve(char* base, int cap_tracks, int n_inst, int n_events, int cap
   q.iny = (double*)take(8 * nt);
   q.outx = (double*)take(8 * nt);
   q.outy = (double*)take(8 * nt);
+  q.fq = (float4*)take(16 * nt);
+  q.fiy = (float*)take(4 * nt);
   q.best_out_chi = (uint64_t*)take(8 * nt);
   q.best_in_chi = (uint64_t*)take(8 * nt);
   q.best_out = (int32_t*)take(4 * nt);
@@ -645,6 +665,7 @@ size_t merge_carve(char* base, int cap_tracks, int n_inst, int n_events, int cap
   if (M) {
     M->status = q.status; M->rx = q.rx; M->inst_of = q.inst_of; M->first = q.first; M->last = q.last; M->alpha = q.alpha;
     M->rref = q.rref; M->xout = q.xout; M->inx = q.inx; M->iny = q.iny; M->outx = q.outx; M->outy = q.outy;
+    M->fq = q.fq; M->fiy = q.fiy;
     M->best_out_chi = q.best_out_chi; M->best_in_chi = q.best_in_chi; M->best_out = q.best_out;
     M->best_in = q.best_in; M->n_pairs = q.n_pairs; M->pair_i = q.pair_i; M->pair_o = q.pair_o;
     M->pair_chi = q.pair_chi; M->head_flag = q.head_flag; M->head_idx = q.head_idx; M->nseg = q.nseg;
