@@ -82,11 +82,18 @@ __device__ __forceinline__ int64_t qpos(float v) {
 // floor(a / b): a quotient estimate from a float division, then the exact
 // correction by the remainder (the estimate is within 2 of the quotient when
 // the quotient is below 2^20); other operands use the 64-bit division.
+// 64-bit integer <-> float conversions run on the FP64 pipe of this part, so
+// the operands are converted in 32-bit halves (the estimate only has to be
+// within a few units of the quotient).
+__device__ __forceinline__ float u64_to_float_approx(uint64_t v) {
+  return __fmaf_rn((float)(uint32_t)(v >> 32), 4294967296.f, (float)(uint32_t)v);
+}
+
 __device__ __forceinline__ uint64_t udiv(uint64_t a, uint64_t b) {
   if (a < (1ull << 62) && b < (1ull << 40)) {
-    const float qf = __fdiv_rn(__ull2float_rn(a), __ull2float_rn(b));
+    const float qf = __fdiv_rn(u64_to_float_approx(a), u64_to_float_approx(b));
     if (qf < 1048576.f) {
-      int64_t q = (int64_t)qf;
+      int64_t q = (int64_t)(int32_t)qf;
       int64_t r = (int64_t)a - q * (int64_t)b;
       for (int k = 0; k < 4 && r < 0; ++k) { --q; r += (int64_t)b; }
       for (int k = 0; k < 4 && r >= (int64_t)b; ++k) { ++q; r -= (int64_t)b; }
@@ -531,7 +538,7 @@ __global__ void k_td_count(const __grid_constant__ TdDev D) {
 // rounded float division gives the same float (V / 200 is a dyadic rational
 // or has a binary expansion of period 20, so no double-rounding case exists).
 __device__ __forceinline__ float grid_to_cm(int64_t V) {
-  if (V > -(1 << 24) && V < (1 << 24)) return __fdiv_rn((float)V, 200.f);
+  if (V > -(1 << 24) && V < (1 << 24)) return __fdiv_rn((float)(int32_t)V, 200.f);
   return (float)((double)V / 200.0);
 }
 
