@@ -188,7 +188,10 @@ __device__ __forceinline__ C kf_chi2(const C* m, C r0, C r1, C vy, C vz) {
   return (r0 * (s11 * r0 - s01 * r1) + r1 * (s00 * r1 - s01 * r0)) / (s00 * s11 - s01 * s01);
 }
 
-// Gain K = C H^T S^-1; p += K r; C -= K H C (lower triangle).
+// Gain K = C H^T S^-1; p += K r; C -= K H C (lower triangle).  Each entry
+// of C takes its two gain terms one after the other, which contracts into
+// two fused multiply-adds (instead of a product, a multiply-add and a
+// subtraction): 30 FP64 operations for the 15 entries.
 template <class C, class S>
 __device__ __forceinline__ void kf_update_inv(S* p, C* m, C r0, C r1, C s00, C s01, C s11, C idet) {
   const C i00 = s11 * idet, i01 = -s01 * idet, i11 = s00 * idet;
@@ -205,7 +208,7 @@ __device__ __forceinline__ void kf_update_inv(S* p, C* m, C r0, C r1, C s00, C s
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j, ++idx) m[idx] -= k0[i] * c0[j] + k1[i] * c1[j];
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] = (m[idx] - k0[i] * c0[j]) - k1[i] * c1[j];
 }
 
 template <class C, class S>
@@ -262,7 +265,7 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j, ++idx) m[idx] -= k0[i] * c0[j] + k1[i] * c1[j];
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] = (m[idx] - k0[i] * c0[j]) - k1[i] * c1[j];
   return true;
 }
 
@@ -298,7 +301,7 @@ __device__ __forceinline__ bool kf_test_update_mixed(double* p, double* m, doubl
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j, ++idx) m[idx] -= k0[i] * c0[j] + k1[i] * c1[j];
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] = (m[idx] - k0[i] * c0[j]) - k1[i] * c1[j];
   return true;
 }
 
