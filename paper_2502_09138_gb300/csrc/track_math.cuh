@@ -273,10 +273,11 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
 // chi2 decision in float (1e-6 relative at most, inside the 1e-5 near-cut
 // band) and the state increment K r in float (1e-7 of an increment far
 // smaller than the state); 1/det, the gain and the covariance update, whose
-// subtraction cancels, in double.  (A float reciprocal of det refined by one
+// subtraction cancels, in double.  (A float det's reciprocal refined by one
 // Newton step in double changed 4 of ~190 k tracklet lists of the
 // 128-collision batch: when S is large and its y-z correlation strong, the
-// float det loses digits and one step does not recover them.)
+// float det loses digits and one step does not recover them; the det here is
+// formed in double and its reciprocal refined twice.)
 __device__ __forceinline__ bool kf_test_update_mixed(double* p, double* m, double r0, double r1, float v,
                                                      float chi2_max) {
   const float f00 = narrow(m[0]) + v, f01 = narrow(m[1]), f11 = narrow(m[2]) + v;
@@ -286,7 +287,19 @@ __device__ __forceinline__ bool kf_test_update_mixed(double* p, double* m, doubl
   if (!(chi2 <= chi2_max)) return false;
   const double vd = widen(v);
   const double s00 = m[0] + vd, s01 = m[1], s11 = m[2] + vd;
-  const double idet = 1.0 / (s00 * s11 - s01 * s01);
+  // 1/det of the double det by Newton-Raphson for the reciprocal,
+  // x <- x + x (1 - det x), twice from a float seed (about 23 -> 46 -> 53
+  // bits; four fused multiply-adds), the float seed taken of the double det
+  const double det = s00 * s11 - s01 * s01;
+  const float fd = narrow(det);
+  double idet;
+  if (fabsf(fd) > 1e-30f && fabsf(fd) < 1e30f) {
+    idet = widen(__frcp_rn(fd));
+    idet = fma(idet, fma(-det, idet, 1.0), idet);
+    idet = fma(idet, fma(-det, idet, 1.0), idet);
+  } else {
+    idet = 1.0 / det;
+  }
   const double i00 = s11 * idet, i01 = -s01 * idet, i11 = s00 * idet;
   const double c0[5] = {m[0], m[1], m[3], m[6], m[10]};
   const double c1[5] = {m[1], m[2], m[4], m[7], m[11]};
