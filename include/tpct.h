@@ -336,9 +336,8 @@ void tpct_default_cf_params(tpct_cf_params* p);
 /* Digits (device, caller-owned, read-only): SoA, grouped by (instance, row),
  * any order inside a row, each (pad, time) cell at most once per row, ADC
  * values below 32768.  The kernel works on tiles of 128 time bins of a row:
- * at most 4096 digits of a row within 132 consecutive time bins (a tile and
- * two bins on each side) and at most 2048 clusters with their peak in one
- * tile (more: TPCT_CF_ROW_OVERFLOW, the rest ignored). */
+ * at most 2048 clusters with their peak in one tile (more:
+ * TPCT_CF_ROW_OVERFLOW, the rest ignored). */
 typedef struct {
   const uint16_t *pad, *time, *adc;   /* [row_offsets[last]]; may be NULL when there are no digits */
   const int64_t* row_offsets;  /* [n_instances * n_rows + 1] */
@@ -361,7 +360,7 @@ typedef struct {
 } tpct_cf_out;
 #define TPCT_CF_BAD_DIGIT 1u      /* a digit outside its row's pads or time bins, or ADC >= 32768 (skipped) */
 #define TPCT_CF_TIMEOUT 2u        /* (not raised: the kernels do not wait for one another) */
-#define TPCT_CF_ROW_OVERFLOW 4u   /* a tile of a row held more digits or clusters than the limits above */
+#define TPCT_CF_ROW_OVERFLOW 4u   /* a tile of a row held more clusters than the limit above */
 #define TPCT_CF_WORKSPACE 16u     /* the workspace was sized for fewer digits than the rows hold (rows skipped) */
 #define TPCT_CF_CAPACITY 8u       /* more clusters than capacity: *n_clusters is the size needed, the
                                      output arrays hold no defined result */
@@ -373,10 +372,12 @@ typedef struct {
 size_t tpct_cf_workspace_bytes(int64_t n_digits, int32_t n_instances, int32_t n_rows, int32_t capacity);
 
 /* Find the clusters of all rows of all instances; asynchronous on `stream`.
- * TPCT_E_INVALID for bad arguments or readout parameters whose largest row
- * map does not fit in one block's shared memory; TPCT_E_NOMEM if the
- * workspace (256-byte aligned) is smaller than tpct_cf_workspace_bytes.
- * Device conditions are reported in *out->status. */
+ * TPCT_E_INVALID for bad arguments or readout parameters that give a row more
+ * than 252 pads or more than 512 time bins; TPCT_E_NOMEM if the workspace
+ * (256-byte aligned) cannot hold even the per-item and staging areas (the
+ * rest holds the sorted digits: rows that end beyond it are skipped and
+ * raise TPCT_CF_WORKSPACE).  Device conditions are reported in
+ * *out->status. */
 tpct_status tpct_find_clusters(tpct_ctx* ctx, const tpct_digits* digits, const tpct_cf_params* params,
                                void* workspace, size_t workspace_bytes, tpct_cf_out* out, tpct_stream stream);
 
