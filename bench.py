@@ -508,6 +508,14 @@ def cpu_baseline_parallel(ev, idx, workers):
             "sample": f"the same {len(idx)} sector instances ({n} clusters) on {workers} processes, {dt:.1f} s"}
 
 
+METRIC = "TPC clusters/s tracked (batched, mixed FP32/FP64)"
+
+
+def workload_name(args):
+    return (f"{args.collisions} collisions, b uniform 0-15 fm, 36 sectors each"
+            if args.workload == "batch" else "one central Pb-Pb-like event, 9000 tracks")
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -530,11 +538,11 @@ def run_reference(args):
     n = sum(a for a, _ in per_step)
     t = sum(b for _, b in per_step)
     v = n / t
-    line = {"impl": "reference", "metric": "TPC clusters/s tracked", "value": v, "unit": "clusters/s",
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "clusters/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(per_step),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.collisions} collisions, b uniform 0-15 fm (36 sector instances "
-                                   "of it per step)", "collisions": args.collisions},
+            "config": {"workload": workload_name(args), "precision": "fp64 (the oracle)",
+                       "form": "single-threaded CPU oracle, a bounded sample of 36 sector instances per step"},
             "cpu_baseline": {"value": v, "unit": "clusters/s", "cores": 1, "kind": "oracle",
                              "sample": f"{len(per_step)} steps of 36 sector instances ({n} clusters)"},
             "e2e": {"value": v, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -652,13 +660,12 @@ def main():
                     "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6800.0), "traffic": None}
 
     line = {
-        "metric": "TPC clusters/s tracked (batched, mixed FP32/FP64)", "value": value, "unit": "clusters/s",
+        "metric": METRIC, "value": value, "unit": "clusters/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64", "mixed_df": "f32+df64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": (f"{args.collisions} collisions, b uniform 0-15 fm, 36 sectors each"
-                                if args.workload == "batch" else "one central Pb-Pb-like event, 9000 tracks"),
+        "config": {"workload": workload_name(args),
                    "clusters_per_rank": ev.n, "sector_instances": ev.n_instances, "precision": args.precision,
                    "form": "batched (graph-captured step chain)", "l2": "inputs 0.8 GB > L2, no flush",
                    "parallelism": f"replicas x{world} (independent collisions)"},
