@@ -1,6 +1,8 @@
 // Steps 1-4 of sector track finding: row binning into y/z grids, neighbour
 // finding by the straight-line criterion, reciprocal cleaning, start hits.
 // (The paper's "TPC Processing (Tracking)" row, Tables 1-3.)
+#include <mutex>
+
 #include "tpct_internal.cuh"
 
 namespace tpct {
@@ -493,11 +495,10 @@ void launch_init_rows(const Params& P, cudaStream_t s) {
 }
 
 void launch_grid_build(const Params& P, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;   // the serving runtime enqueues from several threads
+  std::call_once(attr, [] {
     cudaFuncSetAttribute(k_grid_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kGridSmemBins);
-    attr = true;
-  }
+  });
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
