@@ -73,3 +73,18 @@ def test_static_scratch_fits_one_sector(lib):
     # instance of 65536 clusters at 152 rows; the workspace plan must fit it
     import paper_2502_09138_gb300 as G
     assert G.Tracker(device="cpu").workspace_bytes(65536, 1) <= 20 << 20
+
+
+def test_auxiliary_workspace_sizes_without_gpu(lib):
+    """Host-only size queries of cluster finding and track-model coding: zero
+    for invalid arguments, growing with the digits / clusters and the output
+    capacity."""
+    cf = lib.tpct_cf_workspace_bytes
+    a = cf(1_000_000, 36, 152, 100_000)
+    assert a > 4 * 1_000_000 and cf(2_000_000, 36, 152, 100_000) > a and cf(1_000_000, 36, 152, 200_000) > a
+    assert cf(-1, 36, 152, 10) == 0 and cf(10, -1, 152, 10) == 0 and cf(10, 36, 0, 10) == 0 and cf(10, 36, 152, -1) == 0
+    assert cf(0, 0, 152, 0) > 0
+    tm = lib.tpct_tm_encode_workspace_bytes
+    b = tm(1_000_000, 20_000, 36, 152)
+    assert b > 16 * 1_000_000 and tm(2_000_000, 20_000, 36, 152) > b
+    assert tm(-1, 1, 1, 152) == 0 and tm(1, -1, 1, 152) == 0
