@@ -78,19 +78,6 @@ template <class E> __device__ __forceinline__ E rsqrt_of(E v) { return rsqrt(v);
 template <> __device__ __forceinline__ float rsqrt_of<float>(float v) { return rsqrtf(v); }
 __device__ __forceinline__ df64 rsqrt_of(df64 v) { return df64(1.0f) / sqrt(v); }
 
-// 1/v.  Double: Newton-Raphson for the reciprocal, x <- x + x (1 - v x),
-// twice from the float reciprocal of v (about 23 -> 46 -> 53 bits, four
-// FMAs; within an ulp or two of the IEEE quotient); v beyond the float range
-// takes the division.
-template <class E> __device__ __forceinline__ E recip(E v) { return (E)1 / v; }
-template <> __device__ __forceinline__ double recip<double>(double v) {
-  const float fv = narrow(v);
-  if (!(fabsf(fv) > 1e-30f && fabsf(fv) < 1e30f)) return 1.0 / v;
-  double x = widen(__frcp_rn(fv));
-  x = fma(x, fma(-v, x, 1.0), x);
-  return fma(x, fma(-v, x, 1.0), x);
-}
-
 template <class E>
 __device__ __forceinline__ bool helix_step(E s0, E tl, E qpt, E dx, E kb, E smax, Step<E>& st) {
   const E rho = -kb * qpt;
@@ -102,7 +89,7 @@ __device__ __forceinline__ bool helix_step(E s0, E tl, E qpt, E dx, E kb, E smax
   const E ir0 = rsqrt_of(u0), ir1 = rsqrt_of(u1);
   const E c0 = u0 * ir0, c1 = u1 * ir1;
   const E q0 = s0 * ir0, q1 = s1 * ir1;
-  const E ib = recip<E>(c0 + c1);
+  const E ib = (E)1 / (c0 + c1);
   const E slope = (s0 + s1) * ib;
   const E dy = dx * slope;
   const E l2 = dx * dx + dy * dy;
@@ -227,14 +214,14 @@ __device__ __forceinline__ void kf_update_inv(S* p, C* m, C r0, C r1, C s00, C s
 template <class C, class S>
 __device__ __forceinline__ void kf_update(S* p, C* m, C r0, C r1, C vy, C vz) {
   const C s00 = m[0] + vy, s01 = m[1], s11 = m[2] + vz;
-  kf_update_inv<C, S>(p, m, r0, r1, s00, s01, s11, recip<C>(s00 * s11 - s01 * s01));
+  kf_update_inv<C, S>(p, m, r0, r1, s00, s01, s11, (C)1 / (s00 * s11 - s01 * s01));
 }
 
 // Update that also returns the chi2 of the residual (one reciprocal).
 template <class C, class S>
 __device__ __forceinline__ C kf_chi2_update(S* p, C* m, C r0, C r1, C v) {
   const C s00 = m[0] + v, s01 = m[1], s11 = m[2] + v;
-  const C idet = recip<C>(s00 * s11 - s01 * s01);
+  const C idet = (C)1 / (s00 * s11 - s01 * s01);
   const C chi2 = (r0 * (s11 * r0 - s01 * r1) + r1 * (s00 * r1 - s01 * r0)) * idet;
   kf_update_inv<C, S>(p, m, r0, r1, s00, s01, s11, idet);
   return chi2;
@@ -244,7 +231,7 @@ __device__ __forceinline__ C kf_chi2_update(S* p, C* m, C r0, C r1, C v) {
 template <class C, class S>
 __device__ __forceinline__ bool kf_test_update(S* p, C* m, C r0, C r1, C v, C chi2_max) {
   const C s00 = m[0] + v, s01 = m[1], s11 = m[2] + v;
-  const C idet = recip<C>(s00 * s11 - s01 * s01);
+  const C idet = (C)1 / (s00 * s11 - s01 * s01);
   const C chi2 = (r0 * (s11 * r0 - s01 * r1) + r1 * (s00 * r1 - s01 * r0)) * idet;
   if (!(chi2 <= chi2_max)) return false;
   kf_update_inv<C, S>(p, m, r0, r1, s00, s01, s11, idet);
