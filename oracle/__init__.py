@@ -12,6 +12,10 @@ Parity status of each oracle function (what pins it, in tests/test_oracle_*):
   Kalman update     batch least squares on linear problems; noiseless helices
   neighbour finder  brute-force all-pairs search on small events; hand-built fixture
   clean/start/select brute-force set definitions on small events
+  tracklet growth   hand-worked fixture (tests/golden/tracklet_hand_fixture.json):
+                    miss counter at max_miss and max_miss + 1, a chi2-rejected
+                    link, the downward pass's rejected hits, the edge margin,
+                    the search tie-break; each planted mistake fails it
   whole tracker     generator truth (efficiency, fake rate, chi2/ndf, pulls);
                     the absolute efficiency level is parity unpinned (the paper
                     prints no tracking-efficiency number)
@@ -23,6 +27,7 @@ Parity status of each oracle function (what pins it, in tests/test_oracle_*):
                     centroid residuals, charge); translation and input-order
                     invariance
 """
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -35,6 +40,7 @@ _SRC_CF = os.path.join(_HERE, "cluster_oracle.c")
 _SRC_TM = os.path.join(_HERE, "compress_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libtpct_oracle.so")
 _lib = None
+_CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
 
 (ORC_UP, ORC_DOWN, ORC_UPC, ORC_DOWNC, ORC_NF_MARGIN, ORC_WEIGHT, ORC_TL_INST, ORC_TL_START,
  ORC_TL_NHITS, ORC_TL_STOP_UP, ORC_TL_STOP_DOWN, ORC_TL_ROWREF, ORC_TL_XREF, ORC_TL_MARGIN,
@@ -55,10 +61,24 @@ def build(force: bool = False) -> str:
             os.path.getmtime(_SRC), os.path.getmtime(_SRC_CF), os.path.getmtime(_SRC_TM),
             os.path.getmtime(os.path.join(_HERE, "tpct_oracle.h"))):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, _SRC_CF, _SRC_TM, "-lm"])
+        subprocess.check_call(["gcc"] + _CFLAGS + ["-o", tmp, _SRC, _SRC_CF, _SRC_TM, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def build_variant(tracker_source: str, workdir: str) -> str:
+    """Compile the oracle with ``tracker_source`` in place of tpct_oracle.c
+    (same flags, same other sources) into ``workdir``; returns the library
+    path.  Used by the tests that plant a mistake in a copy of the oracle."""
+    import shutil
+    os.makedirs(workdir, exist_ok=True)
+    shutil.copy(os.path.join(_HERE, "tpct_oracle.h"), workdir)
+    src = os.path.join(workdir, "tpct_oracle.c")
+    with open(src, "w") as f:
+        f.write(tracker_source)
+    out = os.path.join(workdir, "libtpct_oracle_variant.so")
+    subprocess.check_call(["gcc"] + _CFLAGS + ["-I", workdir, "-o", out, src, _SRC_CF, _SRC_TM, "-lm"])
+    return out
 
 
 class _Geom(ctypes.Structure):
@@ -78,39 +98,58 @@ class _Cuts(ctypes.Structure):
                 ("c_qpt_refit", ctypes.c_double)]
 
 
+def load_library(path):
+    """Load an oracle shared library from ``path`` and declare its signatures."""
+    L = ctypes.CDLL(path)
+    L.orc_track.restype = ctypes.c_void_p
+    L.orc_track.argtypes = [ctypes.POINTER(_Geom), ctypes.POINTER(_Cuts), ctypes.c_int64,
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_int]
+    L.orc_free.argtypes = [ctypes.c_void_p]
+    L.orc_count.restype = ctypes.c_int64
+    L.orc_count.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.orc_array.restype = ctypes.c_void_p
+    L.orc_array.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.orc_propagate.restype = ctypes.c_int
+    L.orc_propagate.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_void_p, ctypes.c_void_p]
+    L.orc_merge.restype = ctypes.c_void_p
+    L.orc_merge.argtypes = [ctypes.POINTER(_Geom), ctypes.POINTER(_Cuts), ctypes.POINTER(_MergeCuts),
+                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_void_p]
+    L.orm_free.argtypes = [ctypes.c_void_p]
+    L.orm_count.restype = ctypes.c_int64
+    L.orm_count.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.orm_array.restype = ctypes.c_void_p
+    L.orm_array.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.orc_rotate.restype = ctypes.c_int
+    L.orc_rotate.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.orc_kf_update.restype = ctypes.c_double
+    L.orc_kf_update.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
-        L.orc_track.restype = ctypes.c_void_p
-        L.orc_track.argtypes = [ctypes.POINTER(_Geom), ctypes.POINTER(_Cuts), ctypes.c_int64,
-                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                ctypes.c_void_p, ctypes.c_int]
-        L.orc_free.argtypes = [ctypes.c_void_p]
-        L.orc_count.restype = ctypes.c_int64
-        L.orc_count.argtypes = [ctypes.c_void_p, ctypes.c_int]
-        L.orc_array.restype = ctypes.c_void_p
-        L.orc_array.argtypes = [ctypes.c_void_p, ctypes.c_int]
-        L.orc_propagate.restype = ctypes.c_int
-        L.orc_propagate.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                    ctypes.c_void_p, ctypes.c_void_p]
-        L.orc_merge.restype = ctypes.c_void_p
-        L.orc_merge.argtypes = [ctypes.POINTER(_Geom), ctypes.POINTER(_Cuts), ctypes.POINTER(_MergeCuts),
-                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                ctypes.c_void_p, ctypes.c_void_p]
-        L.orm_free.argtypes = [ctypes.c_void_p]
-        L.orm_count.restype = ctypes.c_int64
-        L.orm_count.argtypes = [ctypes.c_void_p, ctypes.c_int]
-        L.orm_array.restype = ctypes.c_void_p
-        L.orm_array.argtypes = [ctypes.c_void_p, ctypes.c_int]
-        L.orc_rotate.restype = ctypes.c_int
-        L.orc_rotate.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-        L.orc_kf_update.restype = ctypes.c_double
-        L.orc_kf_update.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
-                                    ctypes.c_double, ctypes.c_double]
-        _lib = L
+        _lib = load_library(build())
     return _lib
+
+
+@contextlib.contextmanager
+def using_library(L):
+    """Route the oracle's Python functions through another build of it (the
+    tests load copies with a deliberately planted mistake to show that the
+    pins catch it)."""
+    global _lib
+    saved = lib()
+    _lib = L
+    try:
+        yield L
+    finally:
+        _lib = saved
 
 
 @dataclass
