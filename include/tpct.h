@@ -144,20 +144,34 @@ typedef struct {
 } tpct_debug_out;
 
 /* ---------------------------------------------------------------- context */
+/* Fills the stated readings of the method's constants (the values in
+ * brackets above).  Source: the paper names the tracking step (Tables 1-3)
+ * but fixes none of its constants; these are the readings every result of
+ * this library is defined by. */
 void tpct_default_cuts(tpct_cuts* cuts);
 
+/* Fills the TPC readout the workloads use: 152 pad rows (63 at 0.75 cm pitch
+ * from x = 85.2 cm, 64 at 1.0 cm from 135.1 cm, 25 at 1.5 cm from 199.4 cm),
+ * tan 10 deg sector acceptance, 250 cm drift.  row_x points to static storage
+ * of the library.  Source: the TPC whose processing Tables 1-3 time; the
+ * radii are a reading (the paper gives no geometry). */
+void tpct_default_geometry(tpct_geometry* geometry);
+
 /* Create a context for one geometry, field and cut set.  bz_tesla: field
- * along +z.  Returns TPCT_E_INVALID for a bad geometry or cut set. */
+ * along +z.  Returns TPCT_E_INVALID for a bad geometry or cut set.  Source:
+ * the sector tracking of "TPC Processing (Tracking)", Tables 1-3; the
+ * precision modes are this library's (the paper prints no arithmetic). */
 tpct_status tpct_create(const tpct_geometry* geometry, double bz_tesla, const tpct_cuts* cuts,
                         tpct_precision precision, tpct_ctx** out);
 void tpct_destroy(tpct_ctx* ctx);
 
 /* Tuning knobs that never change results (only speed): clusters per grid
  * bin (>= 1), threads per block of the tracklet and refit kernels (a
- * multiple of 32, at most 256).  0 = default. */
+ * multiple of 32, at most 256).  0 = default.  No counterpart in the paper
+ * (launch shapes of this GPU implementation). */
 tpct_status tpct_set_tuning(tpct_ctx* ctx, int clusters_per_bin, int tracklet_block, int refit_block);
 
-/* Launch shapes of a context. */
+/* Launch shapes of a context (no counterpart in the paper). */
 typedef struct {
   int clusters_per_bin, tracklet_block, refit_block;
   int precision, n_rows;          /* of the context (read-only here) */
@@ -173,31 +187,39 @@ tpct_status tpct_get_tuning(const tpct_ctx* ctx, tpct_tuning* out);
  * name, precision, rows and the size class (log2 clusters per instance, log2
  * instances).  A cached key is reused without timing.  Synchronises `stream`;
  * needs an attached workspace; overwrites `out`.  The shapes never change
- * results. */
+ * results.  No counterpart in the paper (this implementation's autotuner). */
 tpct_status tpct_autotune(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n, tpct_tracks_out* out,
                           tpct_stream stream, const char* cache_path, tpct_tuning* result);
 
 /* ---------------------------------------------------------------- workspace */
 /* Device bytes needed to track up to max_clusters clusters in up to
- * max_instances sector instances in one call. */
+ * max_instances sector instances in one call (this library's memory plan;
+ * no counterpart in the paper). */
 size_t tpct_workspace_bytes(const tpct_ctx* ctx, int64_t max_clusters, int32_t max_instances);
-/* Attach caller-owned device memory (256-byte aligned, >= the size above). */
+/* Attach caller-owned device memory (256-byte aligned, >= the size above).
+ * Touches no device memory: the context's status word in it is cleared in
+ * stream order by the next tracking call. */
 tpct_status tpct_set_workspace(tpct_ctx* ctx, void* device_ptr, size_t bytes,
                                int64_t max_clusters, int32_t max_instances);
 
 /* ---------------------------------------------------------------- tracking */
 /* Track n clusters (all instances of `clusters`) on `stream`: the plain
- * form, one launch per step. */
+ * form, one launch per step.  Source: steps 1-7 above, the sector tracking of
+ * "TPC Processing (Tracking)" (Tables 1-3), with the stated readings of
+ * tpct_cuts.  A cluster whose row[] is >= the geometry's n_rows is tracked on
+ * the last row and makes tpct_last_device_status return TPCT_E_INVALID. */
 tpct_status tpct_track(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n,
                        tpct_tracks_out* out, tpct_stream stream);
 
 /* Batched form: the same result as tpct_track on the same batch, run by
  * persistent kernels that pull work items from device queues, captured once
- * into a CUDA graph per (n, n_instances) and replayed. */
+ * into a CUDA graph per (n, n_instances) and replayed.  Source: the same
+ * steps; batching many collisions into one call is this implementation's
+ * (the paper's farm processes whole time frames per GPU, Section 1). */
 tpct_status tpct_track_batch(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n,
                              tpct_tracks_out* out, tpct_stream stream);
 
-/* Timing hooks: n_events = 7 CUDA events (cudaEvent_t) recorded on the
+/* Timing hooks (no counterpart in the paper): n_events = 7 CUDA events (cudaEvent_t) recorded on the
  * tracking stream at the step boundaries: before step 1, after the grid
  * (step 1), neighbours (2), cleaning and start hits (3-4), tracklets (5),
  * selection (6) and refit (7).  Inside the batched form's graph they are
@@ -223,19 +245,29 @@ tpct_status tpct_set_stage_events(tpct_ctx* ctx, void* const* events, int n_even
  * last call's contents: calls whose work overlaps on the GPU (other streams,
  * other threads, other contexts) race and corrupt each other -- serialise
  * them.  The device status of such a call is not kept: an output overflow
- * shows as *n_tracks > capacity_tracks or *n_ids > capacity_ids, and
- * tpct_last_device_status / tpct_debug_export do not describe it. */
+ * shows as *n_tracks > capacity_tracks or *n_ids > capacity_ids, a cluster
+ * whose row[] is >= n_rows is tracked on the last row without a warning, and
+ * tpct_last_device_status / tpct_debug_export do not describe the call.  The
+ * looked-up address is kept for the life of the process: do not call this
+ * entry point on a device after cudaDeviceReset on it. */
 tpct_status tpct_track_static(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n,
                               tpct_tracks_out* out, tpct_stream stream);
 
 /* Copy intermediate arrays of the last tpct_track / tpct_track_batch call on
- * this context (enqueued on `stream`). */
+ * this context (enqueued on `stream`): the links, start hits and tracklets of
+ * steps 2-6, for parity checks against a reference implementation. */
 tpct_status tpct_debug_export(tpct_ctx* ctx, tpct_debug_out* dbg, tpct_stream stream);
 
 /* Sticky device status of this context (synchronises the context's last
- * stream); TPCT_OK, TPCT_E_CAPACITY or TPCT_E_TIMEOUT.  Reading it clears it. */
+ * stream): TPCT_OK; TPCT_E_CAPACITY if an output or the tracklet plan
+ * overflowed; TPCT_E_INVALID if an input row was outside the geometry.
+ * Reading it clears it.  (No kernel waits for another, so no call on a
+ * context times out on the device; TPCT_E_TIMEOUT comes only from
+ * tpct_server_wait.)  Error reporting of this library (no counterpart in the
+ * paper). */
 tpct_status tpct_last_device_status(tpct_ctx* ctx);
 
+/* Text of a status code (static storage). */
 const char* tpct_status_str(tpct_status s);
 
 /* Text of the CUDA error behind the context's last TPCT_E_CUDA (host-owned, static). */
@@ -261,6 +293,8 @@ typedef struct {
   double max_gap;             /* [cm] (40) */
   double alpha0, dalpha;      /* sector k centred at alpha0 + (k mod 18) dalpha [rad] (10, 20 deg) */
 } tpct_merge_cuts;
+/* Fills the merging readings above (source: the tracking of Tables 1-3 spans
+ * the whole TPC; the paper fixes no merging constant). */
 void tpct_default_merge_cuts(tpct_merge_cuts* cuts);
 
 /* Merged chains (device, caller-owned), ordered by head (innermost) track.
@@ -288,10 +322,13 @@ typedef struct {
   int32_t* link_in;           /* [capacity of the input tracks] inner partner or -1 (may be NULL) */
 } tpct_chains_out;
 
-/* Device workspace of tpct_merge for up to max_tracks input tracks. */
+/* Device workspace of tpct_merge for up to max_tracks input tracks (this
+ * library's memory plan). */
 size_t tpct_merge_workspace_bytes(int32_t max_tracks, int32_t n_instances, int32_t n_events);
 
-/* Merge the output of tpct_track / tpct_track_batch (`tracks`, on the same
+/* Source: cross-sector merging, part of "TPC Processing (Tracking)",
+ * Tables 1-3, with the readings above.
+ * Merge the output of tpct_track / tpct_track_batch (`tracks`, on the same
  * `clusters`; tracks ordered by instance).  inst_sector, inst_event: device
  * [n_instances] sector number (0..35) and collision (0..n_events-1) of every
  * instance.  Asynchronous on `stream`; an overflow of `out` shows as
@@ -331,6 +368,8 @@ typedef struct {
   int32_t q_peak_min;          /* (7) */
   int32_t valley_delta;        /* (2) */
 } tpct_cf_params;
+/* Fills the cluster-finding readings above (source: clustering inside "TPC
+ * Processing", Table 1; the paper fixes no constant). */
 void tpct_default_cf_params(tpct_cf_params* p);
 
 /* Digits (device, caller-owned, read-only): SoA, grouped by (instance, row),
@@ -371,7 +410,9 @@ typedef struct {
  * they are put in order). */
 size_t tpct_cf_workspace_bytes(int64_t n_digits, int32_t n_instances, int32_t n_rows, int32_t capacity);
 
-/* Find the clusters of all rows of all instances; asynchronous on `stream`.
+/* Source: the clustering of "TPC Processing (Tracking, Clustering,
+ * Compression)", Table 1, with the readings above.
+ * Find the clusters of all rows of all instances; asynchronous on `stream`.
  * TPCT_E_INVALID for bad arguments or readout parameters that give a row more
  * than 252 pads or more than 512 time bins; TPCT_E_NOMEM if the workspace
  * (256-byte aligned) cannot hold even the per-item and staging areas (the
@@ -406,22 +447,43 @@ typedef struct {
 } tpct_tm_stream;
 typedef struct {
   int64_t capacity;            /* clusters */
-  int64_t* n;                  /* [1] clusters decoded, always written */
+  int64_t* n;                  /* [1] clusters in the stream, always written (may exceed capacity) */
   float *x, *y, *z;
   uint16_t* charge;
   uint8_t* row;
+  uint32_t* status;            /* [1] TPCT_TD_* bits of this call (cleared by the call) */
 } tpct_tm_decoded;
+enum {
+  TPCT_TD_BAD_STREAM = 1u,     /* an item's offsets leave the stream, a varint runs past its item or beyond 10
+                                  bytes, a count needs more bytes than its item holds, a row lies outside the
+                                  geometry or a charge above 65535: that item decodes no further, the output is
+                                  not a valid decoding */
+  TPCT_TD_CAPACITY = 2u        /* more clusters than out->capacity: only the first capacity are written */
+};
+/* Device workspace of tpct_tm_encode (this library's memory plan). */
 size_t tpct_tm_encode_workspace_bytes(int64_t n_clusters, int32_t capacity_tracks, int32_t n_instances, int32_t n_rows);
-/* Encode the clusters (device; row[] required) with the tracks of
+/* Source: the compression of "TPC Processing", Table 1, with the format
+ * readings above.
+ * Encode the clusters (device; row[] required) with the tracks of
  * tpct_track / tpct_track_batch on them (device; n_tracks read on the device).
  * TPCT_E_NOMEM if the workspace is too small. */
 tpct_status tpct_tm_encode(tpct_ctx* ctx, const tpct_clusters* clusters, int64_t n, const tpct_tracks_out* tracks,
                            void* workspace, size_t workspace_bytes, tpct_tm_stream* out, tpct_stream stream);
+/* Device workspace of tpct_tm_decode (this library's memory plan). */
 size_t tpct_tm_decode_workspace_bytes(int32_t n_tracks, int32_t n_instances, int32_t n_rows);
-/* Decode a stream (device data and offsets; counts on the host). */
-tpct_status tpct_tm_decode(tpct_ctx* ctx, const uint8_t* data, const int64_t* track_offsets, int32_t n_tracks,
-                           const int64_t* row_offsets, int32_t n_instances, void* workspace, size_t workspace_bytes,
-                           tpct_tm_decoded* out, tpct_stream stream);
+/* Source: GPU track-model decoding, Section 2 (1.2-3 % faster offline
+ * reconstruction), with the format readings above.
+ * Decode a stream (device data and offsets; n_bytes, n_tracks and n_instances
+ * on the host).  data holds n_bytes bytes; track_offsets[n_tracks + 1] and
+ * row_offsets[n_instances * n_rows + 1] delimit every item (the layout
+ * tpct_tm_encode writes).  The stream is not trusted: every read stays inside
+ * [0, n_bytes) and inside its item, and a malformed item sets
+ * TPCT_TD_BAD_STREAM in out->status instead (no read or write outside the
+ * buffers).  TPCT_E_INVALID on bad arguments, TPCT_E_NOMEM if the workspace
+ * is too small. */
+tpct_status tpct_tm_decode(tpct_ctx* ctx, const uint8_t* data, int64_t n_bytes, const int64_t* track_offsets,
+                           int32_t n_tracks, const int64_t* row_offsets, int32_t n_instances, void* workspace,
+                           size_t workspace_bytes, tpct_tm_decoded* out, tpct_stream stream);
 
 /* ---------------------------------------------------------------- publishing-rate control */
 /* Pacing of an offline source that feeds frames into a processing chain
@@ -450,15 +512,19 @@ typedef struct {
   double min_delay_s, max_delay_s;   /* (0, 10) */
 } tpct_pacer_config;
 typedef struct tpct_pacer tpct_pacer;
+/* Fills the defaults in brackets above (readings of Section 3). */
 void tpct_default_pacer_config(tpct_pacer_config* config);
-/* TPCT_E_INVALID for a bad configuration. */
+/* Source of the pacer calls: Section 3 (publishing-rate smoothing), with
+ * the reading above.  TPCT_E_INVALID for a bad configuration. */
 tpct_status tpct_pacer_create(const tpct_pacer_config* config, tpct_pacer** out);
+/* Frees the pacer (host memory). */
 void tpct_pacer_destroy(tpct_pacer* pacer);
 /* 1: publish now (recorded as published); 0: not now, *wait_s = the time
  * until the delay has passed (0 when waiting for a consumed frame). */
 int tpct_pacer_try_publish(tpct_pacer* pacer, double now_s, int32_t in_flight, int32_t backlog, double* wait_s);
 /* A frame left the chain; adapts the delay (SMOOTH). */
 void tpct_pacer_on_consumed(tpct_pacer* pacer, double now_s, int32_t in_flight, int32_t backlog);
+/* Current delay between publications [s] (SMOOTH). */
 double tpct_pacer_delay(const tpct_pacer* pacer);
 /* Number of times back pressure started. */
 int64_t tpct_pacer_pressure_events(const tpct_pacer* pacer);
@@ -515,6 +581,10 @@ typedef struct {
   uint64_t bytes_in_use, peak_bytes, budget_bytes;
 } tpct_server_stats;
 
+/* Source of the serving calls: continuous batching of time frames is this
+ * library's reading of serving; the paper's Section 3 supplies the idea of
+ * admitting work by the resources in flight.  TPCT_E_INVALID for bad
+ * arguments; the arena is the caller's and is never freed here. */
 tpct_status tpct_server_create(const tpct_geometry* geometry, double bz_tesla, const tpct_cuts* cuts,
                                tpct_precision precision, const tpct_server_config* config,
                                tpct_server** out);
@@ -523,6 +593,7 @@ tpct_status tpct_server_create(const tpct_geometry* geometry, double bz_tesla, c
 void tpct_server_destroy(tpct_server* server);
 /* Queue a frame; TPCT_E_BUDGET if it could never fit the arena. */
 tpct_status tpct_server_submit(tpct_server* server, const tpct_host_frame* frame, uint64_t* ticket);
+/* State of a frame (never blocks). */
 tpct_status tpct_server_poll(tpct_server* server, uint64_t ticket, tpct_frame_info* info);
 /* Blocks until the frame is done or failed (TPCT_E_TIMEOUT after timeout_s seconds). */
 tpct_status tpct_server_wait(tpct_server* server, uint64_t ticket, double timeout_s);
@@ -531,17 +602,11 @@ tpct_status tpct_server_wait(tpct_server* server, uint64_t ticket, double timeou
 tpct_status tpct_server_fetch(tpct_server* server, uint64_t ticket, tpct_host_tracks* out);
 /* Return a finished frame's outputs to the arena and forget the ticket. */
 tpct_status tpct_server_release(tpct_server* server, uint64_t ticket);
+/* Counters of the server since creation. */
 tpct_status tpct_server_get_stats(tpct_server* server, tpct_server_stats* out);
 
-/* ---------------------------------------------------------------- diagnostics */
-/* Launch count of this context's kernels so far (each kernel launch and each
- * graph kernel node replay counts one). */
-int64_t tpct_kernel_launches(const tpct_ctx* ctx);
-
-/* Throughput probe of the FP64 and FP32 FMA pipes: runs `blocks` x 256
- * threads of `iters` independent FMA chains on `stream`, writes nothing to
- * the caller; returns elapsed milliseconds via *ms (synchronises). */
-tpct_status tpct_probe_fma(int use_fp64, int blocks, int iters, tpct_stream stream, float* ms);
+/* Diagnostics (launch counts, pipe probes, a conversion check) are declared
+ * in tpct_diag.h. */
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,14 @@ def default_cuts(**over) -> B.Cuts:
     return c
 
 
+def default_geometry():
+    """(row_x, tan_half_sector, z_max) of the TPC readout built into the library
+    (152 pad rows, 20-degree sectors, 250 cm drift)."""
+    g = B.Geometry()
+    B.load().tpct_default_geometry(ctypes.byref(g))
+    return np.array(g.row_x[:g.n_rows], dtype=np.float64), float(g.tan_half_sector), float(g.z_max)
+
+
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
@@ -265,14 +273,11 @@ class Tracker:
 
     def __init__(self, row_x=None, tan_half_sector=None, z_max=250.0, bz=0.5, cuts=None,
                  precision="mixed", device="cuda"):
-        import math
         L = B.load()
-        if row_x is None:
-            from synth.geometry import row_radii   # the TPC's 152 rows
-            row_x = row_radii()
-        self.row_x = np.ascontiguousarray(row_x, dtype=np.float64)
+        d_rows, d_tan, _ = default_geometry()
+        self.row_x = np.ascontiguousarray(d_rows if row_x is None else row_x, dtype=np.float64)
         self.n_rows = int(self.row_x.shape[0])
-        tan_half_sector = math.tan(math.radians(10.0)) if tan_half_sector is None else tan_half_sector
+        tan_half_sector = d_tan if tan_half_sector is None else tan_half_sector
         g = B.Geometry(self.n_rows, self.row_x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                        float(tan_half_sector), float(z_max))
         self.cuts = cuts if cuts is not None else default_cuts()
@@ -420,8 +425,11 @@ class Tracker:
                                    ctypes.byref(ts), ctypes.c_void_p(s.cuda_stream)), "tpct_tm_encode", self._h)
         return st
 
-    def tm_decode(self, data, track_offsets, n_tracks, row_offsets, n_instances, capacity, stream=None):
-        """Decode a stream (device tensors): dict of x, y, z, charge, row tensors and n."""
+    def tm_decode(self, data, track_offsets, n_tracks, row_offsets, n_instances, capacity, stream=None,
+                  n_bytes=None):
+        """Decode a stream (device tensors): dict of x, y, z, charge, row tensors, n and
+        status (TD_BAD_STREAM, TD_CAPACITY bits).  n_bytes: the stream's size (default:
+        the whole data tensor)."""
         lib = B.load()
         nb = int(lib.tpct_tm_decode_workspace_bytes(int(n_tracks), int(n_instances), self.n_rows))
         base = self._scratch("_tdws", nb)
@@ -431,12 +439,14 @@ class Tracker:
              "y": torch.empty(c, dtype=torch.float32, device=self.device),
              "z": torch.empty(c, dtype=torch.float32, device=self.device),
              "charge": torch.empty(c, dtype=torch.int16, device=self.device),
-             "row": torch.empty(c, dtype=torch.uint8, device=self.device)}
+             "row": torch.empty(c, dtype=torch.uint8, device=self.device),
+             "status": torch.zeros(1, dtype=torch.int32, device=self.device)}
         ds = B.TmDecoded(int(capacity), _ptr(d["n"]), _ptr(d["x"]), _ptr(d["y"]), _ptr(d["z"]), _ptr(d["charge"]),
-                         _ptr(d["row"]))
+                         _ptr(d["row"]), _ptr(d["status"]))
+        n_bytes = int(data.numel() * data.element_size()) if n_bytes is None else int(n_bytes)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._keep_td = (data, track_offsets, row_offsets, d)
-        B.check(lib.tpct_tm_decode(self._h, _ptr(data), _ptr(track_offsets), int(n_tracks), _ptr(row_offsets),
+        B.check(lib.tpct_tm_decode(self._h, _ptr(data), n_bytes, _ptr(track_offsets), int(n_tracks), _ptr(row_offsets),
                                    int(n_instances), ctypes.c_void_p(base), nb, ctypes.byref(ds),
                                    ctypes.c_void_p(s.cuda_stream)), "tpct_tm_decode", self._h)
         return d
@@ -504,6 +514,20 @@ class Pacer:
             self._h = None
 
 
+def diag_convert(f_in=None, d_in=None, stream=None):
+    """Apply the library's float->double (widen) and double->float (narrow)
+    conversions to device tensors; returns (widened, narrowed)."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    d_out = torch.empty_like(f_in, dtype=torch.float64) if f_in is not None else None
+    f_out = torch.empty_like(d_in, dtype=torch.float32) if d_in is not None else None
+    n = int((f_in if f_in is not None else d_in).numel())
+    if f_in is not None and d_in is not None and f_in.numel() != d_in.numel():
+        raise ValueError("f_in and d_in must have the same length")
+    B.check(B.load().tpct_diag_convert(_ptr(f_in), _ptr(d_out), _ptr(d_in), _ptr(f_out), n,
+                                       ctypes.c_void_p(s.cuda_stream)), "tpct_diag_convert")
+    return d_out, f_out
+
+
 def probe_fma(use_fp64, blocks, iters, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     ms = ctypes.c_float()
@@ -519,13 +543,10 @@ class Server:
 
     def __init__(self, n_slots=3, budget_bytes=8 << 30, precision="mixed", bz=0.5, cuts=None, row_x=None,
                  tan_half_sector=None, z_max=250.0, device="cuda"):
-        import math
         L = B.load()
-        if row_x is None:
-            from synth.geometry import row_radii
-            row_x = row_radii()
-        self.row_x = np.ascontiguousarray(row_x, dtype=np.float64)
-        tan_half_sector = math.tan(math.radians(10.0)) if tan_half_sector is None else tan_half_sector
+        d_rows, d_tan, _ = default_geometry()
+        self.row_x = np.ascontiguousarray(d_rows if row_x is None else row_x, dtype=np.float64)
+        tan_half_sector = d_tan if tan_half_sector is None else tan_half_sector
         g = B.Geometry(int(self.row_x.shape[0]), self.row_x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                        float(tan_half_sector), float(z_max))
         self.cuts = cuts if cuts is not None else default_cuts()

@@ -81,6 +81,7 @@ class CfOut(ctypes.Structure):
 
 
 TPCT_CF_BAD_DIGIT, TPCT_CF_TIMEOUT, TPCT_CF_ROW_OVERFLOW, TPCT_CF_CAPACITY, TPCT_CF_WORKSPACE = 1, 2, 4, 8, 16
+TPCT_TD_BAD_STREAM, TPCT_TD_CAPACITY = 1, 2
 TPCT_PUBLISH_NAIVE, TPCT_PUBLISH_SMOOTH = 0, 1
 
 
@@ -91,7 +92,7 @@ class TmStream(ctypes.Structure):
 
 class TmDecoded(ctypes.Structure):
     _fields_ = [("capacity", c_int64), ("n", c_void_p), ("x", c_void_p), ("y", c_void_p), ("z", c_void_p),
-                ("charge", c_void_p), ("row", c_void_p)]
+                ("charge", c_void_p), ("row", c_void_p), ("status", c_void_p)]
 
 
 class PacerConfig(ctypes.Structure):
@@ -135,6 +136,7 @@ class Tuning(ctypes.Structure):
 
 EXPORTS = {
     "tpct_default_cuts": (None, [ctypes.POINTER(Cuts)]),
+    "tpct_default_geometry": (None, [ctypes.POINTER(Geometry)]),
     "tpct_create": (c_int, [ctypes.POINTER(Geometry), c_double, ctypes.POINTER(Cuts), c_int,
                             ctypes.POINTER(c_void_p)]),
     "tpct_destroy": (None, [c_void_p]),
@@ -163,8 +165,8 @@ EXPORTS = {
     "tpct_tm_encode": (c_int, [c_void_p, ctypes.POINTER(Clusters), c_int64, ctypes.POINTER(TracksOut), c_void_p,
                                c_size_t, ctypes.POINTER(TmStream), c_void_p]),
     "tpct_tm_decode_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
-    "tpct_tm_decode": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_size_t,
-                               ctypes.POINTER(TmDecoded), c_void_p]),
+    "tpct_tm_decode": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
+                               c_size_t, ctypes.POINTER(TmDecoded), c_void_p]),
     "tpct_pacer_create": (c_int, [ctypes.POINTER(PacerConfig), ctypes.POINTER(c_void_p)]),
     "tpct_pacer_destroy": (None, [c_void_p]),
     "tpct_pacer_try_publish": (c_int, [c_void_p, c_double, c_int32, c_int32, ctypes.POINTER(c_double)]),
@@ -186,6 +188,7 @@ EXPORTS = {
     "tpct_server_release": (c_int, [c_void_p, ctypes.c_uint64]),
     "tpct_server_get_stats": (c_int, [c_void_p, ctypes.POINTER(ServerStats)]),
     "tpct_probe_fma": (c_int, [c_int, c_int, c_int, c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "tpct_diag_convert": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
 }
 
 _lib = None

@@ -1,9 +1,11 @@
 // C ABI of the sector tracker: context, workspace layout, launch sequences.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
 #include "tpct_internal.cuh"
+#include "tpct_diag.h"
 
 using namespace tpct;
 
@@ -20,6 +22,7 @@ struct tpct_ctx {
   size_t ws_bytes = 0;
   int64_t plan_n = 0;
   int32_t plan_inst = 0;
+  bool clear_status = false;  // the status word of a newly attached workspace is cleared by the next call
   Params last{};              // parameters of the last call (for debug export)
   bool have_last = false;
   cudaStream_t last_stream = nullptr;
@@ -169,12 +172,9 @@ bool valid_cuts(const tpct_cuts& c) {
 
 tpct_status check_cuda(cudaError_t e) { return e == cudaSuccess ? TPCT_OK : TPCT_E_CUDA; }
 
-// Build the per-call parameters; validates sizes.
-tpct_status make_params(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const tpct_tracks_out* out,
-                        Params* P) {
-  if (!ctx || !cl || !out || n < 0) return TPCT_E_INVALID;
-  if (!ctx->ws) return TPCT_E_STATE;
-  if (n > ctx->plan_n || cl->n_instances > ctx->plan_inst || cl->n_instances < 1) return TPCT_E_NOMEM;
+// Validates a call's clusters and outputs (the checks every tracking entry point makes).
+tpct_status check_call(const tpct_clusters* cl, int64_t n, const tpct_tracks_out* out) {
+  if (!cl || !out || n < 0) return TPCT_E_INVALID;
   if (n > 0 && (!cl->y || !cl->z || (!cl->row && !cl->x))) return TPCT_E_INVALID;
   if (!cl->sector_offsets) return TPCT_E_INVALID;
   if (!out->n_tracks || !out->n_ids || out->capacity_tracks < 0 || out->capacity_ids < 0) return TPCT_E_INVALID;
@@ -182,18 +182,29 @@ tpct_status make_params(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const
                                    !out->status || !out->x_ref || !out->param || !out->cov || !out->chi2))
     return TPCT_E_INVALID;
   if (out->capacity_ids > 0 && !out->cluster_ids) return TPCT_E_INVALID;
-  if (ctx->tl_blocks == 0 || ctx->rf_blocks == 0) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return fail_cuda(ctx, e);
-    ctx->tl_blocks = ctx->n_sm * tracklet_blocks_per_sm((int)ctx->prec, ctx->tracklet_block);
-    ctx->rf_blocks = ctx->n_sm * refit_blocks_per_sm((int)ctx->prec, ctx->refit_block);
-  }
+  return TPCT_OK;
+}
+
+// Persistent grid sizes of the context (queried on its first call).
+tpct_status ensure_grids(tpct_ctx* ctx) {
+  if (ctx->tl_blocks != 0 && ctx->rf_blocks != 0) return TPCT_OK;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return fail_cuda(ctx, e);
+  ctx->tl_blocks = ctx->n_sm * tracklet_blocks_per_sm((int)ctx->prec, ctx->tracklet_block);
+  ctx->rf_blocks = ctx->n_sm * refit_blocks_per_sm((int)ctx->prec, ctx->refit_block);
+  return TPCT_OK;
+}
+
+// The per-call parameters: the workspace `base` carved for `plan_ws`, the
+// constants of the context's cut set and geometry, the call's sizes and
+// buffers.  The one place every tracking entry point fills them.
+void fill_params(const tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const tpct_tracks_out* out, char* base,
+                 const Plan& plan_ws, Params* P) {
   Params p{};
-  Plan pl = make_plan(ctx->n_rows, n, cl->n_instances, ctx->clusters_per_bin);
-  Plan plan_ws = make_plan(ctx->n_rows, ctx->plan_n, ctx->plan_inst, 1);
-  carve(ctx->ws, plan_ws, ctx->n_rows, &p);
+  const Plan pl = make_plan(ctx->n_rows, n, cl->n_instances, ctx->clusters_per_bin);
+  carve(base, plan_ws, ctx->n_rows, &p);
   p.n_rows = ctx->n_rows;
   p.n_inst = cl->n_instances;
   p.n = (int32_t)n;
@@ -220,6 +231,29 @@ tpct_status make_params(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const
   p.x = cl->x; p.y = cl->y; p.z = cl->z; p.row = cl->row; p.inst_off = cl->sector_offsets;
   p.out = *out;
   *P = p;
+}
+
+// Build the per-call parameters of a call on the attached workspace; validates sizes.
+tpct_status make_params(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const tpct_tracks_out* out,
+                        Params* P) {
+  if (!ctx || !cl || !out || n < 0) return TPCT_E_INVALID;
+  if (!ctx->ws) return TPCT_E_STATE;
+  tpct_status st = check_call(cl, n, out);
+  if (st != TPCT_OK) return st;
+  if (n > ctx->plan_n || cl->n_instances > ctx->plan_inst || cl->n_instances < 1) return TPCT_E_NOMEM;
+  st = ensure_grids(ctx);
+  if (st != TPCT_OK) return st;
+  fill_params(ctx, cl, n, out, ctx->ws, make_plan(ctx->n_rows, ctx->plan_n, ctx->plan_inst, 1), P);
+  return TPCT_OK;
+}
+
+// Clears the status word of a newly attached workspace in the order of the
+// call's stream (tpct_set_workspace itself touches no device memory).
+tpct_status clear_status_if_new(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
+  if (!ctx->clear_status) return TPCT_OK;
+  const cudaError_t e = cudaMemsetAsync(P.status, 0, sizeof(uint32_t) * 4, s);
+  if (e != cudaSuccess) return fail_cuda(ctx, e);
+  ctx->clear_status = false;
   return TPCT_OK;
 }
 
@@ -272,6 +306,24 @@ int enqueue_track(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
 }  // namespace
 
 extern "C" {
+
+// The TPC readout of the workload: 152 pad rows in three regions (63 rows at
+// 0.75 cm pitch from x = 85.2 cm, 64 at 1.0 cm from 135.1 cm, 25 at 1.5 cm
+// from 199.4 cm), 20-degree sectors (acceptance |y| <= x tan 10 deg), 250 cm
+// of drift.  The radii live in static storage of the library.
+void tpct_default_geometry(tpct_geometry* g) {
+  if (!g) return;
+  static const std::vector<double> rows = [] {
+    std::vector<double> r(152);
+    for (int i = 0; i < 152; ++i)
+      r[i] = i < 63 ? 85.2 + 0.75 * i : i < 127 ? 135.1 + 1.0 * (i - 63) : 199.4 + 1.5 * (i - 127);
+    return r;
+  }();
+  g->n_rows = 152;
+  g->row_x = rows.data();
+  g->tan_half_sector = 0.17632698070846498;   // tan(10 deg)
+  g->z_max = 250.0;
+}
 
 void tpct_default_cuts(tpct_cuts* c) {
   if (!c) return;
@@ -336,10 +388,8 @@ tpct_status tpct_set_workspace(tpct_ctx* ctx, void* ptr, size_t bytes, int64_t m
   ctx->plan_n = max_clusters;
   ctx->plan_inst = max_instances;
   ctx->have_last = false;
+  ctx->clear_status = true;
   drop_graph(ctx);
-  Params p{};
-  carve(ctx->ws, make_plan(ctx->n_rows, max_clusters, max_instances, 1), ctx->n_rows, &p);
-  if (cudaMemset(p.status, 0, sizeof(uint32_t) * 4) != cudaSuccess) return TPCT_E_CUDA;
   return TPCT_OK;
 }
 
@@ -349,6 +399,8 @@ tpct_status tpct_track(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, tpct_t
   tpct_status st = make_params(ctx, cl, n, out, &P);
   if (st != TPCT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  st = clear_status_if_new(ctx, P, s);
+  if (st != TPCT_OK) return st;
   ctx->launches += enqueue_track(ctx, P, s);
   ctx->last = P;
   ctx->have_last = true;
@@ -362,6 +414,8 @@ tpct_status tpct_track_batch(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, 
   tpct_status st = make_params(ctx, cl, n, out, &P);
   if (st != TPCT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  st = clear_status_if_new(ctx, P, s);
+  if (st != TPCT_OK) return st;
   if (!ctx->gexec || ctx->gstage_on != ctx->stage_on || std::memcmp(&ctx->gparams, &P, sizeof(Params)) != 0) {
     drop_graph(ctx);
     cudaStream_t cap;
@@ -437,14 +491,15 @@ tpct_status tpct_debug_export(tpct_ctx* ctx, tpct_debug_out* dbg, tpct_stream st
 
 tpct_status tpct_last_device_status(tpct_ctx* ctx) {
   if (!ctx || !ctx->ws) return TPCT_E_STATE;
+  if (ctx->clear_status) return TPCT_OK;   // no call since the workspace was attached
   if (ctx->have_last && cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) return TPCT_E_CUDA;
   Params p{};
   carve(ctx->ws, make_plan(ctx->n_rows, ctx->plan_n, ctx->plan_inst, 1), ctx->n_rows, &p);
   uint32_t h = 0;
   if (cudaMemcpy(&h, p.status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return TPCT_E_CUDA;
   if (cudaMemset(p.status, 0, sizeof(uint32_t)) != cudaSuccess) return TPCT_E_CUDA;
-  if (h & kDevTimeout) return TPCT_E_TIMEOUT;
   if (h & (kDevCapacity | kDevTrackletCap)) return TPCT_E_CAPACITY;
+  if (h & kDevBadRow) return TPCT_E_INVALID;
   return TPCT_OK;
 }
 
@@ -558,16 +613,16 @@ size_t tpct_tm_decode_workspace_bytes(int32_t n_tracks, int32_t n_instances, int
   return tm_decode_workspace_bytes(n_tracks, n_instances * n_rows);
 }
 
-tpct_status tpct_tm_decode(tpct_ctx* ctx, const uint8_t* data, const int64_t* track_off, int32_t n_tracks,
-                           const int64_t* row_off, int32_t n_instances, void* ws, size_t ws_bytes,
+tpct_status tpct_tm_decode(tpct_ctx* ctx, const uint8_t* data, int64_t n_bytes, const int64_t* track_off,
+                           int32_t n_tracks, const int64_t* row_off, int32_t n_instances, void* ws, size_t ws_bytes,
                            tpct_tm_decoded* out, tpct_stream stream) {
-  if (!ctx || !ws || !out || n_tracks < 0 || n_instances < 0 || ((uintptr_t)ws % kAlign)) return TPCT_E_INVALID;
-  if ((n_tracks > 0 && !track_off) || (n_instances > 0 && !row_off) || ((n_tracks > 0 || n_instances > 0) && !data))
+  if (!ctx || !ws || !out || n_tracks < 0 || n_instances < 0 || n_bytes < 0 || ((uintptr_t)ws % kAlign))
     return TPCT_E_INVALID;
-  if (!out->n || out->capacity < 0 ||
+  if ((n_tracks > 0 && !track_off) || (n_instances > 0 && !row_off) || (n_bytes > 0 && !data)) return TPCT_E_INVALID;
+  if (!out->n || !out->status || out->capacity < 0 ||
       (out->capacity > 0 && (!out->x || !out->y || !out->z || !out->charge || !out->row)))
     return TPCT_E_INVALID;
-  const int k = enqueue_tm_decode(ctx->row_x.data(), ctx->n_rows, data, track_off, n_tracks, row_off,
+  const int k = enqueue_tm_decode(ctx->row_x.data(), ctx->n_rows, data, n_bytes, track_off, n_tracks, row_off,
                                   n_instances * ctx->n_rows, ws, ws_bytes, *out, (cudaStream_t)stream);
   if (k < 0) return TPCT_E_NOMEM;
   ctx->launches += k;
@@ -612,11 +667,15 @@ __global__ void k_fma_probe(int iters, T a, T b, T* sink) {
 extern "C" tpct_status tpct_probe_fma(int use_fp64, int blocks, int iters, tpct_stream stream, float* ms) {
   if (blocks < 1 || iters < 1 || !ms) return TPCT_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TPCT_E_CUDA;
-  cudaEventRecord(e0, s);
   void* sink = nullptr;
   if (cudaGetSymbolAddress(&sink, g_probe_sink) != cudaSuccess) return TPCT_E_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return TPCT_E_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return TPCT_E_CUDA;
+  }
+  cudaEventRecord(e0, s);
   if (use_fp64) k_fma_probe<double><<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-7, (double*)sink);
   else k_fma_probe<float><<<blocks, 256, 0, s>>>(iters, 0.999999f, 1e-7f, (float*)sink);
   cudaEventRecord(e1, s);
@@ -625,6 +684,25 @@ extern "C" tpct_status tpct_probe_fma(int use_fp64, int blocks, int iters, tpct_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return check_cuda(e == cudaSuccess ? cudaGetLastError() : e);
+}
+
+// ------------------------------------------------------------------ conversion check
+namespace {
+__global__ void k_diag_convert(const float* f_in, double* d_out, const double* d_in, float* f_out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (f_in) d_out[i] = widen(f_in[i]);
+    if (d_in) f_out[i] = narrow(d_in[i]);
+  }
+}
+}  // namespace
+
+extern "C" tpct_status tpct_diag_convert(const float* f_in, double* d_out, const double* d_in, float* f_out,
+                                         int64_t n, tpct_stream stream) {
+  if (n < 0 || (f_in && !d_out) || (d_in && !f_out)) return TPCT_E_INVALID;
+  if (n == 0 || (!f_in && !d_in)) return TPCT_OK;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_diag_convert<<<blocks, 256, 0, (cudaStream_t)stream>>>(f_in, d_out, d_in, f_out, n);
+  return check_cuda(cudaGetLastError());
 }
 
 // ------------------------------------------------------------------ allocation-free entry point
@@ -667,56 +745,20 @@ cudaError_t static_ws_address(void** out) {
 
 extern "C" tpct_status tpct_track_static(tpct_ctx* ctx, const tpct_clusters* cl, int64_t n,
                                          tpct_tracks_out* out, tpct_stream stream) {
-  if (!ctx || !cl || !out || n < 0) return TPCT_E_INVALID;
+  if (!ctx) return TPCT_E_INVALID;
+  tpct_status st = check_call(cl, n, out);
+  if (st != TPCT_OK) return st;
   if (n > kStaticMaxClusters || cl->n_instances > kStaticMaxInstances) return TPCT_E_NOMEM;
-  if (cl->n_instances < 1 || !cl->sector_offsets) return TPCT_E_INVALID;
-  if (n > 0 && (!cl->y || !cl->z || (!cl->row && !cl->x))) return TPCT_E_INVALID;
-  if (!out->n_tracks || !out->n_ids || out->capacity_tracks < 0 || out->capacity_ids < 0) return TPCT_E_INVALID;
-  if (out->capacity_tracks > 0 && (!out->instance || !out->n_cl || !out->offset || !out->ndf ||
-                                   !out->status || !out->x_ref || !out->param || !out->cov || !out->chi2))
-    return TPCT_E_INVALID;
-  if (out->capacity_ids > 0 && !out->cluster_ids) return TPCT_E_INVALID;
+  if (cl->n_instances < 1) return TPCT_E_INVALID;
   const Plan plan_ws = make_plan(ctx->n_rows, kStaticMaxClusters, kStaticMaxInstances, 1);
   if (carve(nullptr, plan_ws, ctx->n_rows, nullptr) > kStaticBytes) return TPCT_E_NOMEM;   // too many rows
   void* base = nullptr;
   cudaError_t e = static_ws_address(&base);
   if (e != cudaSuccess) return fail_cuda(ctx, e);
-  if (ctx->tl_blocks == 0 || ctx->rf_blocks == 0) {
-    int dev = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return fail_cuda(ctx, e);
-    ctx->tl_blocks = ctx->n_sm * tracklet_blocks_per_sm((int)ctx->prec, ctx->tracklet_block);
-    ctx->rf_blocks = ctx->n_sm * refit_blocks_per_sm((int)ctx->prec, ctx->refit_block);
-  }
-  Params p{};
-  carve((char*)base, plan_ws, ctx->n_rows, &p);
-  const Plan pl = make_plan(ctx->n_rows, n, cl->n_instances, ctx->clusters_per_bin);
-  p.n_rows = ctx->n_rows;
-  p.n_inst = cl->n_instances;
-  p.n = (int32_t)n;
-  p.tcap = (int32_t)pl.tcap;
-  p.nbin_cap = (int32_t)pl.nbin;
-  p.clusters_per_bin = ctx->clusters_per_bin;
-  p.tan_half = ctx->tan_half;
-  p.z_max = ctx->z_max;
-  p.kb = kKbPerTesla * ctx->bz;
-  const tpct_cuts& c = ctx->cuts;
-  p.nf_wy = c.nf_wy; p.nf_wz = c.nf_wz; p.nf_dmax = c.nf_dmax; p.s_max = c.s_max;
-  p.edge_margin = c.edge_margin; p.search_k = c.search_k; p.chi2_max = c.chi2_max;
-  p.f_shared = c.f_shared; p.sig_readout = c.sig_readout; p.sig_cathode = c.sig_cathode;
-  p.c_s = c.c_s; p.c_t = c.c_t; p.c_qpt = c.c_qpt; p.c_yz_refit = c.c_yz_refit;
-  p.c_qpt_refit = c.c_qpt_refit; p.sig_slope = (c.sig_cathode - c.sig_readout) / ctx->z_max;
-  p.s_max_f = (float)c.s_max;
-  p.sig_readout_f = (float)c.sig_readout;
-  p.sig_slope_f = (float)p.sig_slope;
-  p.z_max_f = (float)ctx->z_max;
-  p.search_k_f = (float)c.search_k;
-  p.sig_hi_f = (float)(c.sig_readout > c.sig_cathode ? c.sig_readout : c.sig_cathode);
-  p.chi2_max_f = (float)c.chi2_max;
-  p.max_miss = c.max_miss; p.n_min = c.n_min; p.n_refit = c.n_refit;
-  p.x = cl->x; p.y = cl->y; p.z = cl->z; p.row = cl->row; p.inst_off = cl->sector_offsets;
-  p.out = *out;
+  st = ensure_grids(ctx);
+  if (st != TPCT_OK) return st;
+  Params p;
+  fill_params(ctx, cl, n, out, (char*)base, plan_ws, &p);
   cudaStream_t s = (cudaStream_t)stream;
   // the array keeps the previous call's contents: the status word starts at zero;
   // every other array the chain reads is written earlier in the same chain

@@ -127,18 +127,24 @@ __device__ __forceinline__ int vlen(uint64_t v) {
   return n;
 }
 
+// Reads the varints of one stream item: bytes [pos, end).  The encoder's own
+// streams never trip a check; the decoder runs on caller data, so a read past
+// the item's end or a varint longer than 10 bytes (more than 64 bits) sets
+// `bad` and returns 0 instead of reading further.
 struct Source {
   const uint8_t* p;
-  int64_t pos;
+  int64_t pos, end;
+  bool bad;
   __device__ uint64_t u() {
     uint64_t v = 0;
-    int sh = 0;
-    while (true) {
+    for (int i = 0; i < 10; ++i) {
+      if (pos >= end) { bad = true; return 0; }
       const uint8_t b = p[pos++];
-      v |= (uint64_t)(b & 127u) << sh;
+      v |= (uint64_t)(b & 127u) << (7 * i);
       if (!(b & 128u)) return v;
-      sh += 7;
     }
+    bad = true;
+    return 0;
   }
   __device__ int64_t s() { return unzig(u()); }
 };
@@ -518,19 +524,42 @@ __global__ void k_tm_fill(const __grid_constant__ TmDev T) {
 struct TdDev {
   int n_rows;
   int32_t n_tracks, n_blocks;
+  int64_t n_bytes;
   int64_t X[kMaxRows];
   float xf[kMaxRows];
   const uint8_t* data;
-  const int64_t *track_off, *row_off;
+  const int64_t *track_off, *row_off;   // [n_tracks + 1], [n_blocks + 1]
   uint64_t *cnt, *base;          // [n_tracks + n_blocks + 1]
   tpct_tm_decoded out;
 };
 
+// The bytes of work item w (a track, then the (instance, row) blocks) and its
+// cluster count.  An item whose offsets leave [0, n_bytes] or run backwards,
+// whose count varint is unreadable, or whose count needs more bytes than the
+// item holds (every track cluster takes at least 4 varints, every block
+// cluster 3) is bad: count 0, status bit set.
+__device__ Source td_item(const TdDev& D, int w, int64_t* m) {
+  const bool trk = w < D.n_tracks;
+  const int64_t a = trk ? D.track_off[w] : D.row_off[w - D.n_tracks];
+  const int64_t b = trk ? D.track_off[w + 1] : D.row_off[w - D.n_tracks + 1];
+  Source s{D.data, a, b, false};
+  if (!(a >= 0 && a <= b && b <= D.n_bytes)) {
+    s.bad = true;
+    s.end = s.pos = 0;
+  }
+  const uint64_t c = s.bad ? 0u : s.u();
+  if (!s.bad && c > (uint64_t)(s.end - s.pos) / (trk ? 4u : 3u)) s.bad = true;
+  *m = s.bad ? 0 : (int64_t)c;
+  return s;
+}
+
 __global__ void k_td_count(const __grid_constant__ TdDev D) {
   const int nw = D.n_tracks + D.n_blocks;
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
-    Source s{D.data, w < D.n_tracks ? D.track_off[w] : D.row_off[w - D.n_tracks]};
-    D.cnt[w] = s.u();
+    int64_t m;
+    const Source s = td_item(D, w, &m);
+    D.cnt[w] = (uint64_t)m;
+    if (s.bad) atomicOr(D.out.status, (uint32_t)TPCT_TD_BAD_STREAM);
   }
 }
 
@@ -551,29 +580,42 @@ __device__ __forceinline__ void put_cluster(const TdDev& D, int64_t o, int r, in
   D.out.row[o] = (uint8_t)r;
 }
 
+// Decodes every item again from its start.  A row outside the geometry, a
+// charge above 65535 or an unreadable varint ends the item (status bit set;
+// its remaining output slots are left unwritten).
 __global__ void k_td_decode(const __grid_constant__ TdDev D) {
   const int nw = D.n_tracks + D.n_blocks;
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
     int64_t o = (int64_t)D.base[w];
+    int64_t m;
+    Source s = td_item(D, w, &m);
     if (w < D.n_tracks) {
-      Source s{D.data, D.track_off[w]};
-      const int m = (int)s.u();
       int64_t xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
       int r = 0;
-      for (int j = 0; j < m; ++j) {
+      for (int64_t j = 0; j < m; ++j) {
         int64_t Y, Z;
         if (j == 0) {
-          r = (int)s.u();
+          const uint64_t r0 = s.u();
+          if (r0 >= (uint64_t)D.n_rows) s.bad = true;
+          else r = (int)r0;
           Y = s.s();
           Z = s.s();
         } else {
-          r = r + 1 + (int)s.u();
-          const int kk = j < 3 ? j : 3;
+          const uint64_t skip = s.u();
+          if (skip >= (uint64_t)(D.n_rows - 1 - r)) {
+            s.bad = true;
+          } else {
+            r = r + 1 + (int)skip;
+          }
+          const int kk = j < 3 ? (int)j : 3;
           const int64_t X = D.X[r];
           Y = s.s() + predict(xs, ys, kk, X);
           Z = s.s() + predict(xs, zs, kk, X);
         }
-        put_cluster(D, o++, r, Y, Z, s.u());
+        const uint64_t q = s.u();
+        if (q > 65535u) s.bad = true;
+        if (s.bad) break;
+        put_cluster(D, o++, r, Y, Z, q);
         xs[0] = xs[1]; xs[1] = xs[2]; xs[2] = D.X[r];
         ys[0] = ys[1]; ys[1] = ys[2]; ys[2] = Y;
         zs[0] = zs[1]; zs[1] = zs[2]; zs[2] = Z;
@@ -581,17 +623,23 @@ __global__ void k_td_decode(const __grid_constant__ TdDev D) {
     } else {
       const int b = w - D.n_tracks;
       const int r = b % D.n_rows;
-      Source s{D.data, D.row_off[b]};
-      const int64_t m = (int64_t)s.u();
       int64_t Y = 0;
       for (int64_t j = 0; j < m; ++j) {
         Y = j == 0 ? s.s() : Y + (int64_t)s.u();
         const int64_t Z = s.s();
-        put_cluster(D, o++, r, Y, Z, s.u());
+        const uint64_t q = s.u();
+        if (q > 65535u) s.bad = true;
+        if (s.bad) break;
+        put_cluster(D, o++, r, Y, Z, q);
       }
     }
+    if (s.bad) atomicOr(D.out.status, (uint32_t)TPCT_TD_BAD_STREAM);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *D.out.n = (int64_t)D.base[nw];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t n = (int64_t)D.base[nw];
+    *D.out.n = n;
+    if (n > D.out.capacity) atomicOr(D.out.status, (uint32_t)TPCT_TD_CAPACITY);
+  }
 }
 
 int blocks_for_t(int64_t work) {
@@ -662,9 +710,9 @@ int enqueue_tm_encode(const double* row_x, int n_rows, const tpct_clusters& cl, 
   return k;
 }
 
-int enqueue_tm_decode(const double* row_x, int n_rows, const uint8_t* data, const int64_t* track_off, int32_t n_tracks,
-                      const int64_t* row_off, int32_t n_blocks, void* ws, size_t ws_bytes, const tpct_tm_decoded& out,
-                      cudaStream_t s) {
+int enqueue_tm_decode(const double* row_x, int n_rows, const uint8_t* data, int64_t n_bytes, const int64_t* track_off,
+                      int32_t n_tracks, const int64_t* row_off, int32_t n_blocks, void* ws, size_t ws_bytes,
+                      const tpct_tm_decoded& out, cudaStream_t s) {
   if (tm_decode_workspace_bytes(n_tracks, n_blocks) > ws_bytes) return -2;
   TdDev D{};
   const size_t nw = (size_t)n_tracks + n_blocks + 1;
@@ -673,10 +721,11 @@ int enqueue_tm_decode(const double* row_x, int n_rows, const uint8_t* data, cons
   D.base = (uint64_t*)(p + (8 * nw + 255) / 256 * 256 + 256);
   uint64_t* tmp = (uint64_t*)(p + 2 * ((8 * nw + 255) / 256 * 256 + 256));
   tmp = (uint64_t*)(((uintptr_t)tmp + 255) / 256 * 256);
-  D.n_rows = n_rows; D.n_tracks = n_tracks; D.n_blocks = n_blocks;
+  D.n_rows = n_rows; D.n_tracks = n_tracks; D.n_blocks = n_blocks; D.n_bytes = n_bytes;
   for (int r = 0; r < n_rows; ++r) { D.X[r] = (int64_t)std::llrint(row_x[r] * 200.0); D.xf[r] = (float)row_x[r]; }
   D.data = data; D.track_off = track_off; D.row_off = row_off; D.out = out;
   int k = 0;
+  cudaMemsetAsync(out.status, 0, sizeof(uint32_t), s);
   k_td_count<<<blocks_for_t((int64_t)n_tracks + n_blocks), kBlockT, 0, s>>>(D); ++k;
   launch_scan_u64(D.cnt, D.base, (int64_t)n_tracks + n_blocks, tmp, s); k += 3;
   k_td_decode<<<blocks_for_t((int64_t)n_tracks + n_blocks), kBlockT, 0, s>>>(D); ++k;

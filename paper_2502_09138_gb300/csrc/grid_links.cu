@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_build(const __grid_consta
     for (int c = c0 + tid; c < c1; c += kGridThreads) {
       int r = P.row ? (int)P.row[c] : nearest_row(P, P.x[c]);
       if (r >= P.n_rows) {
-        atomicOr(P.status, kDevCapacity);
+        atomicOr(P.status, kDevBadRow);
         r = P.n_rows - 1;
       }
       P.c_ir[c] = inst * P.n_rows + r;

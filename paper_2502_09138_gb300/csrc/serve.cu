@@ -159,8 +159,6 @@ tpct_status launch_frame(tpct_server* S, uint64_t ticket, Frame& F) {
   if (e != cudaSuccess) return TPCT_E_CUDA;
   tpct_status st = tpct_set_workspace(sl.ctx, ws, ws_bytes, f.n, f.n_instances);
   if (st != TPCT_OK) return st;
-  // the context's status word leads its workspace; clear it in stream order
-  if (cudaMemsetAsync(ws, 0, 16, s) != cudaSuccess) return TPCT_E_CUDA;
   // outputs
   char* o = S->base + F.off_out;
   auto takeo = [&](size_t b) { char* q = o; o += align256(b); return q; };

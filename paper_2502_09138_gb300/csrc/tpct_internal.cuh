@@ -24,7 +24,9 @@ constexpr int kLenClasses = 256;               // track-length classes of the re
 constexpr double kKbPerTesla = 0.299792458e-2; // curvature [1/cm] per (q/pT [c/GeV]) per tesla
 
 enum StopReason { kStopEnd = 0, kStopProp = 1, kStopEdge = 2, kStopMiss = 3, kStopSinphi = 4 };
-enum DevStatus : uint32_t { kDevCapacity = 1u, kDevTimeout = 2u, kDevTrackletCap = 4u };
+// Sticky device status bits.  (No kernel waits for another, so none can time
+// out: bit 2 is unused.)
+enum DevStatus : uint32_t { kDevCapacity = 1u, kDevTrackletCap = 4u, kDevBadRow = 8u };
 
 // Per-row grid: bins cover [y0, y0 + ny/idy) x [z0, z0 + nz/idz); indices
 // outside are clamped to the border bins, so every cluster has a bin and the
@@ -210,9 +212,9 @@ size_t tm_encode_workspace_bytes(int64_t n, int32_t cap_tracks, int32_t n_blocks
 size_t tm_decode_workspace_bytes(int32_t n_tracks, int32_t n_blocks);
 int enqueue_tm_encode(const double* row_x, int n_rows, const tpct_clusters& cl, int64_t n, const tpct_tracks_out& tr,
                       void* ws, size_t ws_bytes, const tpct_tm_stream& out, cudaStream_t s);
-int enqueue_tm_decode(const double* row_x, int n_rows, const uint8_t* data, const int64_t* track_off, int32_t n_tracks,
-                      const int64_t* row_off, int32_t n_blocks, void* ws, size_t ws_bytes, const tpct_tm_decoded& out,
-                      cudaStream_t s);
+int enqueue_tm_decode(const double* row_x, int n_rows, const uint8_t* data, int64_t n_bytes, const int64_t* track_off,
+                      int32_t n_tracks, const int64_t* row_off, int32_t n_blocks, void* ws, size_t ws_bytes,
+                      const tpct_tm_decoded& out, cudaStream_t s);
 void launch_own(const Params& P, cudaStream_t s);
 void launch_emit(const Params& P, cudaStream_t s);
 // stage 0: all refit passes; 1: all but the last (PS/PE/PC types); 2: the last

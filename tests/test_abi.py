@@ -88,3 +88,25 @@ def test_auxiliary_workspace_sizes_without_gpu(lib):
     b = tm(1_000_000, 20_000, 36, 152)
     assert b > 16 * 1_000_000 and tm(2_000_000, 20_000, 36, 152) > b
     assert tm(-1, 1, 1, 152) == 0 and tm(1, -1, 1, 152) == 0
+
+
+def test_default_geometry_is_the_tpc_readout(lib):
+    """The library's built-in geometry equals the synthetic events' readout
+    (152 rows in three pitch regions, tan 10 deg, 250 cm)."""
+    import paper_2502_09138_gb300 as G
+    import synth
+    rx, tan_half, z_max = G.default_geometry()
+    g = synth.default_geometry()
+    assert np.array_equal(rx, g.row_x)
+    assert tan_half == g.tan_half_sector and z_max == g.z_max
+    assert rx.shape == (152,) and rx[0] == 85.2 and rx[63] == 135.1 and rx[127] == 199.4
+
+
+def test_package_does_not_import_test_data():
+    """The library package takes its default geometry from the library, not
+    from the synthetic-event package."""
+    import subprocess
+    import sys
+    code = ("import sys, paper_2502_09138_gb300 as G; G.Tracker(device='cpu'); "
+            "sys.exit(1 if 'synth' in sys.modules else 0)")
+    assert subprocess.run([sys.executable, "-c", code], cwd=ROOT).returncode == 0

@@ -52,6 +52,7 @@ def _check(G, ev, off, ncl, ids, trk=None, tracks=None):
     torch.cuda.synchronize()
     od = oracle.tm_decode(ref, ev.n)
     assert int(d["n"].item()) == ev.n
+    assert int(d["status"].item()) == 0
     for k in ("x", "y", "z", "row"):
         assert np.array_equal(d[k][:ev.n].cpu().numpy(), od[k]), k
     assert np.array_equal(d["charge"][:ev.n].cpu().numpy().view(np.uint16), od["charge"])
@@ -94,3 +95,52 @@ def test_no_tracks_and_capacity(G):
     torch.cuda.synchronize()
     ref = oracle.tm_encode(ev, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32))
     assert int(st["n_bytes"].item()) == ref.nbytes > 64
+
+
+def _decode(trk, data, toff, roff, nt, ni, cap, n_bytes=None):
+    import torch
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d = trk.tm_decode(t(np.asarray(data, np.uint8)), t(np.asarray(toff, np.int64)), nt,
+                      t(np.asarray(roff, np.int64)), ni, cap, n_bytes=n_bytes)
+    torch.cuda.synchronize()
+    return int(d["status"].item()), int(d["n"].item())
+
+
+def test_decoder_rejects_malformed_streams(G):
+    """The decoder takes caller data: every malformed item is reported by a
+    status bit, and no read leaves the stream or its item (the kernel's own
+    bounds checks, on inputs built here on the CPU)."""
+    from paper_2502_09138_gb300.binding import TPCT_TD_BAD_STREAM, TPCT_TD_CAPACITY
+    from synth.geometry import row_radii
+    fx, ev, off, ncl, ids = _fixture_event()
+    ref = oracle.tm_encode(ev, off, ncl, ids)
+    nt, ni = int(ncl.shape[0]), ev.n_instances
+    trk = G.Tracker(precision="mixed", bz=ev.bz)
+    assert _decode(trk, ref.data, ref.track_off, ref.row_off, nt, ni, ev.n) == (0, ev.n)
+    # output capacity too small: the count is reported, the bit set
+    assert _decode(trk, ref.data, ref.track_off, ref.row_off, nt, ni, 1) == (TPCT_TD_CAPACITY, ev.n)
+    # truncated stream (the last bytes missing, or none at all)
+    st, _ = _decode(trk, ref.data, ref.track_off, ref.row_off, nt, ni, ev.n, n_bytes=ref.nbytes - 3)
+    assert st & TPCT_TD_BAD_STREAM
+    st, _ = _decode(trk, ref.data, ref.track_off, ref.row_off, nt, ni, ev.n, n_bytes=0)
+    assert st & TPCT_TD_BAD_STREAM
+    # an item offset beyond the stream, and offsets running backwards
+    toff = np.array(ref.track_off, np.int64)
+    toff[0] = ref.nbytes + 100
+    st, _ = _decode(trk, ref.data, toff, ref.row_off, nt, ni, ev.n)
+    assert st & TPCT_TD_BAD_STREAM
+    toff = np.array(ref.track_off, np.int64)
+    toff[1] = toff[0] - 1
+    st, _ = _decode(trk, ref.data, toff, ref.row_off, nt, ni, ev.n)
+    assert st & TPCT_TD_BAD_STREAM
+    # a varint of 11 bytes, and a count larger than its item's bytes allow
+    nb0 = ni * 152
+    for data in ([0x80] * 11 + [0], [0xE8, 0x07]):   # continuation bytes only; the count 1000
+        st, n = _decode(trk, data, [0, len(data)], [len(data)] * (nb0 + 1), 1, ni, 16)
+        assert st == TPCT_TD_BAD_STREAM and n == 0
+    # rows outside the geometry: the same stream decoded with a 12-row geometry
+    # (the track's third cluster lies on row 12)
+    few = G.Tracker(row_x=row_radii()[:12], precision="mixed", bz=ev.bz)
+    assert int(ev.row[ids].max()) >= 12
+    st, _ = _decode(few, ref.data, ref.track_off, ref.row_off, nt, ni, ev.n)
+    assert st & TPCT_TD_BAD_STREAM

@@ -62,13 +62,18 @@ def test_static_matches_workspace_entry_twice(env, which):
     assert ref["n_tracks"] > 0
     lib = G.B.load()
     stream = torch.cuda.current_stream()
-    for _ in range(2):
-        out = trk.make_output(ev.n)
+    outs = [trk.make_output(ev.n) for _ in range(2)]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for out in outs:
         cs, os_ = dc.as_struct(), out.as_struct()
         rc = lib.tpct_track_static(trk._h, ctypes.byref(cs), ev.n, ctypes.byref(os_),
                                    ctypes.c_void_p(stream.cuda_stream))
         assert rc == G.B.TPCT_OK, lib.tpct_last_cuda_error(trk._h)
         torch.cuda.synchronize()
+    # the two calls took no device memory (the device's free memory is unchanged)
+    assert torch.cuda.mem_get_info()[0] == free0
+    for out in outs:
         _check_same(out.to_host(), ref)
 
 
