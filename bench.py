@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-merge", action="store_true")
+    ap.add_argument("--no-central", action="store_true", help="skip the central-event sub-record")
     ap.add_argument("--no-clusters", action="store_true")
     ap.add_argument("--no-compression", action="store_true")
     ap.add_argument("--only-clusters", action="store_true",
@@ -65,9 +66,12 @@ def parse():
     ap.add_argument("--tuning-cache", default=None, help="autotuner cache file (default: a fresh temp file)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variants", default="mixed_df", help="comma-separated extra precisions timed in the same run")
-    ap.add_argument("--frames", type=int, default=40, help="time frames of the serving leg")
+    ap.add_argument("--frames", type=int, default=30, help="time frames of 16-256 collisions per serving run")
+    ap.add_argument("--small-frames", type=int, default=200, help="time frames of 1-8 collisions per serving run")
+    ap.add_argument("--serve-loads", default="0.5,0.9,1.1", help="arrival rate / measured capacity, swept")
+    ap.add_argument("--only-serving", action="store_true", help="the serving sweep alone (after the capacity step)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
-    ap.add_argument("--serve-load", type=float, default=0.7, help="arrival rate / measured capacity")
+
     return ap.parse_args()
 
 
@@ -169,6 +173,142 @@ def tracklet_traffic(helix_steps):
         return None
 
 
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
+
+
+def alg_bytes(n, hits, n_out, k):
+    """Algorithmic DRAM bytes of one pass of the tracking path, the count fixed
+    before any tuning: per cluster 12 B of input, 24 B of grid scatter write and
+    read, 24 B of links written, read and cleaned, 4 B of start flags; per
+    tracklet hit 20 B (y, z read, hit id written, weight atomic, weight read);
+    4 B per output cluster id and 200 B per track."""
+    return 64.0 * n + 20.0 * hits + 4.0 * n_out + 200.0 * k
+
+
+def time_batched(trk, dc, out, steps, stream):
+    """Mean ms per batched step and mean ms per stage over `steps` graph replays
+    (CUDA events recorded inside the graph at the stage boundaries)."""
+    import torch
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(steps)]
+    for row in evs:
+        for e in row:
+            e.record(stream)
+    trk.set_stage_events(evs[0])
+    trk.track(dc, out, batched=True)      # capture with event nodes (untimed)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(steps):
+        trk.set_stage_events(evs[k])
+        trk.track(dc, out, batched=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(steps))
+                for i, name in enumerate(STAGES)}
+    trk.set_stage_events(None)
+    return ms, stage_ms
+
+
+def instance_views(G, dc):
+    """One DeviceClusters view per sector instance (the plain per-sector form)."""
+    import torch
+    offs = dc.sector_offsets.cpu().numpy()
+    views = []
+    for i in range(offs.shape[0] - 1):
+        a, b = int(offs[i]), int(offs[i + 1])
+        so = torch.tensor([0, b - a], dtype=torch.int64, device=dc.y.device)
+        views.append(G.DeviceClusters(dc.x[a:b], dc.y[a:b], dc.z[a:b], dc.charge[a:b],
+                                      dc.row[a:b] if dc.row is not None else None, so))
+    return views
+
+
+def time_plain(trk, parts, stream, reps):
+    """ms of one pass of the plain form: one tpct_track call per part, in turn."""
+    import torch
+    pout = trk.make_output(max(p.n for p in parts))
+    for p in parts[:3]:
+        trk.track(p, pout)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        for p in parts:
+            trk.track(p, pout)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    return a0.elapsed_time(a1) / reps
+
+
+def roofs(ms_step, ms_tracklets, n, gdbg, gout, probe):
+    """HBM fraction of the whole step (algorithmic bytes) and FP64 fractions of
+    the tracklet stage (algorithmic FP64 flops) against the in-run probe and the
+    nominal rate."""
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hits = int(np.asarray(gdbg["tl_nhits"]).sum())
+    b = alg_bytes(n, hits, int(gout["n_ids"]), int(gout["n_tracks"]))
+    steps, updates, tests = (int(v) for v in gdbg["counters"][:3])
+    flops = steps * FLOPS_STEP + tests * FLOPS_TEST + updates * FLOPS_UPDATE
+    fp64 = flops / (ms_tracklets * 1e-3) / 1e12
+    return {"alg_bytes_per_step": b, "tracklet_hits": hits, "hbm_achieved_gbs": b / (ms_step * 1e-3) / 1e9,
+            "hbm_peak_gbs": hbm_peak, "hbm_frac": b / (ms_step * 1e-3) / 1e9 / hbm_peak,
+            "hbm_peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "fallback",
+            "fp64_flops_tracklets": flops, "fp64_achieved_tflops": fp64,
+            "fp64_probe_tflops": probe, "fp64_probe_frac": fp64 / probe if probe else None,
+            "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS, "fp64_nominal_frac": fp64 / FP64_NOMINAL_TFLOPS}
+
+
+def central_leg(args, G, dev, stream, cache, probe):
+    """The central Pb-Pb-like event (one collision, 36 sectors, ~1.33 M
+    clusters): batched and plain forms, rooflines, and the CUDA result checked
+    against the oracle on the whole event."""
+    import torch
+    import synth
+    import oracle
+    from oracle.check import compare
+    ev = synth.generate_config(1)
+    cuts = G.default_cuts(sig_readout=ev.sigma.at_readout, sig_cathode=ev.sigma.at_cathode)
+    trk = G.Tracker(precision=args.precision, bz=ev.bz, cuts=cuts, device=dev)
+    trk.reserve(ev.n, ev.n_instances)
+    dc = G.DeviceClusters.from_event(ev, device=dev)
+    out = trk.make_output(ev.n)
+    tuning = None if args.no_autotune else trk.autotune(dc, out, cache_path=cache)
+    for _ in range(max(3, args.warmup)):
+        trk.track(dc, out, batched=True)
+    torch.cuda.synchronize()
+    status = trk.device_status()
+    dbg = trk.debug(ev.n)
+    torch.cuda.synchronize()
+    gdbg, gout = dbg.to_host(), out.to_host()
+    ms, stage_ms = time_batched(trk, dc, out, max(10, args.steps), stream)
+    per_sector = time_plain(trk, instance_views(G, dc), stream, 3)
+    one_call = time_plain(trk, [dc], stream, 5)
+    t0 = time.perf_counter()
+    ores = oracle.track_event(ev)
+    t_oracle = time.perf_counter() - t0
+    rep = compare(ev, ores, gdbg, gout)
+    parity = {k: rep[k] for k in ("pass", "nf_mismatch", "nf_excused", "tracklet_mismatch", "tracklet_unexcused",
+                                  "tracklets_compared", "track_mismatch", "track_excused", "track_unexcused",
+                                  "tracks_oracle", "tracks_gpu", "eff_oracle", "eff_gpu", "param_max_rel_err",
+                                  "cov_max_rel_err", "param_plain_rel_err", "cov_diag_plain_rel_err")}
+    nt = int(gout["n_tracks"])
+    return {"workload": "one central Pb-Pb-like event, 9000 tracks, 36 sectors", "clusters": ev.n,
+            "tracks": nt, "precision": args.precision, "tuning": tuning, "device_status": status,
+            "batched": {"value": ev.n / (ms * 1e-3), "unit": "clusters/s", "ms_per_event": ms,
+                        "tracks_per_s": nt / (ms * 1e-3), "stage_ms": stage_ms},
+            "plain_per_sector": {"value": ev.n / (per_sector * 1e-3), "unit": "clusters/s", "ms_per_event": per_sector,
+                                 "form": "one tpct_track call per sector instance (36 calls)",
+                                 "batched_speedup": per_sector / ms},
+            "plain_one_call": {"value": ev.n / (one_call * 1e-3), "unit": "clusters/s", "ms_per_event": one_call,
+                               "form": "one tpct_track call for the event (36 instances)",
+                               "batched_speedup": one_call / ms},
+            "roofline": roofs(ms, stage_ms["tracklets"], ev.n, gdbg, gout, probe),
+            "parity_full_event": parity, "oracle_s": t_oracle}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -204,8 +344,10 @@ def cpu_baseline(ev, gpu_out, gpu_dbg, budget_s=20.0):
     if gpu_out is not None:
         tr, dbg = slice_instances(ev, gpu_out, gpu_dbg, idx)
         r = compare(sub, ores, dbg, tr)
-        rep = {k: r[k] for k in ("pass", "nf_mismatch", "nf_excused", "track_mismatch", "track_excused",
-                                 "tracks_oracle", "tracks_gpu", "eff_oracle", "eff_gpu", "cov_max_rel_err")}
+        rep = {k: r[k] for k in ("pass", "nf_mismatch", "nf_excused", "tracklet_mismatch", "tracklet_unexcused",
+                                 "tracklets_compared", "track_mismatch", "track_excused", "track_unexcused",
+                                 "tracks_oracle", "tracks_gpu", "eff_oracle", "eff_gpu", "cov_max_rel_err",
+                                 "param_plain_rel_err", "cov_diag_plain_rel_err")}
         rep["param_max_rel_err"] = max(r["param_max_rel_err"])
     return {"value": sub.n / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(idx)} of {ev.n_instances} sector instances ({sub.n} clusters), "
@@ -321,62 +463,101 @@ def cluster_leg(args, G, dev, stream, copies=4, reps=10):
                          "frac": ach / peak, "algorithmic_bytes_per_launch": bytes_alg}}
 
 
-def serving_leg(args, ev, G, capacity_cps):
-    """Time frames of k collisions (k uniform in [16, min(256, batch size)]) cut
-    from the batch, arriving as a Poisson process at serve_load x the measured
-    batched capacity, tracked by the serving runtime with one slot (frames one
-    after another: the plain per-frame form) and with three slots (continuous
-    batching).  Latency = submission -> results ready."""
+def make_frames(pool, n_frames, k_range, rng, pin):
+    """Frames of k collisions, k uniform in k_range, each a random run of
+    consecutive collisions of the pool (pinned host views)."""
+    ne, spe, offs = pool.n_events, pool.sectors_per_event, pool.sector_offsets
     import torch
-    ne, spe, offs = ev.n_events, ev.sectors_per_event, ev.sector_offsets
-    rng = np.random.default_rng(4000)
-    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(ev, k))).pin_memory()
-           for k in ("x", "y", "z", "charge", "row")}
     frames = []
-    kmax = min(256, ne)
-    for _ in range(args.frames):
-        k = int(rng.integers(min(16, kmax), kmax + 1))
+    for _ in range(n_frames):
+        k = int(rng.integers(k_range[0], min(k_range[1], ne) + 1))
         c0 = int(rng.integers(0, ne - k + 1))
         a, b = int(offs[c0 * spe]), int(offs[(c0 + k) * spe])
         so = torch.from_numpy((offs[c0 * spe:(c0 + k) * spe + 1] - a).astype(np.int64)).pin_memory()
         frames.append(dict(x=pin["x"][a:b], y=pin["y"][a:b], z=pin["z"][a:b], charge=pin["charge"][a:b],
                            row=pin["row"][a:b], sector_offsets=so, collisions=k))
+    return frames
+
+
+def serve_run(G, args, cuts, bz, frames, rate, slots, seed):
+    """Frames arriving as a Poisson process of `rate` Hz into the serving
+    runtime with `slots` slots; a consumer thread releases every frame once it
+    is done (in submission order), so only frames in flight hold the arena.
+    Latency = submission -> results ready, as seen by the runtime."""
+    import threading
     sizes = np.array([f["y"].shape[0] for f in frames], np.float64)
-    rate = args.serve_load * capacity_cps / sizes.mean()
-    gaps = rng.exponential(1.0 / rate, len(frames))
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, len(frames))
     arrive = np.cumsum(gaps) - gaps[0]
-    cuts = G.default_cuts(sig_readout=ev.sigma.at_readout, sig_cathode=ev.sigma.at_cathode)
-    out = {"frames": len(frames), "collisions_per_frame": [int(min(f["collisions"] for f in frames)),
-                                                           int(max(f["collisions"] for f in frames))],
-           "mean_frame_clusters": float(sizes.mean()), "arrival_rate_hz": rate, "load": args.serve_load,
-           "budget_gb": args.serve_budget_gb}
-    for slots, name in ((1, "plain_per_frame"), (3, "continuous_batching")):
-        srv = G.Server(n_slots=slots, budget_bytes=int(args.serve_budget_gb * (1 << 30)), precision=args.precision,
-                       bz=ev.bz, cuts=cuts)
-        for f in frames[:2]:                      # warm-up
-            srv.wait(srv.submit(f))
-        for tk in list(srv._frames):
-            srv.release(tk)
-        t0 = time.perf_counter()
-        tks = []
-        for f, ta in zip(frames, arrive):
-            d = t0 + ta - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            tks.append(srv.submit(f))
-        for tk in tks:
-            srv.wait(tk)
-        lat = np.array([srv.poll(tk)["latency_us"] for tk in tks]) / 1e3
-        end = max(ta * 1e3 + l for ta, l in zip(arrive, lat))
-        st = srv.stats()
-        out[name] = {"slots": slots, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                     "sustained_clusters_per_s": float(sizes.sum() / (end * 1e-3)),
-                     "peak_in_flight": st["peak_in_flight"], "peak_gb": st["peak_bytes"] / 2 ** 30,
-                     "retries": st["retries"]}
-        for tk in tks:
-            srv.release(tk)
-        srv.close()
-        del srv
+    srv = G.Server(n_slots=slots, budget_bytes=int(args.serve_budget_gb * (1 << 30)), precision=args.precision,
+                   bz=bz, cuts=cuts)
+    for f in frames[:2]:                      # warm-up
+        tk = srv.submit(f)
+        srv.wait(tk)
+        srv.release(tk)
+    tks = []
+    lat = np.zeros(len(frames))
+    done = np.zeros(len(frames))
+    status = []
+
+    def consumer():
+        for i in range(len(frames)):
+            while len(tks) <= i:
+                time.sleep(0.0005)
+            srv.wait(tks[i])
+            info = srv.poll(tks[i])
+            lat[i] = info["latency_us"] / 1e3
+            done[i] = time.perf_counter()
+            status.append(info["status"])
+            srv.release(tks[i])
+
+    th = threading.Thread(target=consumer)
+    th.start()
+    t0 = time.perf_counter()
+    for f, ta in zip(frames, arrive):
+        d = t0 + ta - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tks.append(srv.submit(f))
+    th.join()
+    end = done.max() - t0
+    st = srv.stats()
+    srv.close()
+    del srv
+    return {"slots": slots, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "sustained_clusters_per_s": float(sizes.sum() / end), "offered_clusters_per_s": float(sizes.sum() / arrive[-1])
+            if arrive[-1] > 0 else None, "peak_in_flight": st["peak_in_flight"], "peak_gb": st["peak_bytes"] / 2 ** 30,
+            "retries": st["retries"], "failed": int(sum(1 for x in status if x != 0))}
+
+
+def serving_leg(args, pool, G, capacity_cps):
+    """Serving of time frames of 16-256 collisions drawn from a 256-collision
+    pool (the batching generator), arriving as a Poisson process, at several
+    loads (arrival rate x mean frame size / the measured batched capacity),
+    with one slot (frames one after another: the plain per-frame form) and
+    three slots (continuous batching); plus a mix of small frames (1-8
+    collisions), where one frame does not fill the GPU."""
+    import torch
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(pool, k))).pin_memory()
+           for k in ("x", "y", "z", "charge", "row")}
+    cuts = G.default_cuts(sig_readout=pool.sigma.at_readout, sig_cathode=pool.sigma.at_cathode)
+    loads = [float(v) for v in args.serve_loads.split(",") if v]
+    out = {"budget_gb": args.serve_budget_gb, "pool_collisions": pool.n_events, "capacity_clusters_per_s": capacity_cps}
+    for name, n_frames, k_range, seed in (("frames_16_256", args.frames, (16, 256), 4000),
+                                          ("frames_1_8", args.small_frames, (1, 8), 4100)):
+        if n_frames <= 0:
+            continue
+        frames = make_frames(pool, n_frames, k_range, np.random.default_rng(seed), pin)
+        sizes = np.array([f["y"].shape[0] for f in frames], np.float64)
+        coll = [f["collisions"] for f in frames]
+        rec = {"frames": len(frames), "collisions_per_frame": [int(min(coll)), int(max(coll))],
+               "mean_frame_clusters": float(sizes.mean()), "max_frame_clusters": float(sizes.max()), "sweep": []}
+        for load in (loads if name == "frames_16_256" else [0.9]):
+            rate = load * capacity_cps / sizes.mean()
+            for slots in (1, 3):
+                r = serve_run(G, args, cuts, pool.bz, frames, rate, slots, seed + int(load * 100))
+                r.update(load=load, arrival_rate_hz=rate)
+                rec["sweep"].append(r)
+        out[name] = rec
     return out
 
 
@@ -567,6 +748,14 @@ def main():
         return
     # generate before any CUDA call (the generator uses a spawn process pool)
     ev = workload(args, rank)
+    pool = None
+    if not args.no_serving and args.workload == "batch":
+        # the serving frames (16-256 collisions) come from a pool of 256
+        # collisions: the batch plus further collisions of the same generator
+        import synth
+        extra = 256 - ev.n_events
+        pool = ev if extra <= 0 else synth.concat_events([ev, synth.generate_config(
+            3, instance=rank + 1000, n_collisions=extra, workers=min(16, os.cpu_count() or 1))])
     import torch
     import paper_2502_09138_gb300 as G
     torch.cuda.set_device(local)
@@ -602,62 +791,54 @@ def main():
     gdbg = dbg.to_host()
     gout = out.to_host()
 
-    # per-step boundary events, re-pointed on every replay
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
-    for row in evs:
-        for e in row:
-            e.record(stream)
-    trk.set_stage_events(evs[0])
-    trk.track(dc, out, batched=True)      # capture with event nodes (untimed)
-    torch.cuda.synchronize()
-
     launches0 = trk.kernel_launches()
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for k in range(args.steps):
-        trk.set_stage_events(evs[k])
-        trk.track(dc, out, batched=True)
-    t1.record(stream)
-    torch.cuda.synchronize()
+    ms, stage_ms = time_batched(trk, dc, out, args.steps, stream)
     barrier()
     clocks = sampler.stop()
-    launches = trk.kernel_launches() - launches0
-    ms = t0.elapsed_time(t1) / args.steps
-    stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
-                for i, name in enumerate(STAGES)}
-    trk.set_stage_events(None)
+    # the capture replay inside time_batched launches one untimed step
+    launches = (trk.kernel_launches() - launches0) * args.steps // (args.steps + 1)
     ms, n_total = aggregate_ranks(ms, ev.n, world, dev)
     value = n_total / (ms * 1e-3)
     n_tracks = int(gout["n_tracks"])
+    if args.only_serving:
+        # the serving sweep alone, against the capacity just measured
+        if rank == 0:
+            print(json.dumps({"capacity_clusters_per_s": value / world, "ms_per_step": ms,
+                              "serving": serving_leg(args, pool, G, value / world)}), flush=True)
+        return
 
     # roofline of the dominant kernel
     peaks = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
     steps, updates, tests = (int(v) for v in gdbg["counters"][:3])
     fp64_flops = steps * FLOPS_STEP + tests * FLOPS_TEST + updates * FLOPS_UPDATE
-    fp64_probe = None
+    blocks = 152 * 16
+    pm = G.probe_fma(True, blocks, 2048)
+    fp64_probe = 2.0 * 8 * 2048 * blocks * 256 / (pm * 1e-3) / 1e12
+    step_roofs = roofs(ms, stage_ms["tracklets"], ev.n, gdbg, gout, fp64_probe)
     roofline = None
     if dom == "tracklets" and args.precision == "mixed":
-        blocks = 152 * 16
-        pm = G.probe_fma(True, blocks, 2048)
-        fp64_probe = 2.0 * 8 * 2048 * blocks * 256 / (pm * 1e-3) / 1e12
         ach = fp64_flops / (stage_ms["tracklets"] * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": "k_tracklets (FP64 covariance arithmetic)", "achieved": ach,
                     "peak": fp64_probe, "unit": "TFLOP/s", "frac": ach / fp64_probe,
                     "traffic": tracklet_traffic(steps) if args.precision == "mixed" else None,
                     "peak_source": "FP64 FMA probe in this run (152 SMs x 2 FMA/clk nominal)",
-                    "algorithmic_flops_per_launch": fp64_flops}
+                    "algorithmic_flops_per_launch": fp64_flops,
+                    "fp64_nominal_frac": ach / FP64_NOMINAL_TFLOPS,
+                    "hbm_frac": step_roofs["hbm_frac"], "hbm_achieved_gbs": step_roofs["hbm_achieved_gbs"],
+                    "hbm_peak_gbs": step_roofs["hbm_peak_gbs"],
+                    "hbm_alg_bytes_per_step": step_roofs["alg_bytes_per_step"]}
     else:
-        bytes_alg = 90.0 * ev.n
+        bytes_alg = step_roofs["alg_bytes_per_step"]
         ach = bytes_alg / (stage_ms[dom] * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peaks.get("hbm_gbs", 6800.0),
-                    "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6800.0), "traffic": None}
+                    "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                    "hbm_frac": step_roofs["hbm_frac"], "fp64_nominal_frac": step_roofs["fp64_nominal_frac"]}
 
     line = {
         "metric": METRIC, "value": value, "unit": "clusters/s",
@@ -683,23 +864,14 @@ def main():
             a, b = int(offs[c * spe]), int(offs[(c + 1) * spe])
             so = torch.from_numpy((offs[c * spe:(c + 1) * spe + 1] - a).astype(np.int64)).to(dev)
             parts.append(G.DeviceClusters(dc.x[a:b], dc.y[a:b], dc.z[a:b], dc.charge[a:b], dc.row[a:b], so))
-        pout = trk.make_output(max(p.n for p in parts))
-        for p in parts[:3]:
-            trk.track(p, pout)
-        torch.cuda.synchronize()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        reps = max(1, min(3, args.steps))
-        a0.record(stream)
-        for _ in range(reps):
-            for p in parts:
-                trk.track(p, pout)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        pms = a0.elapsed_time(a1) / reps
+        pms = time_plain(trk, parts, stream, max(1, min(3, args.steps)))
+        sms = time_plain(trk, instance_views(G, dc), stream, 2)
         line["plain"] = {"value": ev.n / (pms * 1e-3), "ms_per_step": pms, "unit": "clusters/s",
                          "form": "one tpct_track call per collision (36 instances), plain launches",
-                         "batched_speedup": pms / ms}
+                         "batched_speedup": pms / ms,
+                         "per_sector": {"value": ev.n / (sms * 1e-3), "ms_per_step": sms, "unit": "clusters/s",
+                                        "form": f"one tpct_track call per sector instance ({ev.n_instances} calls)",
+                                        "batched_speedup": sms / ms}}
 
     # end to end through host buffers
     if not args.no_e2e:
@@ -789,6 +961,9 @@ def main():
     if not args.no_compression:
         line["compression"] = compression_leg(args, ev, G, trk, dc, out, stream)
 
+    if not args.no_central and args.workload == "batch":
+        line["central"] = central_leg(args, G, dev, stream, cache, fp64_probe)
+
     variants = {}
     for vp in [v for v in args.variants.split(",") if v and v != args.precision]:
         vt = G.Tracker(precision=vp, bz=ev.bz, cuts=cuts, device=dev)
@@ -825,7 +1000,7 @@ def main():
         line["variants"] = variants
 
     if not args.no_serving and args.workload == "batch":
-        line["serving"] = serving_leg(args, ev, G, value / world)
+        line["serving"] = serving_leg(args, pool, G, value / world)
         line["publishing"] = publishing_leg(args, ev, G, value / world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -18,7 +18,9 @@ of the mixed precisions can flip a later decision of a long tracklet) is
 counted and passes only while it changes no output track and stays below
 0.1 % of the tracklets.  Floating outputs of identical tracks:
 |dp_i| <= rtol_par * max(|p_i|, sigma_i) with sigma_i from the oracle
-covariance; |dC_ij| <= rtol_cov * sqrt(C_ii C_jj).
+covariance; |dC_ij| <= rtol_cov * sqrt(C_ii C_jj).  The plain element-wise
+relative errors (parameters larger than their sigma, diagonal covariance
+terms) are reported beside that bar.
 """
 import numpy as np
 
@@ -168,6 +170,14 @@ def compare(ev, ores, gdbg, gtr, tol=1e-5, rtol_par=1e-4, rtol_cov=1e-3, eff_tol
         ok_status = gtr["status"][kg] == ores.tr_status[ko]
         good = ok_status & (ores.tr_status[ko] == 0)
         rep["param_max_rel_err"] = [float(v) for v in par_err[good].max(0)] if good.any() else [0.0] * 5
+        # the plain element-wise relative error, reported beside the scaled
+        # bar above: parameters with |p| > sigma_p, diagonal covariance terms
+        big = np.abs(op) > sig
+        plain = np.abs(gp - op) / np.where(big, np.abs(op), 1.0)
+        rep["param_plain_rel_err"] = [float(plain[good & big[:, i], i].max()) if (good & big[:, i]).any() else 0.0
+                                      for i in range(5)]
+        dg = np.abs(gcov[:, diag_i] - ocov[:, diag_i]) / np.maximum(np.abs(ocov[:, diag_i]), 1e-300)
+        rep["cov_diag_plain_rel_err"] = float(dg[good].max()) if good.any() else 0.0
         rep["cov_max_rel_err"] = float(cov_err[good].max()) if good.any() else 0.0
         chi2_err = np.abs(gtr["chi2"][kg] - ores.tr_chi2[ko]) / np.maximum(ores.tr_chi2[ko], 1.0)
         rep["chi2_max_rel_err"] = float(chi2_err[good].max()) if good.any() else 0.0
@@ -177,7 +187,8 @@ def compare(ev, ores, gdbg, gtr, tol=1e-5, rtol_par=1e-4, rtol_cov=1e-3, eff_tol
         rep["cov_fail"] = int((cov_err[good] > rtol_cov).any(1).sum())
         rep["xref_mismatch"] = int((gtr["x_ref"][kg] != ores.tr_x_ref[ko])[good].sum())
     else:
-        rep.update(param_max_rel_err=[0.0] * 5, cov_max_rel_err=0.0, chi2_max_rel_err=0.0, ndf_mismatch=0,
+        rep.update(param_max_rel_err=[0.0] * 5, param_plain_rel_err=[0.0] * 5, cov_diag_plain_rel_err=0.0,
+                   cov_max_rel_err=0.0, chi2_max_rel_err=0.0, ndf_mismatch=0,
                    status_mismatch=0, param_fail=0, cov_fail=0, xref_mismatch=0)
 
     # ---------------------------------------------------------------- efficiency

@@ -318,19 +318,22 @@ def concat_events(events) -> Event:
     offs = [np.zeros(1, np.int64)]
     base, mc_base = 0, 0
     mcs = []
+    tracks = []
     for e in events:
         offs.append(e.sector_offsets[1:] + base)
         base += e.n
         m = e.mc.astype(np.int64)
         mcs.append(np.where(m >= 0, m + mc_base, -1).astype(np.int32))
-        mc_base += int(e.meta.get("n_tracks", (m.max() + 1) if m.size else 0))
+        nt = e.meta.get("n_tracks", int(m.max() + 1) if m.size else 0)
+        nt = list(nt) if isinstance(nt, (list, tuple)) else [int(nt)]   # a batch lists its collisions
+        tracks += nt
+        mc_base += int(sum(nt))
     cat = lambda name: np.concatenate([getattr(e, name) for e in events])
     ev0 = events[0]
     return Event(cat("x"), cat("y"), cat("z"), cat("charge"), cat("row"), np.concatenate(offs),
                  np.concatenate([e.sectors for e in events]), np.concatenate(mcs),
-                 n_events=len(events), sectors_per_event=ev0.sectors_per_event, bz=ev0.bz,
-                 sigma=ev0.sigma, meta=dict(n_collisions=len(events),
-                                            n_tracks=[int(e.meta.get("n_tracks", 0)) for e in events]))
+                 n_events=sum(e.n_events for e in events), sectors_per_event=ev0.sectors_per_event, bz=ev0.bz,
+                 sigma=ev0.sigma, meta=dict(n_collisions=sum(e.n_events for e in events), n_tracks=tracks))
 
 
 def _collision(seed, over):

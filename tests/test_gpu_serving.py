@@ -87,3 +87,26 @@ def test_oversize_frame_refused(G, collisions):
         srv.submit(_frame(G, ev))
     assert e.value.code == G.B.TPCT_E_BUDGET
     srv.close()
+
+
+def test_wait_times_out_on_the_host_then_completes(G, collisions):
+    """tpct_server_wait gives up after its host timeout with TPCT_E_TIMEOUT
+    while the frame is still queued or running (no kernel waits for anything:
+    the timeout is the host's); a later wait returns the finished frame, equal
+    to the frame tracked alone."""
+    ev = collisions[2]
+    srv = _server(G, ev, n_slots=1, budget_bytes=4 << 30)
+    tk = srv.submit(_frame(G, ev))
+    with pytest.raises(G.B.TpctError) as e:
+        srv.wait(tk, timeout_s=1e-6)
+    assert e.value.code == G.B.TPCT_E_TIMEOUT
+    srv.wait(tk, timeout_s=600.0)
+    got = srv.fetch(tk)
+    srv.release(tk)
+    tk2 = srv.submit(_frame(G, ev))
+    srv.wait(tk2)
+    ref = srv.fetch(tk2)
+    srv.release(tk2)
+    srv.close()
+    assert got["n_tracks"] == ref["n_tracks"] > 0
+    assert np.array_equal(got["cluster_ids"], ref["cluster_ids"])
