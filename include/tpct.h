@@ -55,7 +55,9 @@ typedef enum {
   TPCT_E_CUDA = 4,       /* a CUDA runtime call failed */
   TPCT_E_TIMEOUT = 5,    /* device: a bounded wait gave up */
   TPCT_E_BUDGET = 6,     /* serving: request larger than the memory budget */
-  TPCT_E_STATE = 7       /* call not valid in the current state (e.g. no workspace) */
+  TPCT_E_STATE = 7,      /* call not valid in the current state (e.g. no workspace) */
+  TPCT_E_BOUNDS = 8      /* device: an index left its array (reported only by the bounds-checked
+                            build of the library, compiled with TPCT_CHECKED) */
 } tpct_status;
 
 /* Readout geometry (host, copied by tpct_create). */
@@ -259,8 +261,9 @@ tpct_status tpct_track_static(tpct_ctx* ctx, const tpct_clusters* clusters, int6
 tpct_status tpct_debug_export(tpct_ctx* ctx, tpct_debug_out* dbg, tpct_stream stream);
 
 /* Sticky device status of this context (synchronises the context's last
- * stream): TPCT_OK; TPCT_E_CAPACITY if an output or the tracklet plan
- * overflowed; TPCT_E_INVALID if an input row was outside the geometry.
+ * stream): TPCT_OK; TPCT_E_BOUNDS if an index left its array (bounds-checked
+ * build only); TPCT_E_CAPACITY if an output or the tracklet plan overflowed;
+ * TPCT_E_INVALID if an input row was outside the geometry.
  * Reading it clears it.  (No kernel waits for another, so no call on a
  * context times out on the device; TPCT_E_TIMEOUT comes only from
  * tpct_server_wait.)  Error reporting of this library (no counterpart in the

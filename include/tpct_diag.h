@@ -29,8 +29,8 @@ tpct_status tpct_probe_fma(int use_fp64, int blocks, int iters, tpct_stream stre
  * normal, infinite and NaN floats and maps float subnormals to zero; narrow
  * rounds to nearest with ties AWAY from zero (the hardware conversion rounds
  * ties to even), flushes results below float's normal range to zero or to a
- * subnormal below 2^-146, saturates beyond float's range to the largest
- * float, and turns infinities and NaNs into NaN.  Asynchronous on `stream`. */
+ * subnormal below 2^-146, saturates beyond float's range to a finite
+ * float within 8 ulp of the largest, and turns infinities and NaNs into NaN.  Asynchronous on `stream`. */
 tpct_status tpct_diag_convert(const float* f_in, double* d_out, const double* d_in, float* f_out, int64_t n,
                               tpct_stream stream);
 

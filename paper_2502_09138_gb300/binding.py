@@ -5,13 +5,16 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libtpct.so")
+# TPCT_CHECKED=1 selects the bounds-checked build (build.py --checked), in
+# which every subscript of the tracking chain's arrays is range-checked on the
+# device and a violation is reported as TPCT_E_BOUNDS
+LIB_PATH = os.path.join(_HERE, "_build_checked" if os.environ.get("TPCT_CHECKED") == "1" else "_build", "libtpct.so")
 
 c_int, c_int32, c_int64, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
                                                         ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t)
 
 TPCT_OK, TPCT_E_INVALID, TPCT_E_NOMEM, TPCT_E_CAPACITY, TPCT_E_CUDA, TPCT_E_TIMEOUT, TPCT_E_BUDGET, \
-    TPCT_E_STATE = range(8)
+    TPCT_E_STATE, TPCT_E_BOUNDS = range(9)
 PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2, "mixed_df": 3}
 
 

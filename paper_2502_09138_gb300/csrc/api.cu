@@ -60,6 +60,13 @@ Plan make_plan(int n_rows, int64_t n, int32_t ni, int clusters_per_bin_min) {
   return p;
 }
 
+// An array of `count` elements of T taken from the workspace (with its
+// length, which the bounds-checked build checks every subscript against).
+template <class T, class Take>
+TPCT_ARR(T) take_arr(Take& take, int64_t count, uint32_t* status) {
+  return mk_arr((T*)take(sizeof(T) * (size_t)count), count, status);
+}
+
 // Assign pointers inside the workspace; returns the bytes used.
 size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   size_t off = 0;
@@ -74,45 +81,45 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   Params q{};
   q.status = (uint32_t*)take(sizeof(uint32_t) * 4);
   q.work = (uint32_t*)take(sizeof(uint32_t) * 4);
-  q.rx = (const double*)take(sizeof(double) * n_rows);
-  q.rxf = (const float*)take(sizeof(float) * n_rows);
-  q.rdx = (const double*)take(sizeof(double) * n_rows);
-  q.rdxf = (const float*)take(sizeof(float) * n_rows);
-  q.edge = (const double*)take(sizeof(double) * n_rows);
-  q.edgef = (const float*)take(sizeof(float) * n_rows);
-  q.row_count = (int32_t*)take(4 * nr1);
-  q.row_start = (int32_t*)take(4 * nr1);
-  q.row_tl_count = (int32_t*)take(4 * nr1);
-  q.row_tl_base = (int32_t*)take(4 * nr1);
-  q.grid = (RowGrid*)take(sizeof(RowGrid) * nr1);
-  q.c_ir = (int32_t*)take(4 * n);
-  q.bin_count = (int32_t*)take(4 * (pl.nbin + 1));
-  q.bin_start = (int32_t*)take(4 * (pl.nbin + 1));
-  q.sy = (float*)take(4 * n);
-  q.sz = (float*)take(4 * n);
-  q.sid = (int32_t*)take(4 * n);
-  q.srow = (uint8_t*)take(n);
-  q.up = (int32_t*)take(4 * n);
-  q.down = (int32_t*)take(4 * n);
-  q.upc = (int32_t*)take(4 * n);
-  q.sflag = (uint8_t*)take(n);
-  q.W = (uint32_t*)take(4 * n);
-  q.tl_start = (int32_t*)take(4 * pl.tcap);
-  q.tl_ir = (int32_t*)take(4 * pl.tcap);
-  q.tl_nhits = (int32_t*)take(4 * pl.tcap);
-  q.tl_rowref = (int32_t*)take(4 * pl.tcap);
-  q.tl_hits = (int32_t*)take(4 * (size_t)pl.tcap * n_rows);
-  q.tl_par = (double*)take(8 * 5 * (size_t)pl.tcap);
-  q.tl_sel = (uint64_t*)take(8 * (pl.tcap + 1));
-  q.tl_sel_scan = (uint64_t*)take(8 * (pl.tcap + 1));
-  q.tl_cnt = (int32_t*)take(4 * 3 * (size_t)pl.tcap);
-  q.trk_est = (double*)take(8 * 5 * (size_t)pl.tcap);
-  q.trk_x = (double*)take(8 * (size_t)pl.tcap);
-  q.trk_st = (int32_t*)take(4 * (size_t)pl.tcap);
-  q.trk_tl = (int32_t*)take(4 * pl.tcap);
-  q.trk_pos = (int32_t*)take(4 * n);
-  q.trk_order = (int32_t*)take(4 * (size_t)pl.tcap);
-  q.len_cnt = (int32_t*)take(4 * (size_t)kLenClasses);
+  q.rx = take_arr<const double>(take, n_rows, q.status);
+  q.rxf = take_arr<const float>(take, n_rows, q.status);
+  q.rdx = take_arr<const double>(take, n_rows, q.status);
+  q.rdxf = take_arr<const float>(take, n_rows, q.status);
+  q.edge = take_arr<const double>(take, n_rows, q.status);
+  q.edgef = take_arr<const float>(take, n_rows, q.status);
+  q.row_count = take_arr<int32_t>(take, nr1, q.status);
+  q.row_start = take_arr<int32_t>(take, nr1, q.status);
+  q.row_tl_count = take_arr<int32_t>(take, nr1, q.status);
+  q.row_tl_base = take_arr<int32_t>(take, nr1, q.status);
+  q.grid = take_arr<RowGrid>(take, nr1, q.status);
+  q.c_ir = take_arr<int32_t>(take, n, q.status);
+  q.bin_count = take_arr<int32_t>(take, (pl.nbin + 1), q.status);
+  q.bin_start = take_arr<int32_t>(take, (pl.nbin + 1), q.status);
+  q.sy = take_arr<float>(take, n, q.status);
+  q.sz = take_arr<float>(take, n, q.status);
+  q.sid = take_arr<int32_t>(take, n, q.status);
+  q.srow = take_arr<uint8_t>(take, n, q.status);
+  q.up = take_arr<int32_t>(take, n, q.status);
+  q.down = take_arr<int32_t>(take, n, q.status);
+  q.upc = take_arr<int32_t>(take, n, q.status);
+  q.sflag = take_arr<uint8_t>(take, n, q.status);
+  q.W = take_arr<uint32_t>(take, n, q.status);
+  q.tl_start = take_arr<int32_t>(take, pl.tcap, q.status);
+  q.tl_ir = take_arr<int32_t>(take, pl.tcap, q.status);
+  q.tl_nhits = take_arr<int32_t>(take, pl.tcap, q.status);
+  q.tl_rowref = take_arr<int32_t>(take, pl.tcap, q.status);
+  q.tl_hits = take_arr<int32_t>(take, (size_t)pl.tcap * n_rows, q.status);
+  q.tl_par = take_arr<double>(take, 5 * (size_t)pl.tcap, q.status);
+  q.tl_sel = take_arr<uint64_t>(take, (pl.tcap + 1), q.status);
+  q.tl_sel_scan = take_arr<uint64_t>(take, (pl.tcap + 1), q.status);
+  q.tl_cnt = take_arr<int32_t>(take, 3 * (size_t)pl.tcap, q.status);
+  q.trk_est = take_arr<double>(take, 5 * (size_t)pl.tcap, q.status);
+  q.trk_x = take_arr<double>(take, (size_t)pl.tcap, q.status);
+  q.trk_st = take_arr<int32_t>(take, (size_t)pl.tcap, q.status);
+  q.trk_tl = take_arr<int32_t>(take, pl.tcap, q.status);
+  q.trk_pos = take_arr<int32_t>(take, n, q.status);
+  q.trk_order = take_arr<int32_t>(take, (size_t)pl.tcap, q.status);
+  q.len_cnt = take_arr<int32_t>(take, (size_t)kLenClasses, q.status);
   q.scan_tmp = (uint64_t*)take(8 * scan_tmp);
   if (P) {
     P->status = q.status; P->work = q.work; P->rx = q.rx; P->rxf = q.rxf;
@@ -142,12 +149,12 @@ __global__ void k_set_tables_v(const Params P, const RowTable tab) {
     const double x = tab.x[i];
     const double dx = i > 0 ? x - tab.x[i - 1] : 0.0;
     const double e = x * P.tan_half + P.edge_margin;
-    const_cast<double*>(P.rx)[i] = x;
-    const_cast<float*>(P.rxf)[i] = (float)x;
-    const_cast<double*>(P.rdx)[i] = dx;
-    const_cast<float*>(P.rdxf)[i] = (float)dx;
-    const_cast<double*>(P.edge)[i] = e;
-    const_cast<float*>(P.edgef)[i] = (float)e;
+    writable(P.rx)[i] = x;
+    writable(P.rxf)[i] = (float)x;
+    writable(P.rdx)[i] = dx;
+    writable(P.rdxf)[i] = (float)dx;
+    writable(P.edge)[i] = e;
+    writable(P.edgef)[i] = (float)e;
   }
 }
 
@@ -228,7 +235,11 @@ void fill_params(const tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const 
   p.sig_hi_f = (float)(c.sig_readout > c.sig_cathode ? c.sig_readout : c.sig_cathode);
   p.chi2_max_f = (float)c.chi2_max;
   p.max_miss = c.max_miss; p.n_min = c.n_min; p.n_refit = c.n_refit;
-  p.x = cl->x; p.y = cl->y; p.z = cl->z; p.row = cl->row; p.inst_off = cl->sector_offsets;
+  p.x = mk_arr(cl->x, n, p.status);
+  p.y = mk_arr(cl->y, n, p.status);
+  p.z = mk_arr(cl->z, n, p.status);
+  p.row = mk_arr(cl->row, n, p.status);
+  p.inst_off = mk_arr(cl->sector_offsets, (int64_t)cl->n_instances + 1, p.status);
   p.out = *out;
   *P = p;
 }
@@ -498,6 +509,7 @@ tpct_status tpct_last_device_status(tpct_ctx* ctx) {
   uint32_t h = 0;
   if (cudaMemcpy(&h, p.status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return TPCT_E_CUDA;
   if (cudaMemset(p.status, 0, sizeof(uint32_t)) != cudaSuccess) return TPCT_E_CUDA;
+  if (h & kDevBounds) return TPCT_E_BOUNDS;
   if (h & (kDevCapacity | kDevTrackletCap)) return TPCT_E_CAPACITY;
   if (h & kDevBadRow) return TPCT_E_INVALID;
   return TPCT_OK;
@@ -510,9 +522,10 @@ const char* tpct_status_str(tpct_status s) {
     case TPCT_E_NOMEM: return "out of memory or workspace too small";
     case TPCT_E_CAPACITY: return "output capacity exceeded";
     case TPCT_E_CUDA: return "CUDA error";
-    case TPCT_E_TIMEOUT: return "device wait timed out";
+    case TPCT_E_TIMEOUT: return "wait timed out";
     case TPCT_E_BUDGET: return "request exceeds the memory budget";
     case TPCT_E_STATE: return "invalid state";
+    case TPCT_E_BOUNDS: return "device index out of bounds (checked build)";
   }
   return "unknown status";
 }

@@ -39,7 +39,8 @@ __device__ __forceinline__ double widen(float f) {
 // double -> float, rounded to nearest (ties away from zero) by adding half a
 // float ulp to the bit pattern before truncating it; results below float's
 // normal range come out as zero or a subnormal below 2^-146, results above
-// it saturate to the largest float, infinities and NaNs become NaN.
+// it saturate to a finite float within 8 ulp of the largest (the exponent
+// saturates, the fraction keeps its top bits), infinities and NaNs become NaN.
 __device__ __forceinline__ float narrow(double d) {
   const uint64_t u = (uint64_t)__double_as_longlong(d) + 0x10000000ull;
   const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;

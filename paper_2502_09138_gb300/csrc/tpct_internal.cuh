@@ -25,8 +25,45 @@ constexpr double kKbPerTesla = 0.299792458e-2; // curvature [1/cm] per (q/pT [c/
 
 enum StopReason { kStopEnd = 0, kStopProp = 1, kStopEdge = 2, kStopMiss = 3, kStopSinphi = 4 };
 // Sticky device status bits.  (No kernel waits for another, so none can time
-// out: bit 2 is unused.)
-enum DevStatus : uint32_t { kDevCapacity = 1u, kDevTrackletCap = 4u, kDevBadRow = 8u };
+// out: bit 2 is unused.)  kDevBounds: an index outside its array, raised only
+// by the bounds-checked build.
+enum DevStatus : uint32_t { kDevCapacity = 1u, kDevTrackletCap = 4u, kDevBadRow = 8u, kDevBounds = 16u };
+
+// ------------------------------------------------------------------ bounds-checked build
+// Compiled with -DTPCT_CHECKED (build.py --checked), every workspace and input
+// array of Params is an Arr: subscripts are range-checked against the
+// array's allocated length before the access; an index outside sets
+// kDevBounds in the status word and the access goes to a scratch cell instead
+// (reads return whatever it holds; no trap, no write outside the arrays).  In
+// the normal build TPCT_ARR(T) is a plain T* and mk_arr returns the pointer.
+#ifdef TPCT_CHECKED
+static __device__ __align__(64) unsigned char g_bounds_sink[64];
+template <class T>
+struct Arr {
+  T* p = nullptr;
+  int64_t n = 0;
+  uint32_t* st = nullptr;
+  __host__ __device__ Arr() {}
+  __host__ __device__ Arr(T* p_, int64_t n_, uint32_t* st_) : p(p_), n(n_), st(st_) {}
+  __host__ __device__ operator T*() const { return p; }
+  __device__ T& operator[](int64_t i) const {
+    if ((uint64_t)i < (uint64_t)n) return p[i];
+    if (st) atomicOr(st, (uint32_t)kDevBounds);
+    return *reinterpret_cast<T*>(g_bounds_sink);
+  }
+  __host__ __device__ Arr operator+(int64_t k) const { return Arr(p + k, n - k, st); }
+};
+template <class T> inline Arr<T> mk_arr(T* p, int64_t n, uint32_t* st) { return Arr<T>(p, n, st); }
+#define TPCT_ARR(T) ::tpct::Arr<T>
+template <class T>
+__host__ __device__ inline Arr<T> writable(const Arr<const T>& a) { return Arr<T>(const_cast<T*>(a.p), a.n, a.st); }
+#else
+template <class T> inline T* mk_arr(T* p, int64_t, uint32_t*) { return p; }
+#define TPCT_ARR(T) T*
+#endif
+// Write access to a table that every kernel but the one filling it reads as const.
+template <class T>
+__host__ __device__ inline T* writable(const T* p) { return const_cast<T*>(p); }
 
 // Per-row grid: bins cover [y0, y0 + ny/idy) x [z0, z0 + nz/idz); indices
 // outside are clamped to the border bins, so every cluster has a bin and the
@@ -51,49 +88,54 @@ struct Params {
   float search_k_f, sig_hi_f, chi2_max_f;   // search_k, max(sig_readout, sig_cathode), chi2_max in float
   int32_t max_miss, n_min, n_refit;
   // input (device, caller-owned)
-  const float *x, *y, *z;
-  const uint8_t* row;
-  const int64_t* inst_off;
+  TPCT_ARR(const float) x;
+  TPCT_ARR(const float) y;
+  TPCT_ARR(const float) z;
+  TPCT_ARR(const uint8_t) row;
+  TPCT_ARR(const int64_t) inst_off;
   // workspace
-  const double* rx;            // [n_rows] row x (double)
-  const float* rxf;            // [n_rows] row x (float)
-  const double* rdx;           // [n_rows] rx[r] - rx[r-1] (0 at r = 0)
-  const float* rdxf;           // [n_rows] the same rounded to float
-  const double* edge;          // [n_rows] rx[r] * tan_half + edge_margin
-  const float* edgef;          // [n_rows] the same rounded to float
+  TPCT_ARR(const double) rx;   // [n_rows] row x (double)
+  TPCT_ARR(const float) rxf;   // [n_rows] row x (float)
+  TPCT_ARR(const double) rdx;  // [n_rows] rx[r] - rx[r-1] (0 at r = 0)
+  TPCT_ARR(const float) rdxf;  // [n_rows] the same rounded to float
+  TPCT_ARR(const double) edge; // [n_rows] rx[r] * tan_half + edge_margin
+  TPCT_ARR(const float) edgef; // [n_rows] the same rounded to float
   float s_max_f;               // s_max rounded to float
   uint32_t* status;            // sticky device status bits
   uint32_t* work;              // [2] work-queue heads of the tracklet and refit kernels
-  int32_t* row_count;          // [n_inst*n_rows + 1]
-  int32_t* row_start;          // [n_inst*n_rows + 1]
-  RowGrid* grid;               // [n_inst*n_rows]
-  int32_t* c_ir;               // [n] row key of each input cluster
-  int32_t* bin_count;          // [nbin_cap + 1]
-  int32_t* bin_start;          // [nbin_cap + 1]
-  float *sy, *sz;              // [n] sorted positions
-  int32_t* sid;                // [n] input id of each sorted position
-  uint8_t* srow;               // [n] row of each sorted position
-  int32_t *up, *down, *upc;    // [n]
-  uint8_t* sflag;              // [n] start-hit flag
-  int32_t* row_tl_count;       // [n_inst*n_rows + 1]
-  int32_t* row_tl_base;        // [n_inst*n_rows + 1]; [n_inst*n_rows] = tracklet count
-  int32_t* tl_start;           // [tcap]
-  int32_t* tl_ir;              // [tcap]
-  int32_t* tl_hits;            // [n_rows * tcap], slot-major
-  int32_t* tl_nhits;           // [tcap]
-  int32_t* tl_rowref;          // [tcap]
-  double* tl_par;              // [5 * tcap]
-  uint32_t* W;                 // [n]
-  uint64_t* tl_sel;            // [tcap + 1]  (accepted << 32 | owned) then its exclusive scan
-  uint64_t* tl_sel_scan;       // [tcap + 1]
-  int32_t* tl_cnt;             // [3 * tcap] helix steps, updates, chi2 tests of each tracklet
-  double* trk_est;             // [5 * tcap] refit estimate after the leading passes (mode 3)
-  double* trk_x;               // [tcap] its x
-  int32_t* trk_st;             // [tcap] transport failure in the leading passes
-  int32_t* trk_tl;             // [cap_tracks] tracklet of each output track
-  int32_t* trk_pos;            // [cap_ids]    sorted position of each output cluster
-  int32_t* trk_order;          // [tcap] output tracks, longest first (the refit's work order)
-  int32_t* len_cnt;            // [kLenClasses] tracks per length class, then cursors
+  TPCT_ARR(int32_t) row_count; // [n_inst*n_rows + 1]
+  TPCT_ARR(int32_t) row_start; // [n_inst*n_rows + 1]
+  TPCT_ARR(RowGrid) grid;      // [n_inst*n_rows]
+  TPCT_ARR(int32_t) c_ir;      // [n] row key of each input cluster
+  TPCT_ARR(int32_t) bin_count; // [nbin_cap + 1]
+  TPCT_ARR(int32_t) bin_start; // [nbin_cap + 1]
+  TPCT_ARR(float) sy;          // [n] sorted positions
+  TPCT_ARR(float) sz;
+  TPCT_ARR(int32_t) sid;       // [n] input id of each sorted position
+  TPCT_ARR(uint8_t) srow;      // [n] row of each sorted position
+  TPCT_ARR(int32_t) up;        // [n]
+  TPCT_ARR(int32_t) down;
+  TPCT_ARR(int32_t) upc;
+  TPCT_ARR(uint8_t) sflag;     // [n] start-hit flag
+  TPCT_ARR(int32_t) row_tl_count;  // [n_inst*n_rows + 1]
+  TPCT_ARR(int32_t) row_tl_base;   // [n_inst*n_rows + 1]; [n_inst*n_rows] = tracklet count
+  TPCT_ARR(int32_t) tl_start;  // [tcap]
+  TPCT_ARR(int32_t) tl_ir;     // [tcap]
+  TPCT_ARR(int32_t) tl_hits;   // [n_rows * tcap], slot-major
+  TPCT_ARR(int32_t) tl_nhits;  // [tcap]
+  TPCT_ARR(int32_t) tl_rowref; // [tcap]
+  TPCT_ARR(double) tl_par;     // [5 * tcap]
+  TPCT_ARR(uint32_t) W;        // [n]
+  TPCT_ARR(uint64_t) tl_sel;   // [tcap + 1]  (accepted << 32 | owned) then its exclusive scan
+  TPCT_ARR(uint64_t) tl_sel_scan;  // [tcap + 1]
+  TPCT_ARR(int32_t) tl_cnt;    // [3 * tcap] helix steps, updates, chi2 tests of each tracklet
+  TPCT_ARR(double) trk_est;    // [5 * tcap] refit estimate after the leading passes (mode 3)
+  TPCT_ARR(double) trk_x;      // [tcap] its x
+  TPCT_ARR(int32_t) trk_st;    // [tcap] transport failure in the leading passes
+  TPCT_ARR(int32_t) trk_tl;    // [tcap] tracklet of each output track
+  TPCT_ARR(int32_t) trk_pos;   // [n]    sorted position of each output cluster
+  TPCT_ARR(int32_t) trk_order; // [tcap] output tracks, longest first (the refit's work order)
+  TPCT_ARR(int32_t) len_cnt;   // [kLenClasses] tracks per length class, then cursors
   uint64_t* scan_tmp;          // block sums of the scans
   // output (device, caller-owned)
   tpct_tracks_out out;

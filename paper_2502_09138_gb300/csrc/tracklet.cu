@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
   int n_step = 0, n_upd = 0, n_test = 0;
   S p[5], top[5], in_p[5];
   C m[15];
-  int* hits = P.tl_hits;
+  auto hits = P.tl_hits;   // the tracklet's hit slots (stride tcap)
 
   while (true) {
     // ---- refill lanes without a tracklet from the work queue
