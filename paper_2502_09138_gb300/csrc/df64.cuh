@@ -130,13 +130,16 @@ __device__ __forceinline__ df64 fma_df(float a, df64 x, df64 y) {
   return fast_two_sum(s.hi, e);
 }
 
-// a / b: three float quotient digits, each from the running remainder.
+// a / b: three float quotient digits, each the running remainder's high part
+// times the float reciprocal of b's high part (the remainders correct each
+// digit's error; one reciprocal instead of three IEEE divisions).
 __device__ __forceinline__ df64 operator/(df64 a, df64 b) {
-  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const float ib = __frcp_rn(b.hi);
+  const float q1 = __fmul_rn(a.hi, ib);
   df64 r = a - b * q1;
-  const float q2 = __fdiv_rn(r.hi, b.hi);
+  const float q2 = __fmul_rn(r.hi, ib);
   r = r - b * q2;
-  const float q3 = __fdiv_rn(r.hi, b.hi);
+  const float q3 = __fmul_rn(r.hi, ib);
   return fast_two_sum(q1, q2) + df64(q3);
 }
 
@@ -159,6 +162,53 @@ __device__ __forceinline__ df64 sqrt(df64 a) {
   const float x = sqrtf(a.hi);
   const df64 r = a - two_prod(x, x);
   return fast_two_sum(x, __fdiv_rn(r.hi, __fmul_rn(2.f, x)));
+}
+
+// ---------------------------------------------------------------- fused double-float expressions
+// Sums of products renormalised once: the high parts of the products exactly
+// (TwoProd), the high parts summed by TwoSum, every low-order term (the
+// products' cross terms and the TwoSum errors) summed in float, one final
+// Fast-TwoSum.  Same error class as the operation-by-operation forms (about
+// 2^-47 of the largest term), fewer instructions.
+
+// a b + c d
+__device__ __forceinline__ df64 dot2(df64 a, df64 b, df64 c, df64 d) {
+  const df64 p = two_prod(a.hi, b.hi), q = two_prod(c.hi, d.hi);
+  const df64 s = two_sum(p.hi, q.hi);
+  float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  lo = __fmaf_rn(c.hi, d.lo, __fmaf_rn(c.lo, d.hi, __fadd_rn(lo, q.lo)));
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, lo));
+}
+
+// m - a b - c d
+__device__ __forceinline__ df64 fms2(df64 m, df64 a, df64 b, df64 c, df64 d) {
+  const df64 p = two_prod(a.hi, b.hi), q = two_prod(c.hi, d.hi);
+  const df64 s1 = two_sum(m.hi, -p.hi);
+  const df64 s2 = two_sum(s1.hi, -q.hi);
+  float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  lo = __fmaf_rn(c.hi, d.lo, __fmaf_rn(c.lo, d.hi, __fadd_rn(lo, q.lo)));
+  const float t = __fadd_rn(__fadd_rn(m.lo, s1.lo), __fsub_rn(s2.lo, lo));
+  return fast_two_sum(s2.hi, t);
+}
+
+// y + a x + b w for float a, b
+__device__ __forceinline__ df64 fma2_df(float a, df64 x, float b, df64 w, df64 y) {
+  const df64 p = two_prod(a, x.hi), q = two_prod(b, w.hi);
+  const df64 s1 = two_sum(y.hi, p.hi);
+  const df64 s2 = two_sum(s1.hi, q.hi);
+  const float lo = __fmaf_rn(a, x.lo, __fmaf_rn(b, w.lo, __fadd_rn(p.lo, q.lo)));
+  return fast_two_sum(s2.hi, __fadd_rn(__fadd_rn(y.lo, s1.lo), __fadd_rn(s2.lo, lo)));
+}
+
+// y + a x + b w + c v for float a, b, c
+__device__ __forceinline__ df64 fma3_df(float a, df64 x, float b, df64 w, float c, df64 v, df64 y) {
+  const df64 p = two_prod(a, x.hi), q = two_prod(b, w.hi), r = two_prod(c, v.hi);
+  const df64 s1 = two_sum(y.hi, p.hi);
+  const df64 s2 = two_sum(s1.hi, q.hi);
+  const df64 s3 = two_sum(s2.hi, r.hi);
+  const float lo = __fmaf_rn(a, x.lo, __fmaf_rn(b, w.lo, __fmaf_rn(c, v.lo, __fadd_rn(__fadd_rn(p.lo, q.lo), r.lo))));
+  const float t = __fadd_rn(__fadd_rn(__fadd_rn(y.lo, s1.lo), __fadd_rn(s2.lo, s3.lo)), lo);
+  return fast_two_sum(s3.hi, t);
 }
 
 // ---------------------------------------------------------------- conversions used by the kernels

@@ -143,32 +143,32 @@ __device__ __forceinline__ void cov_transport(C* m, J a, J b, J c, J d, J e, J f
 }
 
 // Double-float covariance with float Jacobian entries: the same products,
-// each term a fused float x double-float multiply-add.
+// the two or three terms of each entry summed with one renormalisation.
 __device__ __forceinline__ void cov_transport(df64* m, float a, float b, float c, float d, float e, float f) {
   const df64 m00 = m[0], m10 = m[1], m11 = m[2], m20 = m[3], m21 = m[4], m22 = m[5];
   const df64 m30 = m[6], m31 = m[7], m32 = m[8], m33 = m[9];
   const df64 m40 = m[10], m41 = m[11], m42 = m[12], m43 = m[13], m44 = m[14];
-  const df64 g00 = fma_df(b, m40, fma_df(a, m20, m00));
-  const df64 g02 = fma_df(b, m42, fma_df(a, m22, m20));
-  const df64 g04 = fma_df(b, m44, fma_df(a, m42, m40));
-  const df64 g10 = fma_df(e, m40, fma_df(d, m30, fma_df(c, m20, m10)));
-  const df64 g11 = fma_df(e, m41, fma_df(d, m31, fma_df(c, m21, m11)));
-  const df64 g12 = fma_df(e, m42, fma_df(d, m32, fma_df(c, m22, m21)));
-  const df64 g13 = fma_df(e, m43, fma_df(d, m33, fma_df(c, m32, m31)));
-  const df64 g14 = fma_df(e, m44, fma_df(d, m43, fma_df(c, m42, m41)));
+  const df64 g00 = fma2_df(a, m20, b, m40, m00);
+  const df64 g02 = fma2_df(a, m22, b, m42, m20);
+  const df64 g04 = fma2_df(a, m42, b, m44, m40);
+  const df64 g10 = fma3_df(c, m20, d, m30, e, m40, m10);
+  const df64 g11 = fma3_df(c, m21, d, m31, e, m41, m11);
+  const df64 g12 = fma3_df(c, m22, d, m32, e, m42, m21);
+  const df64 g13 = fma3_df(c, m32, d, m33, e, m43, m31);
+  const df64 g14 = fma3_df(c, m42, d, m43, e, m44, m41);
   const df64 g20 = fma_df(f, m40, m20), g21 = fma_df(f, m41, m21), g22 = fma_df(f, m42, m22);
   const df64 g23 = fma_df(f, m43, m32), g24 = fma_df(f, m44, m42);
-  m[0] = fma_df(b, g04, fma_df(a, g02, g00));
-  m[1] = fma_df(b, g14, fma_df(a, g12, g10));
-  m[2] = fma_df(e, g14, fma_df(d, g13, fma_df(c, g12, g11)));
-  m[3] = fma_df(b, g24, fma_df(a, g22, g20));
-  m[4] = fma_df(e, g24, fma_df(d, g23, fma_df(c, g22, g21)));
+  m[0] = fma2_df(a, g02, b, g04, g00);
+  m[1] = fma2_df(a, g12, b, g14, g10);
+  m[2] = fma3_df(c, g12, d, g13, e, g14, g11);
+  m[3] = fma2_df(a, g22, b, g24, g20);
+  m[4] = fma3_df(c, g22, d, g23, e, g24, g21);
   m[5] = fma_df(f, g24, g22);
-  m[6] = fma_df(b, m43, fma_df(a, m32, m30));
-  m[7] = fma_df(e, m43, fma_df(d, m33, fma_df(c, m32, m31)));
+  m[6] = fma2_df(a, m32, b, m43, m30);
+  m[7] = fma3_df(c, m32, d, m33, e, m43, m31);
   m[8] = fma_df(f, m43, m32);
-  m[10] = fma_df(b, m44, fma_df(a, m42, m40));
-  m[11] = fma_df(e, m44, fma_df(d, m43, fma_df(c, m42, m41)));
+  m[10] = fma2_df(a, m42, b, m44, m40);
+  m[11] = fma3_df(c, m42, d, m43, e, m44, m41);
   m[12] = fma_df(f, m44, m42);
 }
 
@@ -188,6 +188,12 @@ __device__ __forceinline__ C kf_chi2(const C* m, C r0, C r1, C vy, C vz) {
   return (r0 * (s11 * r0 - s01 * r1) + r1 * (s00 * r1 - s01 * r0)) / (s00 * s11 - s01 * s01);
 }
 
+// a b + c d and m - a b - c d: for float and double the plain expressions (as
+// the compiler contracts them); double-float has fused overloads (df64.cuh)
+// that renormalise once per expression.
+template <class T> __device__ __forceinline__ T dot2(T a, T b, T c, T d) { return a * b + c * d; }
+template <class T> __device__ __forceinline__ T fms2(T m, T a, T b, T c, T d) { return (m - a * b) - c * d; }
+
 // Gain K = C H^T S^-1; p += K r; C -= K H C (lower triangle).  Each entry
 // of C takes its two gain terms one after the other, which contracts into
 // two fused multiply-adds (instead of a product, a multiply-add and a
@@ -200,15 +206,15 @@ __device__ __forceinline__ void kf_update_inv(S* p, C* m, C r0, C r1, C s00, C s
   C k0[5], k1[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    k0[i] = c0[i] * i00 + c1[i] * i01;
-    k1[i] = c0[i] * i01 + c1[i] * i11;
+    k0[i] = dot2(c0[i], i00, c1[i], i01);
+    k1[i] = dot2(c0[i], i01, c1[i], i11);
     p[i] += (S)(k0[i] * r0 + k1[i] * r1);
   }
   int idx = 0;
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j, ++idx) m[idx] = (m[idx] - k0[i] * c0[j]) - k1[i] * c1[j];
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] = fms2(m[idx], k0[i], c0[j], k1[i], c1[j]);
 }
 
 template <class C, class S>
@@ -257,15 +263,15 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
   df64 k0[5], k1[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    k0[i] = c0[i] * i00 + c1[i] * i01;
-    k1[i] = c0[i] * i01 + c1[i] * i11;
+    k0[i] = dot2(c0[i], i00, c1[i], i01);
+    k1[i] = dot2(c0[i], i01, c1[i], i11);
     p[i] += df64(to_float(k0[i]) * fr0 + to_float(k1[i]) * fr1);
   }
   int idx = 0;
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j, ++idx) m[idx] = (m[idx] - k0[i] * c0[j]) - k1[i] * c1[j];
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] = fms2(m[idx], k0[i], c0[j], k1[i], c1[j]);
   return true;
 }
 

@@ -14,9 +14,9 @@ from gpu_util import run_gpu
 
 pytestmark = pytest.mark.gpu
 
-KEYS = ("nf_mismatch", "nf_excused", "tracklet_mismatch", "track_mismatch", "track_excused", "tracks_gpu",
-        "tracks_oracle", "param_max_rel_err", "cov_max_rel_err", "chi2_max_rel_err", "eff_gpu", "eff_oracle",
-        "fake_gpu", "pass")
+KEYS = ("nf_mismatch", "nf_excused", "tracklet_mismatch", "tracklet_unexcused", "track_mismatch", "track_excused",
+        "tracks_gpu", "tracks_oracle", "param_max_rel_err", "cov_max_rel_err", "param_plain_rel_err",
+        "cov_diag_plain_rel_err", "chi2_max_rel_err", "eff_gpu", "eff_oracle", "fake_gpu", "pass")
 
 
 @pytest.fixture(scope="module")
