@@ -234,7 +234,7 @@ tpct_status tpct_set_stage_events(tpct_ctx* ctx, void* const* events, int n_even
  * its input and output buffers from a host framework that owns all device
  * memory, a process whose memory is fully planned at start-up, or a latency-
  * critical path where a cudaMalloc would synchronise the device -- and so
- * cannot attach a workspace.  The scratch is a fixed 20 MiB array inside this
+ * cannot attach a workspace.  The scratch is a fixed 24 MiB array inside this
  * library, held on every GPU that loads the library until the process exits;
  * it fits ONE sector instance of at most 65536 clusters (n_instances must be
  * 1).  Larger requests return TPCT_E_NOMEM, more instances too; contexts with

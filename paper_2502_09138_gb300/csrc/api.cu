@@ -120,6 +120,8 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   q.trk_pos = take_arr<int32_t>(take, n, q.status);
   q.trk_order = take_arr<int32_t>(take, (size_t)pl.tcap, q.status);
   q.len_cnt = take_arr<int32_t>(take, (size_t)kLenClasses, q.status);
+  q.rf_state = take_arr<double>(take, (size_t)kRefitState * pl.tcap, q.status);
+  q.rf_j = take_arr<int32_t>(take, (size_t)pl.tcap, q.status);
   q.scan_tmp = (uint64_t*)take(8 * scan_tmp);
   if (P) {
     P->status = q.status; P->work = q.work; P->rx = q.rx; P->rxf = q.rxf;
@@ -134,7 +136,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
     P->tl_hits = q.tl_hits; P->tl_par = q.tl_par; P->tl_sel = q.tl_sel; P->tl_sel_scan = q.tl_sel_scan;
     P->tl_cnt = q.tl_cnt; P->trk_tl = q.trk_tl;
     P->trk_est = q.trk_est; P->trk_x = q.trk_x; P->trk_st = q.trk_st; P->trk_pos = q.trk_pos; P->scan_tmp = q.scan_tmp;
-    P->trk_order = q.trk_order; P->len_cnt = q.len_cnt;
+    P->trk_order = q.trk_order; P->len_cnt = q.len_cnt; P->rf_state = q.rf_state; P->rf_j = q.rf_j;
   }
   return off;
 }
@@ -304,9 +306,11 @@ int enqueue_track(tpct_ctx* ctx, const Params& P, cudaStream_t s) {
   cudaMemsetAsync(P.len_cnt, 0, sizeof(int32_t) * kLenClasses, s);
   launch_refit_order(P, s); k += 3;
   if ((mode == 1 || mode == 3) && P.n_refit >= 2) {
-    // leading passes in double-float, the last pass in double
+    // leading passes in double-float; the last pass in double for its first
+    // kRefitHead clusters and in double-float for the rest
     launch_refit(P, mode, 1, ctx->refit_block, ctx->rf_blocks, s); ++k;
     launch_refit(P, mode, 2, ctx->refit_block, ctx->rf_blocks, s); ++k;
+    launch_refit(P, mode, 3, ctx->refit_block, ctx->rf_blocks, s); ++k;
   } else {
     launch_refit(P, mode, 0, ctx->refit_block, ctx->rf_blocks, s); ++k;
   }
@@ -730,7 +734,7 @@ extern "C" tpct_status tpct_diag_convert(const float* f_in, double* d_out, const
 namespace {
 constexpr int64_t kStaticMaxClusters = 65536;
 constexpr int32_t kStaticMaxInstances = 1;
-constexpr size_t kStaticBytes = (size_t)20 << 20;   // 20 MiB; the plan above needs 18.7 MiB at 152 rows
+constexpr size_t kStaticBytes = (size_t)24 << 20;   // 24 MiB; the plan above needs 23.2 MiB at 152 rows
 constexpr int kStaticMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_ws[kStaticBytes];

@@ -110,13 +110,19 @@ template <int MODE, int STAGE> struct RefitTypes {
 template <int MODE> struct RefitTypes<MODE, 1> {
   using S = typename Prec<MODE>::PS; using E = typename Prec<MODE>::PE; using C = typename Prec<MODE>::PC;
 };
+// STAGE 3: the last pass after its first kRefitHead clusters (double-float)
+template <int MODE> struct RefitTypes<MODE, 3> {
+  using S = typename Prec<MODE>::PS; using E = typename Prec<MODE>::PE; using C = typename Prec<MODE>::PC;
+};
 
 template <int MODE, int STAGE>
 __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Params P) {
   using S = typename RefitTypes<MODE, STAGE>::S;
   using E = typename RefitTypes<MODE, STAGE>::E;
   using C = typename RefitTypes<MODE, STAGE>::C;
-  const int pass_begin = STAGE == 2 ? P.n_refit - 1 : 0;
+  // STAGE 0: all passes; 1: the leading passes; 2: the last pass, handing a
+  // track over after its first kRefitHead clusters; 3: the rest of the last pass
+  const int pass_begin = STAGE >= 2 ? P.n_refit - 1 : 0;
   const int pass_end = STAGE == 1 ? P.n_refit - 1 : P.n_refit;
   const tpct_tracks_out& O = P.out;
   const uint64_t total = P.tl_sel_scan[P.tcap];
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
     if (want) {
       const int leader = __ffs(want) - 1;
       int base = 0;
-      if (lane == leader) base = (int)atomicAdd(P.work + 1 + (STAGE == 2 ? 1 : 0), (uint32_t)__popc(want));
+      if (lane == leader) base = (int)atomicAdd(P.work + (STAGE >= 2 ? STAGE : 1), (uint32_t)__popc(want));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
         const int slot = base + __popc(want & lanes_below);
@@ -147,12 +153,26 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
         } else {
           const int mine = P.trk_order[slot];
           const int nn = O.n_cl[mine], off = O.offset[mine];
-          if (nn >= 1 && off >= 0 && off + nn <= O.capacity_ids) {   // ids of overflowing tracks were not written
+          // ids of overflowing tracks were not written; the tail takes only
+          // the tracks the head handed over
+          if (nn >= 1 && off >= 0 && off + nn <= O.capacity_ids && (STAGE != 3 || P.rf_j[mine] >= 0)) {
             k = mine;
             n = nn;
             pos = P.trk_pos + off;
             t = P.trk_tl[k];
-            if (STAGE == 2) {
+            if (STAGE == 3) {
+#pragma unroll
+              for (int i = 0; i < 5; ++i) {
+                ref[i] = conv<S>(P.rf_state[(int64_t)i * P.tcap + k]);
+                d[i] = conv<S>(P.rf_state[(int64_t)(5 + i) * P.tcap + k]);
+              }
+#pragma unroll
+              for (int i = 0; i < 15; ++i) m[i] = conv<C>(P.rf_state[(int64_t)(10 + i) * P.tcap + k]);
+              chi2 = conv<C>(P.rf_state[(int64_t)25 * P.tcap + k]);
+              x_prev = P.rf_state[(int64_t)26 * P.tcap + k];
+              status = 0;
+              j = P.rf_j[k];
+            } else if (STAGE == 2) {
 #pragma unroll
               for (int i = 0; i < 5; ++i) est[i] = (S)P.trk_est[(int64_t)i * P.tcap + k];
               x_cur = P.trk_x[k];
@@ -164,12 +184,13 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
               status = 0;
             }
             pass = pass_begin;
-            j = n - 1;
+            if (STAGE != 3) j = n - 1;
           }
         }
       }
     }
-    if (__ballot_sync(0xffffffffu, k >= 0) == 0u) break;
+    // a lane whose refill found an unusable track (not exhausted) refills again
+    if (__ballot_sync(0xffffffffu, k >= 0 || !exhausted) == 0u) break;
     if (k < 0) continue;
 
     const int pj = pos[j];
@@ -205,6 +226,21 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
       const C sg = sigma_of<C>(P, conv<C>(P.sz[pj]));
       const C r0 = (conv<C>(P.sy[pj]) - ref[0]) - d[0], r1 = (conv<C>(P.sz[pj]) - ref[1]) - d[1];
       chi2 += kf_chi2_update<C, S>(d, m, r0, r1, sg * sg);
+      if (STAGE == 2 && j >= 1 && n - j >= kRefitHead) {
+        // hand the track over to the double-float tail at cluster j - 1
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          P.rf_state[(int64_t)i * P.tcap + k] = to_double(ref[i]);
+          P.rf_state[(int64_t)(5 + i) * P.tcap + k] = to_double(d[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 15; ++i) P.rf_state[(int64_t)(10 + i) * P.tcap + k] = to_double(m[i]);
+        P.rf_state[(int64_t)25 * P.tcap + k] = to_double(chi2);
+        P.rf_state[(int64_t)26 * P.tcap + k] = x_prev;
+        P.rf_j[k] = j - 1;
+        k = -1;
+        continue;
+      }
       if (--j < 0) {
 #pragma unroll
         for (int i = 0; i < 5; ++i) est[i] = ref[i] + d[i];
@@ -219,6 +255,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
       P.trk_st[k] = status;
       k = -1;
     } else if (done) {
+      if (STAGE == 2) P.rf_j[k] = -1;   // finished in the head
       O.status[k] = status;
       O.chi2[k] = status ? 0.0 : to_double(chi2);
       O.x_ref[k] = status ? P.rx[P.tl_rowref[t]] : x_cur;
@@ -339,10 +376,12 @@ void launch_refit(const Params& P, int mode, int stage, int block, int blocks, c
     case 4: k_refit<1, 0><<<blocks, block, 0, s>>>(P); break;
     case 5: k_refit<1, 1><<<blocks, block, 0, s>>>(P); break;
     case 6: k_refit<1, 2><<<blocks, block, 0, s>>>(P); break;
+    case 7: k_refit<1, 3><<<blocks, block, 0, s>>>(P); break;
     case 8: k_refit<2, 0><<<blocks, block, 0, s>>>(P); break;
     case 12: k_refit<3, 0><<<blocks, block, 0, s>>>(P); break;
     case 13: k_refit<3, 1><<<blocks, block, 0, s>>>(P); break;
     case 14: k_refit<3, 2><<<blocks, block, 0, s>>>(P); break;
+    case 15: k_refit<3, 3><<<blocks, block, 0, s>>>(P); break;
     default: break;
   }
 }
@@ -357,6 +396,8 @@ int refit_blocks_per_sm(int mode, int block) {
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<1, 2>, block, 0);
       if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_refit<1, 1>, block, 0);
       if (nb1 < nb) nb = nb1;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_refit<1, 3>, block, 0);
+      if (nb1 < nb) nb = nb1;
       break;
     }
     case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<2, 0>, block, 0); break;
@@ -364,6 +405,8 @@ int refit_blocks_per_sm(int mode, int block) {
       int nb1 = 0;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refit<3, 2>, block, 0);
       if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_refit<3, 1>, block, 0);
+      if (nb1 < nb) nb = nb1;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_refit<3, 3>, block, 0);
       if (nb1 < nb) nb = nb1;
       break;
     }

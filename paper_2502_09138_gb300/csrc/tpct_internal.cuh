@@ -21,6 +21,12 @@ constexpr uint32_t kRankMask = (1u << kRankBits) - 1u;
 constexpr int kStageEvents = 7;               // step boundaries timed by tpct_set_stage_events
 constexpr int kMaxBlock = 256;                 // largest tracklet / refit block
 constexpr int kLenClasses = 256;               // track-length classes of the refit order
+// The refit's last pass runs its first kRefitHead clusters (outermost first)
+// in FP64 and the rest in double-float (modes 1 and 3): the diffuse prior
+// cancels in the first updates, where FP64 is needed; afterwards the
+// covariance is data-dominated.
+constexpr int kRefitHead = 8;
+constexpr int kRefitState = 27;                 // ref[5], d[5], C[15], chi2, x of the last cluster
 constexpr double kKbPerTesla = 0.299792458e-2; // curvature [1/cm] per (q/pT [c/GeV]) per tesla
 
 enum StopReason { kStopEnd = 0, kStopProp = 1, kStopEdge = 2, kStopMiss = 3, kStopSinphi = 4 };
@@ -136,6 +142,8 @@ struct Params {
   TPCT_ARR(int32_t) trk_pos;   // [n]    sorted position of each output cluster
   TPCT_ARR(int32_t) trk_order; // [tcap] output tracks, longest first (the refit's work order)
   TPCT_ARR(int32_t) len_cnt;   // [kLenClasses] tracks per length class, then cursors
+  TPCT_ARR(double) rf_state;   // [kRefitState * tcap] last-pass state handed from the FP64 head to the tail
+  TPCT_ARR(int32_t) rf_j;      // [tcap] next cluster of the tail, -1: the track finished in the head
   uint64_t* scan_tmp;          // block sums of the scans
   // output (device, caller-owned)
   tpct_tracks_out out;
