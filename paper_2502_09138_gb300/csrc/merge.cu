@@ -475,6 +475,69 @@ __device__ __forceinline__ void cov_rotate(df64* m, const Rot& J) {
 // transport and stores the estimate; STAGE 2 runs the last pass, which gives
 // the parameters, covariance and chi2, in double.  One thread per chain, in
 // the longest-first order.
+// Kalman filter of clusters k_hi down to k_lo of a chain of n clusters (a
+// pass runs from the outermost cluster inward; the first has no transport) in state type S, transport type E and
+// covariance type C, rotating the state at every change of sector; the
+// reference, deviation, covariance, chi2, x of the previous cluster and the
+// current segment carry over between spans.
+template <class S, class E, class C>
+__device__ __forceinline__ void chain_span(const MParams& M, const int* ids, const int* segs, int n, int k_hi,
+                                           int k_lo, S* ref, S* d, C* Cm, C& chi2, double& x_prev, int& seg,
+                                           int& seg_start, int& status) {
+  for (int k = k_hi; k >= k_lo && !status; --k) {
+    const int id = ids[k];
+    const double xk = M.rx[row_of(M, id)];
+    if (k < n - 1) {
+      if (k < seg_start) {   // the cluster lies in the previous (inner) segment: rotate
+        const int from = segs[seg];
+        --seg;
+        seg_start -= M.trk.n_cl[segs[seg]];
+        double x1, rd[5];
+        Rot J;
+        for (int i = 0; i < 5; ++i) rd[i] = to_double(ref[i]);
+        if (!rotate_state(wrap_pi(M.alpha[segs[seg]] - M.alpha[from]), M.kb, M.s_max, x_prev, rd, &x1, &J)) {
+          status = 1;
+          return;
+        }
+        for (int i = 0; i < 5; ++i) ref[i] = conv<S>(rd[i]);
+        const S d0 = d[0];
+        d[0] = mulj(J.jyy, d0);
+        d[1] = mulj(J.jzy, d0) + d[1];
+        d[2] = mulj(J.jsy, d0) + mulj(J.jss, d[2]);
+        cov_rotate(Cm, J);
+        x_prev = x1;
+      }
+      Step<E> st;
+      if (!helix_step<E>(to_e<E>(ref[2]), to_e<E>(ref[3]), to_e<E>(ref[4]), conv<E>(xk - x_prev), (E)M.kb,
+                         (E)M.s_max, st)) {
+        status = 1;
+        return;
+      }
+      ref[0] += conv<S>(st.dy); ref[1] += conv<S>(st.dz); ref[2] += conv<S>(st.ds);
+      d[0] += st.j_ys * d[2] + st.j_yq * d[4];
+      d[1] += st.j_zs * d[2] + st.j_zt * d[3] + st.j_zq * d[4];
+      d[2] += st.j_sq * d[4];
+      cov_transport<C, E>(Cm, st);
+    }
+    C var;
+    if constexpr (is_df64<C>::value) {
+      float dd = M.z_max_f - fabsf(M.z[id]);
+      dd = fminf(fmaxf(dd, 0.0f), M.z_max_f);
+      const float sg = M.sig_readout_f + M.sig_slope_f * dd;
+      var = conv<C>(sg * sg);
+    } else {
+      const double zc = widen(M.z[id]);
+      double dd = M.z_max - fabs(zc);
+      dd = dd < 0.0 ? 0.0 : (dd > M.z_max ? M.z_max : dd);
+      const double sg = M.sig_readout + M.sig_slope * dd;
+      var = sg * sg;
+    }
+    const C r0 = (conv<C>(M.y[id]) - ref[0]) - d[0], r1 = (conv<C>(M.z[id]) - ref[1]) - d[1];
+    chi2 += kf_chi2_update<C, S>(d, Cm, r0, r1, var);
+    x_prev = xk;
+  }
+}
+
 template <int STAGE>
 __global__ void __launch_bounds__(128) k_m_refit(const __grid_constant__ MParams M) {
   using S = typename std::conditional<STAGE == 1, df64, double>::type;
@@ -534,57 +597,24 @@ __global__ void __launch_bounds__(128) k_m_refit(const __grid_constant__ MParams
       double x_prev = x_outer;
       int seg = m - 1;
       int seg_start = n - M.trk.n_cl[segs[m - 1]];   // first cluster index of the current segment
-      for (int k = n - 1; k >= 0 && !status; --k) {
-        const int id = ids[k];
-        const double xk = M.rx[row_of(M, id)];
-        if (k < n - 1) {
-          if (k < seg_start) {   // the cluster lies in the previous (inner) segment: rotate
-            const int from = segs[seg];
-            --seg;
-            seg_start -= M.trk.n_cl[segs[seg]];
-            double x1, rd[5];
-            Rot J;
-            for (int i = 0; i < 5; ++i) rd[i] = to_double(ref[i]);
-            if (!rotate_state(wrap_pi(M.alpha[segs[seg]] - M.alpha[from]), M.kb, M.s_max, x_prev, rd, &x1, &J)) {
-              status = 1;
-              break;
-            }
-            for (int i = 0; i < 5; ++i) ref[i] = conv<S>(rd[i]);
-            const S d0 = d[0];
-            d[0] = mulj(J.jyy, d0);
-            d[1] = mulj(J.jzy, d0) + d[1];
-            d[2] = mulj(J.jsy, d0) + mulj(J.jss, d[2]);
-            cov_rotate(Cm, J);
-            x_prev = x1;
-          }
-          Step<E> st;
-          if (!helix_step<E>(to_e<E>(ref[2]), to_e<E>(ref[3]), to_e<E>(ref[4]), conv<E>(xk - x_prev), (E)M.kb,
-                             (E)M.s_max, st)) {
-            status = 1;
-            break;
-          }
-          ref[0] += conv<S>(st.dy); ref[1] += conv<S>(st.dz); ref[2] += conv<S>(st.ds);
-          d[0] += st.j_ys * d[2] + st.j_yq * d[4];
-          d[1] += st.j_zs * d[2] + st.j_zt * d[3] + st.j_zq * d[4];
-          d[2] += st.j_sq * d[4];
-          cov_transport<C, E>(Cm, st);
+      if constexpr (STAGE == 1) {
+        chain_span<S, E, C>(M, ids, segs, n, n - 1, 0, ref, d, Cm, chi2, x_prev, seg, seg_start, status);
+      } else {
+        // the last pass: its first kRefitHead clusters (outermost first) in
+        // FP64, where the diffuse prior cancels, the rest in double-float
+        const int k_split = max(n - kRefitHead, 0);
+        chain_span<S, E, C>(M, ids, segs, n, n - 1, k_split, ref, d, Cm, chi2, x_prev, seg, seg_start, status);
+        if (!status && k_split > 0) {
+          df64 rf[5], df[5], Cf[15];
+          for (int i = 0; i < 5; ++i) { rf[i] = df64(ref[i]); df[i] = df64(d[i]); }
+          for (int i = 0; i < 15; ++i) Cf[i] = df64(Cm[i]);
+          df64 chi2f = df64(chi2);
+          chain_span<df64, float, df64>(M, ids, segs, n, k_split - 1, 0, rf, df, Cf, chi2f, x_prev, seg, seg_start,
+                                        status);
+          for (int i = 0; i < 5; ++i) { ref[i] = to_double(rf[i]); d[i] = to_double(df[i]); }
+          for (int i = 0; i < 15; ++i) Cm[i] = to_double(Cf[i]);
+          chi2 = to_double(chi2f);
         }
-        C var;
-        if constexpr (STAGE == 1) {
-          float dd = M.z_max_f - fabsf(M.z[id]);
-          dd = fminf(fmaxf(dd, 0.0f), M.z_max_f);
-          const float sg = M.sig_readout_f + M.sig_slope_f * dd;
-          var = conv<C>(sg * sg);
-        } else {
-          const double zc = widen(M.z[id]);
-          double dd = M.z_max - fabs(zc);
-          dd = dd < 0.0 ? 0.0 : (dd > M.z_max ? M.z_max : dd);
-          const double sg = M.sig_readout + M.sig_slope * dd;
-          var = sg * sg;
-        }
-        const C r0 = (conv<C>(M.y[id]) - ref[0]) - d[0], r1 = (conv<C>(M.z[id]) - ref[1]) - d[1];
-        chi2 += kf_chi2_update<C, S>(d, Cm, r0, r1, var);
-        x_prev = xk;
       }
       if (status) break;
       for (int i = 0; i < 5; ++i) est[i] = to_double(ref[i] + d[i]);
