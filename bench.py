@@ -35,12 +35,12 @@ sys.path.insert(0, ROOT)
 
 STAGES = ["grid", "neighbours", "clean_start", "tracklets", "selection", "refit"]
 # FP64 flops of the mixed-precision tracklet filter: a helix step transports
-# the covariance (51 multiply-adds) and adds the float increments to the
-# double state (3 adds); a chi2 test forms the double residuals (2 adds, the
-# chi2 itself is float); an update forms S (2), det (3), 1/det (1), S^-1 (3),
-# the gain (10 + 10), the covariance (30 multiply-adds) and adds the state
-# increments (5)
-FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 2 * 51 + 3, 2, 2 + 3 + 1 + 3 + 30 + 60 + 5
+# the covariance (51 multiply-adds; the float increments go to the
+# double-float state on the FP32 pipes); a chi2 test widens the two
+# double-float residuals (2 adds, the chi2 itself is float); an update forms
+# S (2), det (3), 1/det (1), S^-1 (3), the gain (10 + 10) and the covariance
+# (30 multiply-adds)
+FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 2 * 51, 2, 2 + 3 + 1 + 3 + 30 + 60
 
 
 def parse():
@@ -307,6 +307,31 @@ def central_leg(args, G, dev, stream, cache, probe):
                                "batched_speedup": one_call / ms},
             "roofline": roofs(ms, stage_ms["tracklets"], ev.n, gdbg, gout, probe),
             "parity_full_event": parity, "oracle_s": t_oracle}
+
+
+def tracklet_issue(helix_steps, ms, sm_mhz):
+    """Issue-slot use of the double-float tracklet kernel: its warp
+    instructions (the committed ncu count per helix step, scaled by this run's
+    helix steps) over the issue slots of 152 SMs x 4 schedulers in its
+    CUDA-event time at the sampled SM clock; None if the kernel's sources
+    changed since the count was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_tracklets_df_issue.json")) as f:
+            doc = json.load(f)
+        h = hashlib.sha256()
+        for src in doc["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != doc["sources_sha256"]:
+            return None
+    except (OSError, KeyError, ValueError):
+        return None
+    mhz = sm_mhz or 2070.0
+    instr = doc["warp_instructions_per_helix_step"] * helix_steps
+    slots = 152 * 4 * ms * 1e-3 * mhz * 1e6
+    return {"warp_instructions": instr, "issue_slots": slots, "issue_frac": instr / slots,
+            "sm_mhz": mhz, "source": "profiles/k_tracklets_df_issue.json"}
 
 
 def measured_peaks():
@@ -844,7 +869,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "clusters/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64", "mixed_df": "f32+df64"}[args.precision],
+        # arithmetic types of the path: float transport and search; FP64
+        # tracklet covariance update and refit head; double-float (float pairs)
+        # tracklet state and refit passes, and the tracklet covariance in mixed_df
+        "dtype": {"mixed": "f32+f64+df64", "fp32": "f32", "fp64": "f64", "mixed_df": "f32+df64+f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": workload_name(args),
                    "clusters_per_rank": ev.n, "sector_instances": ev.n_instances, "precision": args.precision,
@@ -994,6 +1022,9 @@ def main():
                         "stage_ms": {name: statistics.mean(vev[k][i].elapsed_time(vev[k][i + 1])
                                                            for k in range(args.steps))
                                      for i, name in enumerate(STAGES)}}
+        if vp == "mixed_df":
+            variants[vp]["tracklet_issue"] = tracklet_issue(steps, variants[vp]["stage_ms"]["tracklets"],
+                                                            clocks.get("sm_mhz") if clocks else None)
         vt.set_stage_events(None)
         del vt
     if variants:

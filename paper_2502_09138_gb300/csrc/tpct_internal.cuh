@@ -152,8 +152,9 @@ struct Params {
 // ------------------------------------------------------------------ precision
 // S: track state, E: helix-transport / neighbour / search arithmetic,
 // C: covariance, Kalman update; RS/RE/RC: the same for the refit.
-// MODE 0 FP32; 1 mixed (float E, double S/C: float transport increments,
-// double Kalman update); 2 FP64; 3 mixed double-float (float E, double-float
+// MODE 0 FP32; 1 mixed (float E, double C, double-float S: float transport
+// increments added to a double-float state on the FP32 pipes, double Kalman
+// gain and covariance update); 2 FP64; 3 mixed double-float (float E, double-float
 // S/C in the tracklets).  The last refit pass is all-double in modes 1-3: its
 // covariance starts from a diffuse prior and amplifies rounding by ~1e12,
 // beyond what the 48-bit double-float keeps.
@@ -166,7 +167,7 @@ template <int MODE> struct Prec;
 template <> struct Prec<0> { using S = float;  using E = float;  using C = float;
                              using RS = float;  using RE = float;  using RC = float;
                              using PS = float;  using PE = float;  using PC = float; };
-template <> struct Prec<1> { using S = double; using E = float;  using C = double;
+template <> struct Prec<1> { using S = df64;   using E = float;  using C = double;
                              using RS = double; using RE = double; using RC = double;
                              using PS = df64;   using PE = float;  using PC = df64; };
 template <> struct Prec<2> { using S = double; using E = double; using C = double;

@@ -275,7 +275,8 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
   return true;
 }
 
-// Mixed tracklet filter (double state and covariance, float transport): the
+// Mixed tracklet filter (double-float state, double covariance, float
+// transport; S is the state type, double in the FP64-state form): the
 // chi2 decision in float (1e-6 relative at most, inside the 1e-5 near-cut
 // band) and the state increment K r in float (1e-7 of an increment far
 // smaller than the state); 1/det, the gain and the covariance update, whose
@@ -284,7 +285,8 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
 // 128-collision batch: when S is large and its y-z correlation strong, the
 // float det loses digits and one step does not recover them; the det here is
 // formed in double and its reciprocal refined twice.)
-__device__ __forceinline__ bool kf_test_update_mixed(double* p, double* m, double r0, double r1, float v,
+template <class S>
+__device__ __forceinline__ bool kf_test_update_mixed(S* p, double* m, double r0, double r1, float v,
                                                      float chi2_max) {
   const float f00 = narrow(m[0]) + v, f01 = narrow(m[1]), f11 = narrow(m[2]) + v;
   const float fr0 = narrow(r0), fr1 = narrow(r1);
@@ -314,7 +316,7 @@ __device__ __forceinline__ bool kf_test_update_mixed(double* p, double* m, doubl
   for (int i = 0; i < 5; ++i) {
     k0[i] = c0[i] * i00 + c1[i] * i01;
     k1[i] = c0[i] * i01 + c1[i] * i11;
-    p[i] += widen(narrow(k0[i]) * fr0 + narrow(k1[i]) * fr1);
+    p[i] += conv<S>(narrow(k0[i]) * fr0 + narrow(k1[i]) * fr1);
   }
   int idx = 0;
 #pragma unroll

@@ -55,6 +55,11 @@ __device__ int search_row(const Params& P, int ir, S py, S pz, E cyy, E czz) {
   return best;
 }
 
+// A residual (state type) in the covariance type; a double-float residual
+// becomes a double by widening both halves and one addition.
+template <class C, class T> __device__ __forceinline__ C to_c(T v) { return (C)v; }
+template <> __device__ __forceinline__ double to_c<double, df64>(df64 v) { return to_double(v); }
+template <> __device__ __forceinline__ float to_c<float, df64>(df64 v) { return to_float(v); }
 template <int MODE>
 __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__ Params P) {
   using S = typename Prec<MODE>::S;
@@ -156,7 +161,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
     __syncwarp(active);
     bool ok = false;
     if (cand >= 0) {
-      const C ry = (C)(conv<S>(P.sy[cand]) - p[0]), rz = (C)(conv<S>(P.sz[cand]) - p[1]);
+      const C ry = to_c<C>(conv<S>(P.sy[cand]) - p[0]), rz = to_c<C>(conv<S>(P.sz[cand]) - p[1]);
       ++n_test;
       bool pass;
       if constexpr (kMixed) pass = kf_test_update_mixed(p, m, ry, rz, cluster_var(P, P.sz[cand]), P.chi2_max_f);
