@@ -13,39 +13,73 @@
 // tracklet ends takes the next one from a device work queue (warp-aggregated
 // atomic), so the FP64 (or double-float) covariance arithmetic of each
 // iteration runs with full warps instead of idling lanes of finished
-// tracklets.  Results do not depend on which lane or order runs a tracklet.
+// tracklets.  The grid search of the lanes that need one is done by the whole
+// warp together (candidates tested one per lane), since per lane its loop
+// length varies and left most lanes idle.  Results do not depend on which
+// lane or order runs a tracklet.
 #include "track_math.cuh"
 
 namespace tpct {
 namespace {
 
-// Best cluster of row key ir around (py, pz): inside |dy|^2 <= k^2 (Cyy + s_c^2)
-// and |dz|^2 <= k^2 (Czz + s_c^2) with s_c the cluster's sigma; minimal
-// dy^2/(Cyy+s_c^2) + dz^2/(Czz+s_c^2), ties to the smaller input id.
+// Search window of row key ir around (py, pz): inside |dy|^2 <= k^2 (Cyy + s_c^2)
+// and |dz|^2 <= k^2 (Czz + s_c^2) with s_c the cluster's sigma, over the grid
+// bins [iy0, iy1] x [iz0, iz1] that cover it.
+template <class E>
+struct SearchWin {
+  RowGrid g;
+  E ey, ez, cyy, czz, k2;
+  int iy0, iy1, iz0, iz1;
+};
+
 template <class E, class S>
-__device__ int search_row(const Params& P, int ir, S py, S pz, E cyy, E czz) {
-  const RowGrid g = P.grid[ir];
+__device__ __forceinline__ SearchWin<E> search_window(const Params& P, int ir, S py, S pz, E cyy, E czz) {
+  SearchWin<E> w;
+  w.g = P.grid[ir];
   constexpr bool kF = std::is_same<E, float>::value;
-  const E k = kF ? (E)P.search_k_f : (E)P.search_k, k2 = k * k;
+  const E k = kF ? (E)P.search_k_f : (E)P.search_k;
+  w.k2 = k * k;
   const E sig_hi = kF ? (E)P.sig_hi_f : (E)fmax(P.sig_readout, P.sig_cathode);
   const E wy = k * sqrt(cyy + sig_hi * sig_hi), wz = k * sqrt(czz + sig_hi * sig_hi);
-  const E ey = to_e<E>(py), ez = to_e<E>(pz);
-  const float fy = (float)ey, fz = (float)ez;
+  w.ey = to_e<E>(py);
+  w.ez = to_e<E>(pz);
+  w.cyy = cyy;
+  w.czz = czz;
+  const float fy = (float)w.ey, fz = (float)w.ez;
   const float wyf = (float)wy * 1.0001f + 1e-4f, wzf = (float)wz * 1.0001f + 1e-4f;
-  const int iy0 = bin_y(g, fy - wyf), iy1 = bin_y(g, fy + wyf);
-  const int iz0 = bin_z(g, fz - wzf), iz1 = bin_z(g, fz + wzf);
+  w.iy0 = bin_y(w.g, fy - wyf);
+  w.iy1 = bin_y(w.g, fy + wyf);
+  w.iz0 = bin_z(w.g, fz - wzf);
+  w.iz1 = bin_z(w.g, fz + wzf);
+  return w;
+}
+
+// Cluster q against a window centred at (ey, ez): inside the box, and if so
+// its distance d = dy^2/(Cyy+s_c^2) + dz^2/(Czz+s_c^2).
+template <class E>
+__device__ __forceinline__ bool search_test(const Params& P, int q, E ey, E ez, E cyy, E czz, E k2, E& d) {
+  const float cz = P.sz[q];
+  const E dy = (E)P.sy[q] - ey, dz = (E)cz - ez;
+  const E sg = sigma_of<E>(P, (E)cz);
+  const E vy = cyy + sg * sg, vz = czz + sg * sg;
+  if (!(dy * dy <= k2 * vy && dz * dz <= k2 * vz)) return false;
+  d = dy * dy / vy + dz * dz / vz;
+  return true;
+}
+
+// Best cluster of row key ir around (py, pz): minimal d inside the window,
+// ties to the smaller input id.  One lane alone.
+template <class E, class S>
+__device__ int search_row(const Params& P, int ir, S py, S pz, E cyy, E czz) {
+  const SearchWin<E> w = search_window<E, S>(P, ir, py, pz, cyy, czz);
   int best = -1, best_id = 0;
   E best_d = (E)0;
-  for (int iz = iz0; iz <= iz1; ++iz) {
-    const int q0 = P.bin_start[g.bin_base + iz * g.ny + iy0];
-    const int q1 = P.bin_start[g.bin_base + iz * g.ny + iy1 + 1];
+  for (int iz = w.iz0; iz <= w.iz1; ++iz) {
+    const int q0 = P.bin_start[w.g.bin_base + iz * w.g.ny + w.iy0];
+    const int q1 = P.bin_start[w.g.bin_base + iz * w.g.ny + w.iy1 + 1];
     for (int q = q0; q < q1; ++q) {
-      const float cz = P.sz[q];
-      const E dy = (E)P.sy[q] - ey, dz = (E)cz - ez;
-      const E sg = sigma_of<E>(P, (E)cz);
-      const E vy = cyy + sg * sg, vz = czz + sg * sg;
-      if (!(dy * dy <= k2 * vy && dz * dz <= k2 * vz)) continue;
-      const E d = dy * dy / vy + dz * dz / vz;
+      E d;
+      if (!search_test<E>(P, q, w.ey, w.ez, w.cyy, w.czz, w.k2, d)) continue;
       if (best < 0 || d <= best_d) {
         const int id = P.sid[q];
         if (best < 0 || d < best_d || id < best_id) { best = q; best_d = d; best_id = id; }
@@ -53,6 +87,98 @@ __device__ int search_row(const Params& P, int ir, S py, S pz, E cyy, E czz) {
     }
   }
   return best;
+}
+
+// The same search for the lanes of a full warp together (float window
+// arithmetic).  A lane's candidates are the clusters of its window's z bins,
+// one contiguous range of the sorted copy per z bin; each searching lane
+// lists its ranges (up to kSegLane of them) in shared memory, the warp
+// concatenates all lanes' candidates by a prefix sum and tests them 32 at a
+// time, one per lane, and every searching lane's best is the minimum of the
+// key (bits of d, input id) over its candidates, kept with a shared-memory
+// atomicMin.  d >= 0, so its bit pattern orders like its value: the key's
+// minimum is the per-lane loop's choice (minimal d, ties to the smaller id),
+// with the same test and the same arithmetic.  A lane whose window spans more
+// z bins searches alone afterwards.
+constexpr int kSegLane = 4;
+struct SearchShared {
+  unsigned long long key[32];   // per searching lane: minimal (d bits, id)
+  int best[32];                 // per searching lane: its sorted position
+  int start[32];                // first concatenated candidate of each lane
+  int q0[32][kSegLane];         // per lane and z bin: first sorted position
+  int cum[32][kSegLane];        // per lane and z bin: candidates up to its end
+};
+
+__device__ __forceinline__ int search_row_warp(const Params& P, bool need, int ir, float py, float pz, float cyy,
+                                               float czz, SearchShared& sh) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  SearchWin<float> w;
+  w.ey = py; w.ez = pz; w.cyy = cyy; w.czz = czz; w.k2 = 0.f;
+  w.iy0 = w.iy1 = w.iz0 = 0; w.iz1 = -1;
+  if (need) w = search_window<float, float>(P, ir, py, pz, cyy, czz);
+  const int nseg = w.iz1 - w.iz0 + 1;
+  const bool coop = need && nseg <= kSegLane;
+  int n_lane = 0;
+  if (coop) {
+#pragma unroll
+    for (int j = 0; j < kSegLane; ++j) {
+      if (j < nseg) {
+        const int b = w.g.bin_base + (w.iz0 + j) * w.g.ny;
+        const int q0 = P.bin_start[b + w.iy0], q1 = P.bin_start[b + w.iy1 + 1];
+        sh.q0[lane][j] = q0;
+        n_lane += q1 - q0;
+      }
+      sh.cum[lane][j] = n_lane;
+    }
+  }
+  int incl = n_lane;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(full, incl, d);
+    if (lane >= d) incl += v;
+  }
+  const int total = __shfl_sync(full, incl, 31);
+  sh.start[lane] = incl - n_lane;
+  sh.key[lane] = ~0ull;
+  sh.best[lane] = -1;
+  const float k2 = P.search_k_f * P.search_k_f;
+  __syncwarp();
+  for (int base = 0; base < total; base += 32) {
+    const int f = base + lane;
+    // owner: the last lane whose first candidate is at or before f
+    int owner = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1)
+      if (sh.start[owner + s] <= f) owner += s;
+    const float oey = __shfl_sync(full, w.ey, owner), oez = __shfl_sync(full, w.ez, owner);
+    const float ocyy = __shfl_sync(full, w.cyy, owner), oczz = __shfl_sync(full, w.czz, owner);
+    bool hit = false;
+    unsigned long long key = 0ull;
+    int q = 0;
+    if (f < total) {
+      const int k = f - sh.start[owner];
+      int j = 0, prev = 0;
+#pragma unroll
+      for (int jj = 0; jj + 1 < kSegLane; ++jj) {
+        const int c = sh.cum[owner][jj];
+        if (j == jj && k >= c) { j = jj + 1; prev = c; }
+      }
+      q = sh.q0[owner][j] + (k - prev);
+      float d;
+      if (search_test<float>(P, q, oey, oez, ocyy, oczz, k2, d)) {
+        key = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)P.sid[q];
+        atomicMin(&sh.key[owner], key);
+        hit = true;
+      }
+    }
+    __syncwarp();
+    if (hit && sh.key[owner] == key) sh.best[owner] = q;
+    __syncwarp();
+  }
+  int cand = coop ? sh.best[lane] : -1;
+  if (need && !coop) cand = search_row<float, float>(P, ir, py, pz, cyy, czz);
+  return cand;
 }
 
 // A residual (state type) in the covariance type; a double-float residual
@@ -86,6 +212,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
   S p[5], top[5], in_p[5];
   C m[15];
   auto hits = P.tl_hits;   // the tracklet's hit slots (stride tcap)
+  __shared__ SearchShared s_search[kMaxBlock / 32];
 
   while (true) {
     // ---- refill lanes without a tracklet from the work queue
@@ -149,6 +276,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
     const bool inside = stepped && !abs_exceeds(to_e<E>(p[0]), EdgeOf<E>::get(P, r));
     go = inside;
     int cand = -1;
+    bool srch = false;   // this lane searches the row's grid
     if (inside) {
       if (up) {
         if (prev_row == r - 1) cand = P.upc[prev];
@@ -156,8 +284,17 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
         const int h = hits[(int64_t)j_up * ts];
         if ((int)P.srow[h] == r) { cand = h; --j_up; }
       }
-      if (cand < 0) cand = search_row<E, S>(P, row0 + r, p[0], p[1], to_e<E>(m[0]), to_e<E>(m[2]));
+      srch = cand < 0;
     }
+    if constexpr (std::is_same<E, float>::value) {
+      if (active == 0xffffffffu) {
+        const int c = search_row_warp(P, srch, row0 + r, to_e<E>(p[0]), to_e<E>(p[1]), to_e<E>(m[0]),
+                                      to_e<E>(m[2]), s_search[threadIdx.x >> 5]);
+        if (srch) cand = c;
+        srch = false;
+      }
+    }
+    if (srch) cand = search_row<E, S>(P, row0 + r, p[0], p[1], to_e<E>(m[0]), to_e<E>(m[2]));
     __syncwarp(active);
     bool ok = false;
     if (cand >= 0) {
