@@ -15,8 +15,9 @@
 // iteration runs with full warps instead of idling lanes of finished
 // tracklets.  The grid search of the lanes that need one is done by the whole
 // warp together (candidates tested one per lane), since per lane its loop
-// length varies and left most lanes idle.  Results do not depend on which
-// lane or order runs a tracklet.
+// length varies and left most lanes idle; lanes whose queue ran dry stay in
+// the loop as idle lanes, so that every warp stays whole for that search.
+// Results do not depend on which lane or order runs a tracklet.
 #include "track_math.cuh"
 
 namespace tpct {
@@ -89,8 +90,8 @@ __device__ int search_row(const Params& P, int ir, S py, S pz, E cyy, E czz) {
   return best;
 }
 
-// The same search for the lanes of a full warp together (float window
-// arithmetic).  A lane's candidates are the clusters of its window's z bins,
+// The same search for all 32 lanes of a warp together (float window
+// arithmetic; lanes that do not search take part with no candidates).  A lane's candidates are the clusters of its window's z bins,
 // one contiguous range of the sorted copy per z bin; each searching lane
 // lists its ranges (up to kSegLane of them) in shared memory, the warp
 // concatenates all lanes' candidates by a prefix sum and tests them 32 at a
@@ -165,9 +166,10 @@ __device__ __forceinline__ int search_row_warp(const Params& P, bool need, int i
         if (j == jj && k >= c) { j = jj + 1; prev = c; }
       }
       q = sh.q0[owner][j] + (k - prev);
+      const unsigned id = (unsigned)P.sid[q];
       float d;
       if (search_test<float>(P, q, oey, oez, ocyy, oczz, k2, d)) {
-        key = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)P.sid[q];
+        key = ((unsigned long long)__float_as_uint(d) << 32) | id;
         atomicMin(&sh.key[owner], key);
         hit = true;
       }
@@ -211,6 +213,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
   int n_step = 0, n_upd = 0, n_test = 0;
   S p[5], top[5], in_p[5];
   C m[15];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) p[i] = top[i] = in_p[i] = conv<S>(0.0f);
+#pragma unroll
+  for (int i = 0; i < 15; ++i) m[i] = conv<C>(0.0f);
   auto hits = P.tl_hits;   // the tracklet's hit slots (stride tcap)
   __shared__ SearchShared s_search[kMaxBlock / 32];
 
@@ -256,8 +262,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
     }
     const uint32_t active = __ballot_sync(0xffffffffu, t >= 0);
     if (active == 0u) break;
-    if (t < 0) continue;
-    __syncwarp(active);
+    const bool live = t >= 0;   // lanes whose queue ran dry stay in the loop, idle, so that warps stay full
+    __syncwarp();
 
     // ---- one row of the current pass.  Every lane with a tracklet runs the
     // same straight-line sequence (transport, candidate, test/update); the
@@ -265,8 +271,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
     // that the covariance arithmetic issues once per warp.
     bool go = true;   // pass continues after this row
     Step<E> st;
-    const E dx = up ? row_dx<E>(P, r) : -row_dx<E>(P, r + 1);
-    const bool stepped = helix_step<E>(to_e<E>(p[2]), to_e<E>(p[3]), to_e<E>(p[4]), dx, kb, smax, st);
+    const E dx = !live ? (E)0 : up ? row_dx<E>(P, r) : -row_dx<E>(P, r + 1);
+    const bool stepped = live && helix_step<E>(to_e<E>(p[2]), to_e<E>(p[3]), to_e<E>(p[4]), dx, kb, smax, st);
     if (stepped) {
       ++n_step;
       p[0] += conv<S>(st.dy); p[1] += conv<S>(st.dz); p[2] += conv<S>(st.ds);
@@ -287,15 +293,14 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
       srch = cand < 0;
     }
     if constexpr (std::is_same<E, float>::value) {
-      if (active == 0xffffffffu) {
-        const int c = search_row_warp(P, srch, row0 + r, to_e<E>(p[0]), to_e<E>(p[1]), to_e<E>(m[0]),
-                                      to_e<E>(m[2]), s_search[threadIdx.x >> 5]);
-        if (srch) cand = c;
-        srch = false;
-      }
+      // every lane of the warp is here (idle lanes included): the whole warp searches
+      const int c = search_row_warp(P, srch, row0 + r, to_e<E>(p[0]), to_e<E>(p[1]), to_e<E>(m[0]),
+                                    to_e<E>(m[2]), s_search[threadIdx.x >> 5]);
+      if (srch) cand = c;
+      srch = false;
     }
     if (srch) cand = search_row<E, S>(P, row0 + r, p[0], p[1], to_e<E>(m[0]), to_e<E>(m[2]));
-    __syncwarp(active);
+    __syncwarp();
     bool ok = false;
     if (cand >= 0) {
       const C ry = to_c<C>(conv<S>(P.sy[cand]) - p[0]), rz = to_c<C>(conv<S>(P.sz[cand]) - p[1]);
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
       else pass = kf_test_update<C, S>(p, m, ry, rz, conv<C>(cluster_var(P, P.sz[cand])), chi2_max);
       if (pass) { ++n_upd; ok = true; }
     }
-    __syncwarp(active);
+    __syncwarp();
     if (inside) {
       {
         if (ok) {
@@ -333,7 +338,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
       r += up ? 1 : -1;
       go = up ? r < R : r >= 0;
     }
-    if (!go && up) {
+    if (live && !go && up) {
       // switch to the downward pass from the outermost accepted cluster.
       // Final clusters go to slots R-1, R-2, ... (never over an unread upward entry).
       up = false;
@@ -349,7 +354,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
       r = top_row - 1;
       go = r >= 0;
     }
-    if (!go) {
+    if (live && !go) {
       P.tl_nhits[t] = n_f;
       P.tl_rowref[t] = in_row;
       P.tl_cnt[t] = n_step;
