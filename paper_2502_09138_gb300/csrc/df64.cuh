@@ -211,6 +211,30 @@ __device__ __forceinline__ df64 fma3_df(float a, df64 x, float b, df64 w, float 
   return fast_two_sum(s3.hi, t);
 }
 
+// The same three sums without the final renormalisation (an intermediate
+// that only feeds exact products: its low part may exceed half an ulp)
+__device__ __forceinline__ df64 fma_df_nr(float a, df64 x, df64 y) {
+  df64 p = two_prod(a, x.hi);
+  p.lo = __fmaf_rn(a, x.lo, p.lo);
+  const df64 s = two_sum(p.hi, y.hi);
+  return df64(s.hi, __fadd_rn(s.lo, __fadd_rn(p.lo, y.lo)));
+}
+__device__ __forceinline__ df64 fma2_df_nr(float a, df64 x, float b, df64 w, df64 y) {
+  const df64 p = two_prod(a, x.hi), q = two_prod(b, w.hi);
+  const df64 s1 = two_sum(y.hi, p.hi);
+  const df64 s2 = two_sum(s1.hi, q.hi);
+  const float lo = __fmaf_rn(a, x.lo, __fmaf_rn(b, w.lo, __fadd_rn(p.lo, q.lo)));
+  return df64(s2.hi, __fadd_rn(__fadd_rn(y.lo, s1.lo), __fadd_rn(s2.lo, lo)));
+}
+__device__ __forceinline__ df64 fma3_df_nr(float a, df64 x, float b, df64 w, float c, df64 v, df64 y) {
+  const df64 p = two_prod(a, x.hi), q = two_prod(b, w.hi), r = two_prod(c, v.hi);
+  const df64 s1 = two_sum(y.hi, p.hi);
+  const df64 s2 = two_sum(s1.hi, q.hi);
+  const df64 s3 = two_sum(s2.hi, r.hi);
+  const float lo = __fmaf_rn(a, x.lo, __fmaf_rn(b, w.lo, __fmaf_rn(c, v.lo, __fadd_rn(__fadd_rn(p.lo, q.lo), r.lo))));
+  return df64(s3.hi, __fadd_rn(__fadd_rn(__fadd_rn(y.lo, s1.lo), __fadd_rn(s2.lo, s3.lo)), lo));
+}
+
 // ---------------------------------------------------------------- conversions used by the kernels
 __device__ __forceinline__ float to_float(float a) { return a; }
 __device__ __forceinline__ float to_float(double a) { return narrow(a); }

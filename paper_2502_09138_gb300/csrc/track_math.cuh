@@ -143,21 +143,23 @@ __device__ __forceinline__ void cov_transport(C* m, J a, J b, J c, J d, J e, J f
 }
 
 // Double-float covariance with float Jacobian entries: the same products,
-// the two or three terms of each entry summed with one renormalisation.
+// the two or three terms of each entry summed with one renormalisation (the
+// rows of F C, which only feed the exact products of the second stage, are
+// left unrenormalised).
 __device__ __forceinline__ void cov_transport(df64* m, float a, float b, float c, float d, float e, float f) {
   const df64 m00 = m[0], m10 = m[1], m11 = m[2], m20 = m[3], m21 = m[4], m22 = m[5];
   const df64 m30 = m[6], m31 = m[7], m32 = m[8], m33 = m[9];
   const df64 m40 = m[10], m41 = m[11], m42 = m[12], m43 = m[13], m44 = m[14];
-  const df64 g00 = fma2_df(a, m20, b, m40, m00);
-  const df64 g02 = fma2_df(a, m22, b, m42, m20);
-  const df64 g04 = fma2_df(a, m42, b, m44, m40);
-  const df64 g10 = fma3_df(c, m20, d, m30, e, m40, m10);
-  const df64 g11 = fma3_df(c, m21, d, m31, e, m41, m11);
-  const df64 g12 = fma3_df(c, m22, d, m32, e, m42, m21);
-  const df64 g13 = fma3_df(c, m32, d, m33, e, m43, m31);
-  const df64 g14 = fma3_df(c, m42, d, m43, e, m44, m41);
-  const df64 g20 = fma_df(f, m40, m20), g21 = fma_df(f, m41, m21), g22 = fma_df(f, m42, m22);
-  const df64 g23 = fma_df(f, m43, m32), g24 = fma_df(f, m44, m42);
+  const df64 g00 = fma2_df_nr(a, m20, b, m40, m00);
+  const df64 g02 = fma2_df_nr(a, m22, b, m42, m20);
+  const df64 g04 = fma2_df_nr(a, m42, b, m44, m40);
+  const df64 g10 = fma3_df_nr(c, m20, d, m30, e, m40, m10);
+  const df64 g11 = fma3_df_nr(c, m21, d, m31, e, m41, m11);
+  const df64 g12 = fma3_df_nr(c, m22, d, m32, e, m42, m21);
+  const df64 g13 = fma3_df_nr(c, m32, d, m33, e, m43, m31);
+  const df64 g14 = fma3_df_nr(c, m42, d, m43, e, m44, m41);
+  const df64 g20 = fma_df_nr(f, m40, m20), g21 = fma_df_nr(f, m41, m21), g22 = fma_df_nr(f, m42, m22);
+  const df64 g23 = fma_df_nr(f, m43, m32), g24 = fma_df_nr(f, m44, m42);
   m[0] = fma2_df(a, g02, b, g04, g00);
   m[1] = fma2_df(a, g12, b, g14, g10);
   m[2] = fma3_df(c, g12, d, g13, e, g14, g11);

@@ -41,7 +41,14 @@ __device__ __forceinline__ SearchWin<E> search_window(const Params& P, int ir, S
   const E k = kF ? (E)P.search_k_f : (E)P.search_k;
   w.k2 = k * k;
   const E sig_hi = kF ? (E)P.sig_hi_f : (E)fmax(P.sig_readout, P.sig_cathode);
-  const E wy = k * sqrt(cyy + sig_hi * sig_hi), wz = k * sqrt(czz + sig_hi * sig_hi);
+  E wy, wz;
+  if constexpr (kF) {
+    // the window only selects bins (1e-4 margin below): a root within a few ulp is enough
+    const float a = cyy + sig_hi * sig_hi, b = czz + sig_hi * sig_hi;
+    wy = k * (a * rsqrtf(a)); wz = k * (b * rsqrtf(b));
+  } else {
+    wy = k * sqrt(cyy + sig_hi * sig_hi); wz = k * sqrt(czz + sig_hi * sig_hi);
+  }
   w.ey = to_e<E>(py);
   w.ez = to_e<E>(pz);
   w.cyy = cyy;
@@ -64,7 +71,10 @@ __device__ __forceinline__ bool search_test(const Params& P, int q, E ey, E ez, 
   const E sg = sigma_of<E>(P, (E)cz);
   const E vy = cyy + sg * sg, vz = czz + sg * sg;
   if (!(dy * dy <= k2 * vy && dz * dz <= k2 * vz)) return false;
-  d = dy * dy / vy + dz * dz / vz;
+  // float d: quotients within 2 ulp (the choice is exact up to that; closer
+  // calls are inside the near-cut band of the search's top-2 gap)
+  if constexpr (std::is_same<E, float>::value) d = __fdividef(dy * dy, vy) + __fdividef(dz * dz, vz);
+  else d = dy * dy / vy + dz * dz / vz;
   return true;
 }
 
@@ -211,10 +221,24 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
   int r = 0, row0 = 0;          // next row; row key of row 0 of the instance
   int prev = 0, prev_row = 0, miss = 0, top_row = 0, top_hit = 0, n_up = 0, j_up = 0, n_f = 0, in_row = 0;
   int n_step = 0, n_upd = 0, n_test = 0;
-  S p[5], top[5], in_p[5];
+  S p[5];
   C m[15];
+  // saved states: the outermost accepted state of the upward pass (top) and
+  // the innermost of the downward pass (in_p); written at accepted clusters,
+  // read at the pass switch and the end.  The mixed filter keeps them in
+  // shared memory (one column per thread), which frees registers of its
+  // FP64-bound loop; the other modes keep them in registers.
+  constexpr bool kSmemState = kMixed;
+  S top_r[kSmemState ? 1 : 5], inp_r[kSmemState ? 1 : 5];
+  __shared__ S s_top[kSmemState ? 5 : 1][kSmemState ? kMaxBlock : 1], s_inp[kSmemState ? 5 : 1][kSmemState ? kMaxBlock : 1];
+  auto top = [&](int i) -> S& {
+    if constexpr (kSmemState) return s_top[i][threadIdx.x]; else return top_r[i];
+  };
+  auto in_p = [&](int i) -> S& {
+    if constexpr (kSmemState) return s_inp[i][threadIdx.x]; else return inp_r[i];
+  };
 #pragma unroll
-  for (int i = 0; i < 5; ++i) p[i] = top[i] = in_p[i] = conv<S>(0.0f);
+  for (int i = 0; i < 5; ++i) p[i] = top(i) = in_p(i) = conv<S>(0.0f);
 #pragma unroll
   for (int i = 0; i < 15; ++i) m[i] = conv<C>(0.0f);
   auto hits = P.tl_hits;   // the tracklet's hit slots (stride tcap)
@@ -251,7 +275,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
           n_up = 1;
           prev = p0; prev_row = r0; miss = 0; top_row = r0; top_hit = p0;
 #pragma unroll
-          for (int i = 0; i < 5; ++i) top[i] = p[i];
+          for (int i = 0; i < 5; ++i) top(i) = p[i];
           n_step = n_upd = n_test = 0;
           up = true;
           r = r0 + 1;
@@ -320,13 +344,13 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
             ++n_up;
             prev = cand; prev_row = r; top_row = r; top_hit = cand;
 #pragma unroll
-            for (int i = 0; i < 5; ++i) top[i] = p[i];
+            for (int i = 0; i < 5; ++i) top(i) = p[i];
           } else {
             hits[(int64_t)(R - 1 - n_f) * ts] = cand;
             ++n_f;
             in_row = r;
 #pragma unroll
-            for (int i = 0; i < 5; ++i) in_p[i] = p[i];
+            for (int i = 0; i < 5; ++i) in_p(i) = p[i];
           }
           if (!abs_below(to_e<E>(p[2]), SmaxOf<E>::get(P))) go = false;
         } else if (++miss > P.max_miss) {
@@ -343,7 +367,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
       // Final clusters go to slots R-1, R-2, ... (never over an unread upward entry).
       up = false;
 #pragma unroll
-      for (int i = 0; i < 5; ++i) { p[i] = top[i]; in_p[i] = top[i]; }
+      for (int i = 0; i < 5; ++i) { p[i] = top(i); in_p(i) = top(i); }
       const C v0 = conv<C>(cluster_var(P, P.sz[top_hit]));
       cov_diag<C>(m, v0, v0, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
       j_up = n_up - 2;
@@ -361,7 +385,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
       P.tl_cnt[ts + t] = n_upd;
       P.tl_cnt[2 * ts + t] = n_test;
 #pragma unroll
-      for (int i = 0; i < 5; ++i) P.tl_par[(int64_t)i * ts + t] = to_double(in_p[i]);
+      for (int i = 0; i < 5; ++i) P.tl_par[(int64_t)i * ts + t] = to_double(in_p(i));
       t = -1;
     }
   }
