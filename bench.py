@@ -36,11 +36,10 @@ sys.path.insert(0, ROOT)
 STAGES = ["grid", "neighbours", "clean_start", "tracklets", "selection", "refit"]
 # FP64 flops of the mixed-precision tracklet filter: a helix step transports
 # the covariance (51 multiply-adds; the float increments go to the
-# double-float state on the FP32 pipes); a chi2 test widens the two
-# double-float residuals (2 adds, the chi2 itself is float); an update forms
-# S (2), det (3), 1/det (1), S^-1 (3), the gain (10 + 10) and the covariance
-# (30 multiply-adds)
-FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 2 * 51, 2, 2 + 3 + 1 + 3 + 30 + 60
+# double-float state on the FP32 pipes); a chi2 test has none (residuals and
+# chi2 in float); an update forms S (2), det (3), 1/det (1), S^-1 (3), the
+# gain (10 entries of 3) and the covariance (30 multiply-adds)
+FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 2 * 51, 0, 2 + 3 + 1 + 3 + 30 + 60
 
 
 def parse():

@@ -480,7 +480,7 @@ __device__ __forceinline__ void cov_rotate(df64* m, const Rot& J) {
 // covariance type C, rotating the state at every change of sector; the
 // reference, deviation, covariance, chi2, x of the previous cluster and the
 // current segment carry over between spans.
-template <class S, class E, class C>
+template <class S, class E, class C, bool kChi2 = true>
 __device__ __forceinline__ void chain_span(const MParams& M, const int* ids, const int* segs, int n, int k_hi,
                                            int k_lo, S* ref, S* d, C* Cm, C& chi2, double& x_prev, int& seg,
                                            int& seg_start, int& status) {
@@ -533,7 +533,8 @@ __device__ __forceinline__ void chain_span(const MParams& M, const int* ids, con
       var = sg * sg;
     }
     const C r0 = (conv<C>(M.y[id]) - ref[0]) - d[0], r1 = (conv<C>(M.z[id]) - ref[1]) - d[1];
-    chi2 += kf_chi2_update<C, S>(d, Cm, r0, r1, var);
+    if constexpr (kChi2) chi2 += kf_chi2_update<C, S>(d, Cm, r0, r1, var);
+    else kf_update<C, S>(d, Cm, r0, r1, var, var);   // leading passes: chi2 never read
     x_prev = xk;
   }
 }
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(128) k_m_refit(const __grid_constant__ MParams
       int seg = m - 1;
       int seg_start = n - M.trk.n_cl[segs[m - 1]];   // first cluster index of the current segment
       if constexpr (STAGE == 1) {
-        chain_span<S, E, C>(M, ids, segs, n, n - 1, 0, ref, d, Cm, chi2, x_prev, seg, seg_start, status);
+        chain_span<S, E, C, false>(M, ids, segs, n, n - 1, 0, ref, d, Cm, chi2, x_prev, seg, seg_start, status);
       } else {
         // the last pass: its first kRefitHead clusters (outermost first) in
         // FP64, where the diffuse prior cancels, the rest in double-float

@@ -278,7 +278,7 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
 }
 
 // Mixed tracklet filter (double-float state, double covariance, float
-// transport; S is the state type, double in the FP64-state form): the
+// transport and float residuals; S is the state type): the
 // chi2 decision in float (1e-6 relative at most, inside the 1e-5 near-cut
 // band) and the state increment K r in float (1e-7 of an increment far
 // smaller than the state); 1/det, the gain and the covariance update, whose
@@ -288,10 +288,9 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
 // float det loses digits and one step does not recover them; the det here is
 // formed in double and its reciprocal refined twice.)
 template <class S>
-__device__ __forceinline__ bool kf_test_update_mixed(S* p, double* m, double r0, double r1, float v,
+__device__ __forceinline__ bool kf_test_update_mixed(S* p, double* m, float fr0, float fr1, float v,
                                                      float chi2_max) {
   const float f00 = narrow(m[0]) + v, f01 = narrow(m[1]), f11 = narrow(m[2]) + v;
-  const float fr0 = narrow(r0), fr1 = narrow(r1);
   const float fdet = f00 * f11 - f01 * f01;
   const float chi2 = (fr0 * (f11 * fr0 - f01 * fr1) + fr1 * (f00 * fr1 - f01 * fr0)) / fdet;
   if (!(chi2 <= chi2_max)) return false;

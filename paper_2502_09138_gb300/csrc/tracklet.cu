@@ -327,11 +327,17 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
     __syncwarp();
     bool ok = false;
     if (cand >= 0) {
-      const C ry = to_c<C>(conv<S>(P.sy[cand]) - p[0]), rz = to_c<C>(conv<S>(P.sz[cand]) - p[1]);
       ++n_test;
       bool pass;
-      if constexpr (kMixed) pass = kf_test_update_mixed(p, m, ry, rz, cluster_var(P, P.sz[cand]), P.chi2_max_f);
-      else pass = kf_test_update<C, S>(p, m, ry, rz, conv<C>(cluster_var(P, P.sz[cand])), chi2_max);
+      if constexpr (kMixed) {
+        // the mixed filter uses the residuals only in float (chi2 decision,
+        // state increment): rounded once from the state's difference
+        const float fry = to_float(conv<S>(P.sy[cand]) - p[0]), frz = to_float(conv<S>(P.sz[cand]) - p[1]);
+        pass = kf_test_update_mixed(p, m, fry, frz, cluster_var(P, P.sz[cand]), P.chi2_max_f);
+      } else {
+        const C ry = to_c<C>(conv<S>(P.sy[cand]) - p[0]), rz = to_c<C>(conv<S>(P.sz[cand]) - p[1]);
+        pass = kf_test_update<C, S>(p, m, ry, rz, conv<C>(cluster_var(P, P.sz[cand])), chi2_max);
+      }
       if (pass) { ++n_upd; ok = true; }
     }
     __syncwarp();
