@@ -12,7 +12,7 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kGridThreads = 512;
 constexpr int kNbDown = 8;                     // down candidates of a hit listed in shared memory
-constexpr int kGridSmemBins = 16384;           // bin counters of one instance held in shared memory
+constexpr int kGridSmemWords = 24576;          // 96 KB of bin counters per CTA (two CTAs per SM)
 
 
 // ------------------------------------------------------------------ step 1: rows and grids
@@ -41,14 +41,16 @@ __device__ __forceinline__ int nearest_row(const Params& P, float xc) {
 // clusters fill the sorted positions [inst_off[i], inst_off[i+1]) and its
 // bins the entries [ib(i), ib(i+1)) of bin_start, ib(i) = inst_off[i] / k +
 // 2 n_rows i, so no step needs a device-wide scan and the counters live in
-// shared memory (an instance whose bins exceed it counts in global memory).
+// shared memory: two 16-bit counters per 32-bit word when the instance's
+// clusters fit 16-bit offsets (49,152 bins), else one 32-bit counter per word
+// (24,576 bins), else global memory.
 // row_start and bin_start hold what device-wide exclusive scans of the row
 // and bin counts would give; the bin grid of a row holds about k clusters
 // per bin with bins roughly square in cm, and its bin_start entries start at
 // row_start / k + 2 ir, which leaves room for max(1, n / k) bins plus the
 // end entry.
 __global__ void __launch_bounds__(kGridThreads) k_grid_build(const __grid_constant__ Params P) {
-  extern __shared__ int g_bins[];               // [kGridSmemBins]
+  extern __shared__ int g_bins[];               // [kGridSmemWords]
   __shared__ int r_cnt[kMaxRows], r_start[kMaxRows + 1];
   __shared__ uint32_t r_ext[4][kMaxRows];
   __shared__ RowGrid r_grid[kMaxRows];
@@ -134,21 +136,36 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_build(const __grid_consta
     // this instance's bin entries [ib0, ib1]
     const int ib0 = c0 / k + 2 * inst * P.n_rows, ib1 = c1 / k + 2 * (inst + 1) * P.n_rows;
     const int span = ib1 - ib0;
-    int* cnt = span <= kGridSmemBins ? g_bins : P.bin_count + ib0;
-    for (int b = tid; b < span; b += kGridThreads) cnt[b] = 0;
+    // counters: packed halves of shared words (every running offset of the
+    // instance, its final value included, stays below 2^16, so a half never
+    // carries into its neighbour), whole shared words, or global memory
+    const bool packed = c1 - c0 < 65536 && span <= 2 * kGridSmemWords;
+    int* cnt = packed || span <= kGridSmemWords ? g_bins : P.bin_count + ib0;
+    unsigned* wcnt = reinterpret_cast<unsigned*>(g_bins);
+    const int n_words = packed ? (span + 1) >> 1 : span;
+    for (int b = tid; b < n_words; b += kGridThreads) cnt[b] = 0;
     __syncthreads();
+    auto bump = [&](int b) -> int {   // add one to counter b, return its old value
+      if (packed) {
+        const int sh = (b & 1) << 4;
+        return (int)((atomicAdd(&wcnt[b >> 1], 1u << sh) >> sh) & 0xffffu);
+      }
+      return atomicAdd(&cnt[b], 1);
+    };
+    auto get = [&](int b) -> int { return packed ? (int)((wcnt[b >> 1] >> ((b & 1) << 4)) & 0xffffu) : cnt[b]; };
     // pass B: bin counts
     for (int c = c0 + tid; c < c1; c += kGridThreads) {
       const RowGrid g = r_grid[P.c_ir[c] - inst * P.n_rows];
       const int b = g.bin_base - ib0 + bin_z(g, P.z[c]) * g.ny + bin_y(g, P.y[c]);
-      atomicAdd(&cnt[b], 1);
+      bump(b);
     }
     __syncthreads();
-    // exclusive scan of the counts in place (a contiguous chunk per thread)
-    const int per = (span + kGridThreads - 1) / kGridThreads;
+    // exclusive scan of the counts in place (a contiguous chunk per thread;
+    // chunks of whole words when packed, so no two threads write one word)
+    const int per = ((span + kGridThreads - 1) / kGridThreads + 1) & ~1;
     const int b_lo = min(tid * per, span), b_hi = min(b_lo + per, span);
     int sum = 0;
-    for (int b = b_lo; b < b_hi; ++b) sum += cnt[b];
+    for (int b = b_lo; b < b_hi; ++b) sum += get(b);
     int incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -160,8 +177,13 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_build(const __grid_consta
     int run = incl - sum;
     for (int q = 0; q < warp; ++q) run += s_wsum[q];
     for (int b = b_lo; b < b_hi; ++b) {
-      const int v = cnt[b];
-      cnt[b] = run;
+      const int v = get(b);
+      if (packed) {
+        const int sh = (b & 1) << 4;
+        wcnt[b >> 1] = (wcnt[b >> 1] & ~(0xffffu << sh)) | ((unsigned)run << sh);
+      } else {
+        cnt[b] = run;
+      }
       P.bin_start[ib0 + b] = c0 + run;
       run += v;
     }
@@ -172,7 +194,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_build(const __grid_consta
       const int r = P.c_ir[c] - inst * P.n_rows;
       const RowGrid g = r_grid[r];
       const int b = g.bin_base - ib0 + bin_z(g, P.z[c]) * g.ny + bin_y(g, P.y[c]);
-      const int pos = c0 + atomicAdd(&cnt[b], 1);
+      const int pos = c0 + bump(b);
       P.sy[pos] = P.y[c];
       P.sz[pos] = P.z[c];
       P.sid[pos] = c;
@@ -497,13 +519,13 @@ void launch_init_rows(const Params& P, cudaStream_t s) {
 void launch_grid_build(const Params& P, cudaStream_t s) {
   static std::once_flag attr;   // the serving runtime enqueues from several threads
   std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_grid_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kGridSmemBins);
+    cudaFuncSetAttribute(k_grid_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kGridSmemWords);
   });
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::max(1, std::min(P.n_inst, n_sm * 2));
-  k_grid_build<<<grid, kGridThreads, 4 * kGridSmemBins, s>>>(P);
+  k_grid_build<<<grid, kGridThreads, 4 * kGridSmemWords, s>>>(P);
 }
 
 template <class Tin, class T>
