@@ -41,11 +41,13 @@ def _ptr(t):
 
 @dataclass
 class DeviceClusters:
-    """Clusters resident on the device (SoA)."""
-    x: torch.Tensor
+    """Clusters resident on the device (SoA).  Tracking reads y, z, row and the
+    offsets; x only when row is None (nearest row), charge never (it is
+    carried for compression): both may be None for a tracking-only caller."""
+    x: torch.Tensor               # or None when row is given
     y: torch.Tensor
     z: torch.Tensor
-    charge: torch.Tensor
+    charge: torch.Tensor          # or None
     row: torch.Tensor            # uint8, or None (row from x)
     sector_offsets: torch.Tensor  # int64 [n_instances + 1]
 
@@ -58,10 +60,13 @@ class DeviceClusters:
         return int(self.sector_offsets.shape[0] - 1)
 
     @classmethod
-    def from_event(cls, ev, device="cuda", with_row=True, non_blocking=False):
+    def from_event(cls, ev, device="cuda", with_row=True, non_blocking=False, tracking_only=False):
+        """tracking_only: leave out x and charge (needs the row)."""
+        if tracking_only and not with_row:
+            raise ValueError("tracking_only needs the row (x is read only when the row is absent)")
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device, non_blocking=non_blocking)
-        return cls(t(ev.x), t(ev.y), t(ev.z), t(ev.charge), t(ev.row) if with_row else None,
-                   t(ev.sector_offsets.astype(np.int64)))
+        return cls(None if tracking_only else t(ev.x), t(ev.y), t(ev.z), None if tracking_only else t(ev.charge),
+                   t(ev.row) if with_row else None, t(ev.sector_offsets.astype(np.int64)))
 
     def as_struct(self) -> B.Clusters:
         return B.Clusters(_ptr(self.x), _ptr(self.y), _ptr(self.z), _ptr(self.charge), _ptr(self.row),

@@ -110,3 +110,9 @@ def test_package_does_not_import_test_data():
     code = ("import sys, paper_2502_09138_gb300 as G; G.Tracker(device='cpu'); "
             "sys.exit(1 if 'synth' in sys.modules else 0)")
     assert subprocess.run([sys.executable, "-c", code], cwd=ROOT).returncode == 0
+
+
+def test_tracking_only_clusters_need_the_row():
+    import paper_2502_09138_gb300 as G
+    with pytest.raises(ValueError):
+        G.DeviceClusters.from_event(None, device="cpu", with_row=False, tracking_only=True)

@@ -85,3 +85,25 @@ def test_clusters_outside_acceptance(event0):
     assert st == 0
     rep = compare(ev, ores, gdbg, gtr)
     assert rep["pass"] and rep["nf_mismatch"] == 0, rep
+
+
+def test_tracking_reads_neither_x_nor_charge_when_the_row_is_given(event0):
+    """Tracking with the row given reads y, z and row only: the same call with
+    x and charge left out (NULL) gives the same tracks."""
+    import torch
+    import paper_2502_09138_gb300 as G
+    cuts = G.default_cuts(sig_readout=event0.sigma.at_readout, sig_cathode=event0.sigma.at_cathode)
+    trk = G.Tracker(precision="mixed", bz=event0.bz, cuts=cuts)
+    res = []
+    for only in (False, True):
+        dc = G.DeviceClusters.from_event(event0, tracking_only=only)
+        assert (dc.x is None) == only and (dc.charge is None) == only
+        out = trk.make_output(event0.n)
+        trk.track(dc, out)
+        torch.cuda.synchronize()
+        assert trk.device_status() == 0
+        res.append(out.to_host())
+    a, b = res
+    assert a["n_tracks"] == b["n_tracks"] > 0
+    for k in ("n_cl", "offset", "cluster_ids", "param", "cov", "chi2"):
+        assert np.array_equal(a[k], b[k]), k
