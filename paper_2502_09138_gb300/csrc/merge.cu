@@ -19,6 +19,9 @@ namespace tpct {
 namespace {
 
 constexpr int kBlock = 256;
+
+// A hint to bring the line holding a (a valid address) into L1.
+__device__ __forceinline__ void prefetch_l1(const void* a) { asm volatile("prefetch.global.L1 [%0];" :: "l"(a)); }
 constexpr int kLenBins = 1024;   // chain-length classes of the refit order (longer chains share the top one)
 
 struct MParams {
@@ -486,6 +489,7 @@ __device__ __forceinline__ void chain_span(const MParams& M, const int* ids, con
                                            int& seg_start, int& status) {
   for (int k = k_hi; k >= k_lo && !status; --k) {
     const int id = ids[k];
+    const int id_next = k > k_lo ? ids[k - 1] : -1;   // the next cluster, prefetched after the transport
     const double xk = M.rx[row_of(M, id)];
     if (k < n - 1) {
       if (k < seg_start) {   // the cluster lies in the previous (inner) segment: rotate
@@ -518,6 +522,11 @@ __device__ __forceinline__ void chain_span(const MParams& M, const int* ids, con
       d[1] += st.j_zs * d[2] + st.j_zt * d[3] + st.j_zq * d[4];
       d[2] += st.j_sq * d[4];
       cov_transport<C, E>(Cm, st);
+    }
+    if (id_next >= 0) {   // its position and row into L1 while this cluster is filtered
+      prefetch_l1(&M.y[id_next]);
+      prefetch_l1(&M.z[id_next]);
+      if (M.row) prefetch_l1(&M.row[id_next]);
     }
     C var;
     if constexpr (is_df64<C>::value) {

@@ -8,6 +8,9 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// A hint to bring the line holding a (a valid address) into L1.
+__device__ __forceinline__ void prefetch_l1(const void* a) { asm volatile("prefetch.global.L1 [%0];" :: "l"(a)); }
+
 __device__ __forceinline__ int tracklet_count(const Params& P) {
   return min(P.row_tl_base[P.n_inst * P.n_rows], P.tcap);
 }
@@ -194,6 +197,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
     if (k < 0) continue;
 
     const int pj = pos[j];
+    const int pj_next = j > 0 ? pos[j - 1] : -1;   // the next cluster of this pass, prefetched below
     const double xj = P.rx[P.srow[pj]];
     // One transport per iteration for every lane: at a pass start the
     // reference restarts from the previous estimate at x_cur, otherwise it
@@ -219,6 +223,13 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
         d[2] += st.j_sq * d[4];
         cov_transport<C, E>(m, st);
       }
+    }
+    // the next cluster's position, row and row radius into L1 while this
+    // one is filtered (each iteration otherwise waits on two dependent loads)
+    if (pj_next >= 0) {
+      prefetch_l1(&P.sy[pj_next]);
+      prefetch_l1(&P.sz[pj_next]);
+      prefetch_l1(&P.srow[pj_next]);
     }
     bool done = status != 0 || pass >= pass_end;
     if (!done) {
