@@ -219,6 +219,7 @@ void fill_params(const tpct_ctx* ctx, const tpct_clusters* cl, int64_t n, const 
   p.n = (int32_t)n;
   p.tcap = (int32_t)pl.tcap;
   p.nbin_cap = (int32_t)pl.nbin;
+  p.hits_by_tracklet = hits_by_tracklet_for((int)ctx->prec) ? 1 : 0;
   p.clusters_per_bin = ctx->clusters_per_bin;
   p.tan_half = ctx->tan_half;
   p.z_max = ctx->z_max;

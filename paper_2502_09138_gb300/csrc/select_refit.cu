@@ -31,8 +31,8 @@ __global__ void k_weights(const __grid_constant__ Params P) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tl; t += gridDim.x * blockDim.x) {
     const int nh = P.tl_nhits[t];
     const uint32_t w = tracklet_weight(P, t, nh);
-    // slots from R-1 down: the lanes of a warp read the same slot (coalesced)
-    for (int j = R - 1; j >= R - nh; --j) atomicMax(&P.W[P.tl_hits[(int64_t)j * P.tcap + t]], w);
+    // slots from R-1 down (slot-major: the lanes of a warp read one slot row)
+    for (int j = R - 1; j >= R - nh; --j) atomicMax(&P.W[P.tl_hits[hit_at(P, t, j)]], w);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int T = P.row_tl_base[P.n_inst * R];
@@ -51,7 +51,7 @@ __global__ void k_own(const __grid_constant__ Params P) {
       const int nh = P.tl_nhits[t];
       const uint32_t w = tracklet_weight(P, t, nh);
       int own = 0;
-      for (int j = R - 1; j >= R - nh; --j) own += P.W[P.tl_hits[(int64_t)j * P.tcap + t]] == w;
+      for (int j = R - 1; j >= R - nh; --j) own += P.W[P.tl_hits[hit_at(P, t, j)]] == w;
       const bool acc = own >= P.n_min && (double)(nh - own) <= P.f_shared * (double)nh;
       if (acc) sel = (1ull << 32) | (uint64_t)own;
     }
@@ -89,7 +89,7 @@ __global__ void k_emit(const __grid_constant__ Params P) {
     // fill the track's id range from its end
     int m = own;
     for (int j = R - 1; j >= R - nh; --j) {
-      const int p = P.tl_hits[(int64_t)j * P.tcap + t];
+      const int p = P.tl_hits[hit_at(P, t, j)];
       if (P.W[p] == w) {
         --m;
         O.cluster_ids[off + m] = P.sid[p];
@@ -351,7 +351,7 @@ __global__ void k_export_tracklets(const __grid_constant__ Params P, tpct_debug_
       int32_t* h = D.tl_hits + (int64_t)t * R;
       for (int r = 0; r < R; ++r) h[r] = -1;
       for (int j = R - nh; j < R; ++j) {
-        const int p = P.tl_hits[(int64_t)j * P.tcap + t];
+        const int p = P.tl_hits[hit_at(P, t, j)];
         h[P.srow[p]] = P.sid[p];
       }
     }

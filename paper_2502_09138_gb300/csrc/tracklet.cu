@@ -241,7 +241,14 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
   for (int i = 0; i < 5; ++i) p[i] = top(i) = in_p(i) = conv<S>(0.0f);
 #pragma unroll
   for (int i = 0; i < 15; ++i) m[i] = conv<C>(0.0f);
-  auto hits = P.tl_hits;   // the tracklet's hit slots (stride tcap)
+  // the tracklet's hit slots: consecutive, or stride tcap (hit_at)
+  constexpr bool kByTracklet = hits_by_tracklet_for(MODE);
+  const int64_t hs = kByTracklet ? 1 : ts;
+  if (P.hits_by_tracklet != (kByTracklet ? 1 : 0)) {   // the host set another layout: refuse
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(P.status, kDevBounds);
+    return;
+  }
+  auto hits = P.tl_hits;
   __shared__ SearchShared s_search[kMaxBlock / 32];
 
   while (true) {
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
           p[4] = conv<S>(0.0f);
           const C v0 = conv<C>(cluster_var(P, P.sz[p0]));
           cov_diag<C>(m, v0, v0, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
-          hits = P.tl_hits + t;
+          hits = P.tl_hits + (kByTracklet ? (int64_t)t * R : (int64_t)t);
           hits[0] = p0;
           n_up = 1;
           prev = p0; prev_row = r0; miss = 0; top_row = r0; top_hit = p0;
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
       if (up) {
         if (prev_row == r - 1) cand = P.upc[prev];
       } else if (j_up >= 0) {
-        const int h = hits[(int64_t)j_up * ts];
+        const int h = hits[(int64_t)j_up * hs];
         if ((int)P.srow[h] == r) { cand = h; --j_up; }
       }
       srch = cand < 0;
@@ -346,13 +353,13 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
         if (ok) {
           miss = 0;
           if (up) {
-            hits[(int64_t)n_up * ts] = cand;
+            hits[(int64_t)n_up * hs] = cand;
             ++n_up;
             prev = cand; prev_row = r; top_row = r; top_hit = cand;
 #pragma unroll
             for (int i = 0; i < 5; ++i) top(i) = p[i];
           } else {
-            hits[(int64_t)(R - 1 - n_f) * ts] = cand;
+            hits[(int64_t)(R - 1 - n_f) * hs] = cand;
             ++n_f;
             in_row = r;
 #pragma unroll
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_tracklets(const __grid_constant__
       cov_diag<C>(m, v0, v0, (C)P.c_s, (C)P.c_t, (C)P.c_qpt);
       j_up = n_up - 2;
       n_f = 1;
-      hits[(int64_t)(R - 1) * ts] = top_hit;
+      hits[(int64_t)(R - 1) * hs] = top_hit;
       in_row = top_row;
       miss = 0;
       r = top_row - 1;
