@@ -87,6 +87,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   q.rdxf = take_arr<const float>(take, n_rows, q.status);
   q.edge = take_arr<const double>(take, n_rows, q.status);
   q.edgef = take_arr<const float>(take, n_rows, q.status);
+  q.nf_tab = take_arr<const float>(take, (int64_t)5 * n_rows, q.status);
   q.row_count = take_arr<int32_t>(take, nr1, q.status);
   q.row_start = take_arr<int32_t>(take, nr1, q.status);
   q.row_tl_count = take_arr<int32_t>(take, nr1, q.status);
@@ -125,7 +126,7 @@ size_t carve(char* base, const Plan& pl, int n_rows, Params* P) {
   q.scan_tmp = (uint64_t*)take(8 * scan_tmp);
   if (P) {
     P->status = q.status; P->work = q.work; P->rx = q.rx; P->rxf = q.rxf;
-    P->rdx = q.rdx; P->rdxf = q.rdxf; P->edge = q.edge; P->edgef = q.edgef;
+    P->rdx = q.rdx; P->rdxf = q.rdxf; P->edge = q.edge; P->edgef = q.edgef; P->nf_tab = q.nf_tab;
     P->row_count = q.row_count; P->row_start = q.row_start;
     P->row_tl_count = q.row_tl_count; P->row_tl_base = q.row_tl_base;
     P->grid = q.grid; P->c_ir = q.c_ir;
@@ -145,7 +146,8 @@ struct RowTable {
   double x[kMaxRows];
 };
 // Row tables: x, the step to the previous row, the sector edge plus margin,
-// in double and float.
+// in double and float; the float constants of the neighbour test of every
+// inner row (formed in double once here instead of per row and lane).
 __global__ void k_set_tables_v(const Params P, const RowTable tab) {
   for (int i = threadIdx.x; i < P.n_rows; i += blockDim.x) {
     const double x = tab.x[i];
@@ -157,6 +159,18 @@ __global__ void k_set_tables_v(const Params P, const RowTable tab) {
     writable(P.rdxf)[i] = (float)dx;
     writable(P.edge)[i] = e;
     writable(P.edgef)[i] = (float)e;
+    float f = 0.f, wyu = 0.f, wzu = 0.f, wyd = 0.f, wzd = 0.f;
+    if (i > 0 && i + 1 < P.n_rows) {
+      const double xu = tab.x[i + 1], xd = tab.x[i - 1];
+      f = (float)((x - xd) / (xu - xd));
+      wyu = (float)(P.nf_wy * (xu - x)); wzu = (float)(P.nf_wz * (xu - x));
+      wyd = (float)(P.nf_wy * (x - xd)); wzd = (float)(P.nf_wz * (x - xd));
+    }
+    writable(P.nf_tab)[5 * i] = f;
+    writable(P.nf_tab)[5 * i + 1] = wyu;
+    writable(P.nf_tab)[5 * i + 2] = wzu;
+    writable(P.nf_tab)[5 * i + 3] = wyd;
+    writable(P.nf_tab)[5 * i + 4] = wzd;
   }
 }
 

@@ -333,10 +333,17 @@ __global__ void __launch_bounds__(kBlock) k_neighbours(const __grid_constant__ P
       for (int p = beg + lane; p < end; p += 32) { P.up[p] = -1; P.down[p] = -1; }
       continue;
     }
-    const double xr = P.rx[r], xu = P.rx[r + 1], xd = P.rx[r - 1];
-    const E f = (E)((xr - xd) / (xu - xd));
-    const E wyu = (E)(P.nf_wy * (xu - xr)), wzu = (E)(P.nf_wz * (xu - xr));
-    const E wyd = (E)(P.nf_wy * (xr - xd)), wzd = (E)(P.nf_wz * (xr - xd));
+    E f, wyu, wzu, wyd, wzd;
+    if constexpr (std::is_same<E, float>::value) {
+      // the row's constants from the table (formed in double once per step)
+      f = P.nf_tab[5 * r]; wyu = P.nf_tab[5 * r + 1]; wzu = P.nf_tab[5 * r + 2];
+      wyd = P.nf_tab[5 * r + 3]; wzd = P.nf_tab[5 * r + 4];
+    } else {
+      const double xr = P.rx[r], xu = P.rx[r + 1], xd = P.rx[r - 1];
+      f = (E)((xr - xd) / (xu - xd));
+      wyu = (E)(P.nf_wy * (xu - xr)); wzu = (E)(P.nf_wz * (xu - xr));
+      wyd = (E)(P.nf_wy * (xr - xd)); wzd = (E)(P.nf_wz * (xr - xd));
+    }
     const E dmax = (E)P.nf_dmax;
     const RowGrid gu = P.grid[ir + 1], gd = P.grid[ir - 1];
     for (int p = beg + lane; p < end; p += 32) {

@@ -107,6 +107,8 @@ struct Params {
   TPCT_ARR(const float) rdxf;  // [n_rows] the same rounded to float
   TPCT_ARR(const double) edge; // [n_rows] rx[r] * tan_half + edge_margin
   TPCT_ARR(const float) edgef; // [n_rows] the same rounded to float
+  TPCT_ARR(const float) nf_tab;  // [5 n_rows] neighbour test per row r: f = (x_r - x_r-1) / (x_r+1 - x_r-1),
+                                 // window half-widths up (y, z) and down (y, z); computed in double, rounded
   float s_max_f;               // s_max rounded to float
   uint32_t* status;            // sticky device status bits
   uint32_t* work;              // [2] work-queue heads of the tracklet and refit kernels
