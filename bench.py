@@ -37,9 +37,10 @@ STAGES = ["grid", "neighbours", "clean_start", "tracklets", "selection", "refit"
 # FP64 flops of the mixed-precision tracklet filter: a helix step transports
 # the covariance (51 multiply-adds; the float increments go to the
 # double-float state on the FP32 pipes); a chi2 test has none (residuals and
-# chi2 in float); an update forms S (2), det (3), 1/det (1), S^-1 (3), the
-# gain (10 entries of 3) and the covariance (30 multiply-adds)
-FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 2 * 51, 0, 2 + 3 + 1 + 3 + 30 + 60
+# chi2 in float); an update is two scalar updates (the measurement covariance
+# is diagonal), each forming S (1), 1/S (1), the gain (5) and the covariance
+# (15 multiply-adds)
+FLOPS_STEP, FLOPS_TEST, FLOPS_UPDATE = 2 * 51, 0, 2 * (1 + 1 + 5 + 30)
 
 
 def parse():

@@ -281,12 +281,8 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
 // transport and float residuals; S is the state type): the
 // chi2 decision in float (1e-6 relative at most, inside the 1e-5 near-cut
 // band) and the state increment K r in float (1e-7 of an increment far
-// smaller than the state); 1/det, the gain and the covariance update, whose
-// subtraction cancels, in double.  (A float det's reciprocal refined by one
-// Newton step in double changed 4 of ~190 k tracklet lists of the
-// 128-collision batch: when S is large and its y-z correlation strong, the
-// float det loses digits and one step does not recover them; the det here is
-// formed in double and its reciprocal refined twice.)
+// smaller than the state); the gain and the covariance update, whose
+// subtraction cancels, in double.
 template <class S>
 __device__ __forceinline__ bool kf_test_update_mixed(S* p, double* m, float fr0, float fr1, float v,
                                                      float chi2_max) {
@@ -294,36 +290,51 @@ __device__ __forceinline__ bool kf_test_update_mixed(S* p, double* m, float fr0,
   const float fdet = f00 * f11 - f01 * f01;
   const float chi2 = (fr0 * (f11 * fr0 - f01 * fr1) + fr1 * (f00 * fr1 - f01 * fr0)) / fdet;
   if (!(chi2 <= chi2_max)) return false;
+  // The measurement covariance is diagonal (v, v), so the 2-D update is
+  // two scalar updates, y then z with the z residual taken after the y step
+  // (sequential processing of independent measurements: the same posterior):
+  // 25 FP64 operations each instead of 61 for the joint one.  Each 1/S by
+  // two Newton-Raphson steps, x <- x + x (1 - S x), from a float seed
+  // (about 23 -> 46 -> 53 bits).
   const double vd = widen(v);
-  const double s00 = m[0] + vd, s01 = m[1], s11 = m[2] + vd;
-  // 1/det of the double det by Newton-Raphson for the reciprocal,
-  // x <- x + x (1 - det x), twice from a float seed (about 23 -> 46 -> 53
-  // bits; four fused multiply-adds), the float seed taken of the double det
-  const double det = s00 * s11 - s01 * s01;
-  const float fd = narrow(det);
-  double idet;
-  if (fabsf(fd) > 1e-30f && fabsf(fd) < 1e30f) {
-    idet = widen(__frcp_rn(fd));
-    idet = fma(idet, fma(-det, idet, 1.0), idet);
-    idet = fma(idet, fma(-det, idet, 1.0), idet);
-  } else {
-    idet = 1.0 / det;
-  }
-  const double i00 = s11 * idet, i01 = -s01 * idet, i11 = s00 * idet;
-  const double c0[5] = {m[0], m[1], m[3], m[6], m[10]};
-  const double c1[5] = {m[1], m[2], m[4], m[7], m[11]};
-  double k0[5], k1[5];
+  auto recip = [](double s) {
+    const float fs = narrow(s);
+    double r;
+    if (fabsf(fs) > 1e-30f && fabsf(fs) < 1e30f) {
+      r = widen(__frcp_rn(fs));
+      r = fma(r, fma(-s, r, 1.0), r);
+      r = fma(r, fma(-s, r, 1.0), r);
+    } else {
+      r = 1.0 / s;
+    }
+    return r;
+  };
+  // y: column 0 of C
+  const double a[5] = {m[0], m[1], m[3], m[6], m[10]};
+  const double ia = recip(a[0] + vd);
+  double k0[5];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    k0[i] = c0[i] * i00 + c1[i] * i01;
-    k1[i] = c0[i] * i01 + c1[i] * i11;
-    p[i] += conv<S>(narrow(k0[i]) * fr0 + narrow(k1[i]) * fr1);
-  }
+  for (int i = 0; i < 5; ++i) k0[i] = a[i] * ia;
   int idx = 0;
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j, ++idx) m[idx] = (m[idx] - k0[i] * c0[j]) - k1[i] * c1[j];
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] = m[idx] - k0[i] * a[j];
+  // z: column 1 of the updated C, residual after the y step
+  const float fr1b = fr1 - narrow(k0[1]) * fr0;
+  const double b[5] = {m[1], m[2], m[4], m[7], m[11]};
+  const double ib = recip(b[1] + vd);
+  double k1[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    k1[i] = b[i] * ib;
+    p[i] += conv<S>(narrow(k0[i]) * fr0 + narrow(k1[i]) * fr1b);
+  }
+  idx = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] = m[idx] - k1[i] * b[j];
   return true;
 }
 
