@@ -93,3 +93,32 @@ def test_pulls_and_chi2_clean_events():
     assert K > 1500
     assert np.all(np.abs(pulls.mean(0)) < 3.0 / np.sqrt(K)), pulls.mean(0)
     assert np.all(np.abs(pulls.std(0) - 1.0) < 0.05), pulls.std(0)
+
+
+def test_sequential_scalar_updates_equal_the_oracle_update():
+    """The tracking kernels update with two scalar measurements, y then z
+    (the z residual taken after the y step), where the oracle takes the joint
+    2-D update; for the diagonal cluster covariance the two are the same
+    posterior and the same chi2 (sequential processing of independent
+    measurements).  Written here in plain numpy against the oracle's update,
+    including prior covariances far wider than the measurement."""
+    r = np.random.default_rng(12)
+    for trial in range(200):
+        A = r.normal(size=(5, 5))
+        scale = np.diag(10.0 ** r.uniform(-3, 3, 5))
+        C = scale @ (A @ A.T + 0.1 * np.eye(5)) @ scale
+        p = r.normal(size=5)
+        m = p[:2] + r.normal(scale=0.1, size=2)
+        v = r.uniform(0.005, 0.05)
+        chi2, p1, C1 = oracle.kf_update(p, C.ravel(), m[0], m[1], v, v)
+        ps, Cs, chi2s = p.copy(), C.copy(), 0.0
+        for k in (0, 1):
+            res = m[k] - ps[k]                    # residual after the previous scalar step
+            S = Cs[k, k] + v
+            K = Cs[:, k] / S
+            chi2s += res * res / S
+            ps = ps + K * res
+            Cs = Cs - np.outer(K, Cs[k, :])
+        assert np.allclose(Cs, C1.reshape(5, 5), rtol=1e-7, atol=1e-9 * np.abs(C).max())
+        assert np.allclose(ps, p1, rtol=1e-9, atol=1e-9)
+        assert chi2s == pytest.approx(chi2, rel=1e-9, abs=1e-12)
