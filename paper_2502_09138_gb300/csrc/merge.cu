@@ -13,7 +13,7 @@
 // and best inner partner (smallest chi2, ties to the smaller index) and
 // mutual best pairs are linked.  Linked tracks form chains, refitted together
 // in FP64 with the reference rotated at every change of sector.
-#include "track_math.cuh"
+#include "refit_update.cuh"
 
 namespace tpct {
 namespace {
@@ -542,8 +542,8 @@ __device__ __forceinline__ void chain_span(const MParams& M, const int* ids, con
       var = sg * sg;
     }
     const C r0 = (conv<C>(M.y[id]) - ref[0]) - d[0], r1 = (conv<C>(M.z[id]) - ref[1]) - d[1];
-    if constexpr (kChi2) chi2 += kf_chi2_update<C, S>(d, Cm, r0, r1, var);
-    else kf_update<C, S>(d, Cm, r0, r1, var, var);   // leading passes: chi2 never read
+    const C c2 = refit_update<C, S>(d, Cm, r0, r1, var);
+    if constexpr (kChi2) chi2 += c2;   // leading passes: chi2 never read
     x_prev = xk;
   }
 }

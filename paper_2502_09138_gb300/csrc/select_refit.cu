@@ -1,7 +1,7 @@
 // Steps 6-7 of sector track finding: selection by owned clusters and shared
 // fraction, output compaction, and the iterated refit of every selected
 // track.  (The paper's "TPC Processing (Tracking)", Tables 1-3.)
-#include "track_math.cuh"
+#include "refit_update.cuh"
 
 namespace tpct {
 namespace {
@@ -236,9 +236,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_refit(const __grid_constant__ Par
       x_prev = xj;
       const C sg = sigma_of<C>(P, conv<C>(P.sz[pj]));
       const C r0 = (conv<C>(P.sy[pj]) - ref[0]) - d[0], r1 = (conv<C>(P.sz[pj]) - ref[1]) - d[1];
-      // the leading passes only move the reference: their chi2 is never read
-      if constexpr (STAGE == 1) kf_update<C, S>(d, m, r0, r1, sg * sg, sg * sg);
-      else chi2 += kf_chi2_update<C, S>(d, m, r0, r1, sg * sg);
+      // (the leading passes only move the reference: their chi2 is never read)
+      chi2 += refit_update<C, S>(d, m, r0, r1, sg * sg);
       if (STAGE == 2 && j >= 1 && n - j >= kRefitHead) {
         // hand the track over to the double-float tail at cluster j - 1
 #pragma unroll
