@@ -191,6 +191,14 @@ __device__ __forceinline__ df64 fms2(df64 m, df64 a, df64 b, df64 c, df64 d) {
   return fast_two_sum(s2.hi, t);
 }
 
+// m - a b
+__device__ __forceinline__ df64 fms1(df64 m, df64 a, df64 b) {
+  const df64 p = two_prod(a.hi, b.hi);
+  const df64 s = two_sum(m.hi, -p.hi);
+  const float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  return fast_two_sum(s.hi, __fsub_rn(__fadd_rn(m.lo, s.lo), lo));
+}
+
 // y + a x + b w for float a, b
 __device__ __forceinline__ df64 fma2_df(float a, df64 x, float b, df64 w, df64 y) {
   const df64 p = two_prod(a, x.hi), q = two_prod(b, w.hi);

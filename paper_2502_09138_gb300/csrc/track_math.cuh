@@ -249,7 +249,8 @@ __device__ __forceinline__ bool kf_test_update(S* p, C* m, C r0, C r1, C v, C ch
 // Double-float tracklet filter: the chi2 decision and the state increment
 // K r are formed in float (1e-7 relative on a cut decision or on an
 // increment much smaller than the state); the gain and the covariance, whose
-// update cancels, stay double-float.
+// update cancels, stay double-float, as two scalar updates (y, then z with
+// the residual after the y step; exact for the diagonal cluster covariance).
 template <>
 __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df64 r0, df64 r1, df64 v,
                                                          df64 chi2_max) {
@@ -258,22 +259,30 @@ __device__ __forceinline__ bool kf_test_update<df64, df64>(df64* p, df64* m, df6
   const float fr0 = to_float(r0), fr1 = to_float(r1);
   const float chi2 = (fr0 * (f11 * fr0 - f01 * fr1) + fr1 * (f00 * fr1 - f01 * fr0)) / (f00 * f11 - f01 * f01);
   if (!(chi2 <= to_float(chi2_max))) return false;
-  const df64 idet = df64(1.0f) / (s00 * s11 - s01 * s01);
-  const df64 i00 = s11 * idet, i01 = -(s01 * idet), i11 = s00 * idet;
-  const df64 c0[5] = {m[0], m[1], m[3], m[6], m[10]};
-  const df64 c1[5] = {m[1], m[2], m[4], m[7], m[11]};
-  df64 k0[5], k1[5];
+  const df64 a[5] = {m[0], m[1], m[3], m[6], m[10]};
+  const df64 ia = df64(1.0f) / s00;
+  df64 k0[5];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    k0[i] = dot2(c0[i], i00, c1[i], i01);
-    k1[i] = dot2(c0[i], i01, c1[i], i11);
-    p[i] += df64(to_float(k0[i]) * fr0 + to_float(k1[i]) * fr1);
-  }
+  for (int i = 0; i < 5; ++i) k0[i] = a[i] * ia;
   int idx = 0;
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j, ++idx) m[idx] = fms2(m[idx], k0[i], c0[j], k1[i], c1[j]);
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] = fms1(m[idx], k0[i], a[j]);
+  const float fr1b = fr1 - to_float(k0[1]) * fr0;
+  const df64 b[5] = {m[1], m[2], m[4], m[7], m[11]};
+  const df64 ib = df64(1.0f) / (b[1] + v);
+  df64 k1[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    k1[i] = b[i] * ib;
+    p[i] += df64(to_float(k0[i]) * fr0 + to_float(k1[i]) * fr1b);
+  }
+  idx = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j, ++idx) m[idx] = fms1(m[idx], k1[i], b[j]);
   return true;
 }
 
